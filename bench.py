@@ -1,0 +1,398 @@
+"""Benchmark: active-particle forces/s and interactions/s of the tree-gravity
+force path on one GB300 (or N replicas under torchrun).
+
+Workload (headline): Hernquist halo, N = 2^20 (M = G = a = 1, r <= 100 a),
+softening h = 0.005, leaf bucket 8, all particles active.  One step is one
+local time step of the paper's gravity path: tree construction from scratch
+(keys, sort, nodes, FP64 monopoles) followed by the relative-criterion walk
+(alpha = 0.0025) against |a| of the previous step.  Before timing, the first
+force is computed with the geometric criterion (theta = 0.5), as the paper
+prescribes for the very first force evaluation.
+
+The periodic TreePM box (128^3 Zel'dovich lattice, PM 256^3) is measured
+beside it and reported under "periodic_treepm".
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "active-particle forces/s and interactions/s at p99 rel. force err <=5e-3; p50/p99 latency"
+FLOPS_PER_INTERACTION = 20  # monopole pair term, FP32 (offset 3, r^2 5 flops... see the design doc)
+
+# ------------------------------------------------------------------ configs
+HERNQUIST = dict(n=1 << 20, seed=W.CONFIG_SEEDS[2], h=0.005, G=1.0, bucket=8, theta=0.5, alpha=0.0025)
+ZELDOVICH = dict(ngrid=128, seed=W.CONFIG_SEEDS[3], pm_n=256, asmth=1.25, rcut=4.5, G=1.0, bucket=8, theta=0.5,
+                 alpha=0.005)
+
+
+def hernquist_inputs():
+    pos, mass = W.hernquist(HERNQUIST["n"], HERNQUIST["seed"])
+    return pos, mass
+
+
+def zeldovich_inputs():
+    return W.zeldovich(ZELDOVICH["ngrid"], ZELDOVICH["seed"])
+
+
+def zeldovich_h():
+    return (1.0 / ZELDOVICH["ngrid"]) / 40.0
+
+
+def root_shift(step: int, base: int):
+    return tuple(float(v) for v in W.root_shift(base * 1000 + step))
+
+
+# ------------------------------------------------------------------ helpers
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    def __init__(self, device: int):
+        self.device = device
+        self.samples = []
+        self._stop = threading.Event()
+        self._proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self._proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + q,
+                                           "--format=csv,noheader,nounits", "-lms", "100"],
+                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self._proc = None
+        return self
+
+    def _read(self):
+        for line in self._proc.stdout:
+            self.samples.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self._proc:
+            self._proc.terminate()
+            try:
+                self._proc.wait(timeout=5)
+            except Exception:
+                self._proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if len(s) > 4 + i and s[4 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def l2_flush(buf):
+    buf.zero_()
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args, rank, world):
+    import torch
+
+    import paper_1909_04667_gb300 as tpm
+
+    dev = torch.device("cuda", 0 if world == 1 else int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    props = torch.cuda.get_device_properties(dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = tpm.Context(dev.index)
+    cfg = HERNQUIST
+    pos, mass = hernquist_inputs()
+    n = len(pos)
+    pos_d = torch.from_numpy(pos).to(dev)
+    mass_d = torch.from_numpy(mass).to(dev)
+    bp = lambda step: tpm.BuildParams(G=cfg["G"], h=cfg["h"], shift=root_shift(step, 2), leaf_bucket=cfg["bucket"])
+    fp_bh = tpm.ForceParams(crit=tpm.CRIT_BH, theta=cfg["theta"])
+    fp_rel = tpm.ForceParams(crit=tpm.CRIT_RELATIVE, alpha=cfg["alpha"])
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 256 MiB > 129 MB L2
+
+    # first force: geometric criterion
+    s = ctx.build_tree(pos_d, mass_d, bp(0))
+    acc, pot, nint = s.compute_forces(fp=fp_bh)
+    s.release()
+    a_old = torch.linalg.vector_norm(acc, dim=1).contiguous()
+    acc_buf = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    pot_buf = torch.empty(n, dtype=torch.float32, device=dev)
+    nint_buf = torch.empty(n, dtype=torch.int32, device=dev)
+
+    def step(k, ev=None):
+        if ev:
+            ev[0].record(stream)
+        sy = ctx.build_tree(pos_d, mass_d, bp(k))
+        if ev:
+            ev[1].record(stream)
+        sy.compute_forces(a_old=a_old, fp=fp_rel, acc=acc_buf, pot=pot_buf, n_int=nint_buf)
+        if ev:
+            ev[2].record(stream)
+        sy.release()
+
+    for k in range(args.warmup):
+        step(1 + k)
+        a_old.copy_(torch.linalg.vector_norm(acc_buf, dim=1))
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    t_build, t_walk, t_step = [], [], []
+    k0, c0 = tpm.launch_counts()
+    with ClockSampler(dev.index) as clk:
+        for k in range(args.steps):
+            l2_flush(flush)
+            step(1000 + k, evs[k])
+        torch.cuda.synchronize()
+    k1, c1 = tpm.launch_counts()
+    for e in evs:
+        t_build.append(e[0].elapsed_time(e[1]))
+        t_walk.append(e[1].elapsed_time(e[2]))
+        t_step.append(e[0].elapsed_time(e[2]))
+    if world > 1:
+        torch.distributed.barrier()
+    ms = sum(t_step) / len(t_step)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    interactions = int(nint_buf.to(torch.int64).sum().item())
+    walk_ms = statistics.mean(t_walk)
+    build_ms = statistics.mean(t_build)
+
+    # ---------------- end to end through the C ABI with host buffers
+    pos_h = torch.from_numpy(pos).pin_memory()
+    mass_h = torch.from_numpy(mass).pin_memory()
+    aold_h = a_old.cpu().pin_memory()
+    acc_h = torch.empty((n, 3), dtype=torch.float32).pin_memory()
+    pot_h = torch.empty(n, dtype=torch.float32).pin_memory()
+    e2e_ms = [float("nan")]
+    for k in range(0 if args.no_e2e else max(3, min(args.steps, 10))):
+        if k == 0:
+            e2e_ms = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sy = ctx.build_tree(pos_h, mass_h, bp(5000 + k))
+        sy.compute_forces(a_old=aold_h, fp=fp_rel, acc=acc_h, pot=pot_h, want_nint=False)
+        sy.release()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_ms = statistics.median(e2e_ms)
+    h2d = pos.nbytes + mass.nbytes + aold_h.numel() * 4
+    d2h = acc_h.numel() * 4 + pot_h.numel() * 4
+
+    # ---------------- periodic TreePM box (128^3, PM 256^3)
+    periodic = None if args.no_periodic else run_periodic(ctx, tpm, torch, dev, stream, flush,
+                                                          max(2, min(args.steps, 5)))
+
+    ctx.close()
+    pk, pk_kind = peaks()
+    sm_max = pk.get("sm_max_mhz", 2070.0)
+    fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+    achieved = interactions * FLOPS_PER_INTERACTION / (walk_ms * 1e-3) / 1e12
+    n_levels = None
+    clocks = clk.summary()
+    value = world * n / (ms * 1e-3)
+    return dict(
+        metric=METRIC, value=value, unit="forces/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
+        ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
+        data="synthetic",
+        config={"workload": "hernquist_n2^20_relative_alpha0.0025", "n_particles": n, "n_active": n,
+                "softening_h": cfg["h"], "leaf_bucket": cfg["bucket"], "criterion": "relative",
+                "alpha": cfg["alpha"], "first_force": "geometric theta=0.5", "global_batch": n,
+                "parallelism": "replicas" if world > 1 else "single",
+                "l2": "flushed (256 MiB write) between timed steps"},
+        interactions_per_s=world * interactions / (walk_ms * 1e-3),
+        interactions_per_particle=interactions / n,
+        build_ms=build_ms, walk_ms=walk_ms,
+        e2e={"value": n / (e2e_ms * 1e-3), "unit": "forces/s", "ms_per_step": e2e_ms,
+             "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        roofline={"bound": "alu", "kernel": "k_walk (relative criterion)", "achieved": achieved,
+                  "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                  "peak_kind": "FP32 CUDA-core peak = SMs x 128 x 2 x %.0f MHz (%s sm_max)" % (sm_max, pk_kind),
+                  "algorithmic": "%d flops x %d useful interactions per launch" % (FLOPS_PER_INTERACTION,
+                                                                                    interactions)},
+        gpu_launches=int(k1 - k0),
+        cub_calls=int(c1 - c0),
+        clocks=clocks,
+        periodic_treepm=periodic,
+    )
+
+
+def run_periodic(ctx, tpm, torch, dev, stream, flush, steps):
+    cfg = ZELDOVICH
+    pos, mass = zeldovich_inputs()
+    n = len(pos)
+    pos_d = torch.from_numpy(pos).to(dev)
+    mass_d = torch.from_numpy(mass).to(dev)
+    h = zeldovich_h()
+    bp = lambda k: tpm.BuildParams(G=cfg["G"], h=h, periodic=True, box=1.0, shift=root_shift(k, 3),
+                                   leaf_bucket=cfg["bucket"])
+    common = dict(treepm=True, pm_n=cfg["pm_n"], asmth=cfg["asmth"], rcut=cfg["rcut"])
+    fp_bh = tpm.ForceParams(crit=tpm.CRIT_BH, theta=cfg["theta"], **common)
+    fp_rel = tpm.ForceParams(crit=tpm.CRIT_RELATIVE, alpha=cfg["alpha"], **common)
+    s = ctx.build_tree(pos_d, mass_d, bp(0))
+    s.pm_long_range(fp_bh)
+    acc, pot, nint = s.compute_forces(fp=fp_bh)
+    s.release()
+    a_old = torch.linalg.vector_norm(acc, dim=1).contiguous()
+    acc_b = torch.empty_like(acc)
+    pot_b = torch.empty_like(pot)
+    nint_b = torch.empty_like(nint)
+    res = []
+    for k in range(steps + 2):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        l2_flush(flush)
+        ev[0].record(stream)
+        sy = ctx.build_tree(pos_d, mass_d, bp(100 + k))
+        ev[1].record(stream)
+        sy.pm_long_range(fp_rel)
+        ev[2].record(stream)
+        sy.compute_forces(a_old=a_old, fp=fp_rel, acc=acc_b, pot=pot_b, n_int=nint_b)
+        ev[3].record(stream)
+        sy.release()
+        torch.cuda.synchronize()
+        if k >= 2:
+            res.append([ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])])
+    r = np.array(res).mean(0)
+    ms = float(r.sum())
+    inter = int(nint_b.to(torch.int64).sum().item())
+    return {"workload": "zeldovich_128^3_pm256_relative_alpha0.005", "value": n / (ms * 1e-3), "unit": "forces/s",
+            "ms_per_step": ms, "build_ms": float(r[0]), "pm_ms": float(r[1]), "walk_interp_ms": float(r[2]),
+            "interactions_per_particle": inter / n}
+
+
+# ------------------------------------------------------------------ CPU oracle
+def run_oracle_sample(sample: int, nthreads: int = 0):
+    """The FP64 oracle (as it stands) on a bounded sample of the headline
+    workload: the whole tree build plus the relative-criterion walk of
+    `sample` random active particles, |a_old| from its own geometric pass."""
+    import oracle
+
+    cfg = HERNQUIST
+    pos, mass = hernquist_inputs()
+    n = len(pos)
+    tg = W.random_targets(n, sample, 77)
+    shift = root_shift(0, 2)
+    t0 = time.perf_counter()
+    tree = oracle.Tree(pos, mass, bucket=cfg["bucket"], shift=shift)
+    t_build = time.perf_counter() - t0
+    a_bh, _, _ = tree.walk(tg, cfg["G"], cfg["h"], theta=cfg["theta"], nthreads=nthreads)
+    a_old = np.linalg.norm(a_bh, axis=1).astype(np.float32)
+    t0 = time.perf_counter()
+    _, _, nint = tree.walk(tg, cfg["G"], cfg["h"], crit="rel", alpha=cfg["alpha"], a_old=a_old, nthreads=nthreads)
+    t_walk = time.perf_counter() - t0
+    # forces/s of a full step (build + all-particle walk) extrapolated from the sample
+    t_step = t_build + t_walk * n / len(tg)
+    return dict(value=n / t_step, unit="forces/s", t_build=t_build, t_walk_sample=t_walk, sample=len(tg),
+                interactions_per_particle=float(nint.mean()))
+
+
+def cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import oracle
+
+    oracle.build()
+    sample = 65536
+    vals = []
+    for _ in range(args.warmup):
+        run_oracle_sample(sample)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(run_oracle_sample(sample))
+    wall = time.perf_counter() - t0
+    v = statistics.median([r["value"] for r in vals])
+    ms = statistics.median([(1 << 20) / r["value"] * 1e3 for r in vals])
+    c = cores()
+    return dict(
+        impl="reference", metric=METRIC, value=v, unit="forces/s", n_gpus=world, steps=args.steps,
+        warmup=args.warmup, ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+        data="synthetic",
+        config={"workload": "hernquist_n2^20_relative_alpha0.0025", "n_particles": 1 << 20, "leaf_bucket": 8,
+                "criterion": "relative", "alpha": 0.0025},
+        cpu_baseline={"value": v, "unit": "forces/s", "cores": c, "kind": "oracle",
+                      "sample": "whole tree build + relative walk of %d random active particles per step, "
+                                "extrapolated to all 2^20" % sample},
+        e2e={"value": v, "unit": "forces/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        wall_s=wall,
+    )
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
+    ap.add_argument("--no-periodic", action="store_true", help="skip the periodic TreePM measurement")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    if world > 1:
+        import torch
+
+        torch.distributed.init_process_group("nccl")
+    out = run_ours(args, rank, world)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            import oracle
+
+            oracle.build()
+            r = run_oracle_sample(65536)
+            out["cpu_baseline"] = {"value": r["value"], "unit": "forces/s", "cores": cores(), "kind": "oracle",
+                                   "sample": "whole tree build + relative walk of %d random active particles, "
+                                             "extrapolated to all 2^20" % r["sample"]}
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/*
+ * treepm.h -- C ABI of libtreepm, a GB300 (sm_103a) implementation of the
+ * TreePM gravitational force on the currently active particles, as described
+ * in Weinberger, Springel & Pakmor, "The AREPO public code release"
+ * (Sec. 3 gravity, Sec. 7.2 local time steps).
+ *
+ * The library builds an oct-tree with monopole moments for a particle set
+ * (Sec. 3.1), keeps it resident on the GPU, and evaluates the force and
+ * potential on any subset of "active" particles from the full mass
+ * distribution (Sec. 7.3: an active particle interacts with all mass).  For a
+ * periodic box the force is split into a short-range tree part and a
+ * long-range particle-mesh part (Sec. 3.3, 3.4).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Every call returns a tpm_status.  Nothing is thrown and nothing aborts
+ *   across the ABI.  tpm_last_error() gives a message for the last failing
+ *   call of the calling thread.
+ * - Pointers may be host or device memory; the library tells them apart with
+ *   cudaPointerGetAttributes.  Device pointers must belong to the context's
+ *   device.  With host pointers a call copies inputs in, runs, copies results
+ *   out and synchronises the stream before returning; with device pointers a
+ *   call is stream-ordered on `stream` (a cudaStream_t, NULL = legacy default
+ *   stream) and returns once the work is enqueued (the tree build itself
+ *   synchronises `stream` between tree levels).
+ * - The caller owns every buffer it passes.  Inputs are read during the call
+ *   (host) or before the stream reaches the end of the call's work (device)
+ *   and may be reused afterwards.  The library owns the resident trees and
+ *   all of its scratch memory, drawn from a per-context pool under the HBM
+ *   budget given at tpm_create.
+ * - Arrays are tightly packed, C order: positions are n x 3 doubles
+ *   (x, y, z per particle), accelerations n_active x 3 floats.
+ * - Units are set by G; the library applies no other scaling.
+ */
+#ifndef TREEPM_H
+#define TREEPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TPM_API_VERSION 1
+
+typedef struct tpm_ctx tpm_ctx; /* opaque: device, memory pool, resident systems */
+typedef uint64_t tpm_sys;       /* handle of a resident particle system; 0 is never valid */
+
+typedef enum {
+    TPM_OK = 0,
+    TPM_EINVAL = -1,           /* malformed argument (null pointer, bad size, bad parameter) */
+    TPM_EBUDGET = -2,          /* admission refused: the call would exceed the HBM budget; no side effects */
+    TPM_ENOSYS_HANDLE = -3,    /* unknown or released system handle */
+    TPM_ECUDA = -4,            /* a CUDA runtime / cuFFT call failed; the message names it */
+    TPM_ETIMEDOUT = -5,        /* a bounded device wait gave up; the context stays usable */
+    TPM_ENAN = -6              /* non-finite input (position, mass, |a_old|) */
+} tpm_status;
+
+typedef enum {
+    TPM_CRIT_BH = 0,       /* geometric criterion: open if L > theta d (Sec. 3.1) */
+    TPM_CRIT_RELATIVE = 1  /* relative criterion: open if G M L^2 / d^4 > alpha |a_old| (Sec. 3.1) */
+} tpm_crit;
+
+/* Parameters of a tree build (Sec. 3.1, 3.2). */
+typedef struct {
+    double G;            /* gravitational constant, > 0 */
+    double h;            /* spline softening support, > 0: Newtonian beyond h; h = 2.8 eps (Sec. 3.2) */
+    int32_t periodic;    /* 0: open boundaries; 1: periodic cube [0, box)^3 (needs TreePM forces) */
+    double box;          /* periodic box side (> 0; ignored when periodic = 0) */
+    double shift[3];     /* random root placement in [0, 1)^3 drawn by the caller per build
+                            (Sec. 3.1: randomised tree domain / random box shift) */
+    int32_t leaf_bucket; /* B >= 1: a cell holding more than B particles is split; B = 1 is the paper's tree */
+} tpm_build_params;
+
+/* Parameters of a force evaluation (Sec. 3.1, 3.4; names of Table 1). */
+typedef struct {
+    int32_t crit;       /* tpm_crit */
+    double theta;       /* ErrTolTheta, used when crit = TPM_CRIT_BH (> 0) */
+    double alpha;       /* ErrTolForceAcc, used when crit = TPM_CRIT_RELATIVE (>= 0) */
+    int32_t box_guard;  /* 1: always open a node whose 1.2 L cube around its centre holds the particle */
+    int32_t treepm;     /* 1: short-range tree force + long-range PM (periodic systems only) */
+    int32_t pm_n;       /* PMGRID: mesh points per side (power of two, 8..1024) */
+    double asmth;       /* ASMTH a_s: split scale r_s = a_s box / pm_n */
+    double rcut;        /* RCUT a_cut: tree cutoff radius a_cut r_s */
+} tpm_force_params;
+
+/* Version of this header the library was built from (TPM_API_VERSION). */
+int tpm_version(void);
+
+/* Process-wide counts since the library was loaded: launches of the
+ * library's own kernels, and calls of CUB device primitives (radix sort,
+ * scan), each of which launches a few kernels of its own.  Either pointer
+ * may be NULL. */
+int tpm_launch_counts(uint64_t *kernels, uint64_t *cub_calls);
+
+/* Message for the last failing call on the calling thread ("" if none).
+ * The pointer stays valid until the thread's next library call. */
+const char *tpm_last_error(void);
+
+/* Creates a context on CUDA device `device` whose allocations (trees, meshes,
+ * scratch) may total at most `hbm_budget_bytes` (0 = 90% of the free memory).
+ * *ctx receives the context.  Errors: TPM_EINVAL (null ctx, bad device),
+ * TPM_ECUDA. */
+int tpm_create(tpm_ctx **ctx, int device, size_t hbm_budget_bytes);
+
+/* Releases every system of the context and the context itself.  Waits for the
+ * context's outstanding work.  A null ctx is a no-op. */
+int tpm_destroy(tpm_ctx *ctx);
+
+/* Bytes currently held by resident systems and the budget. */
+int tpm_memory(const tpm_ctx *ctx, size_t *used_bytes, size_t *budget_bytes);
+
+/*
+ * Builds the oct-tree of n particles and keeps it resident (Sec. 3.1):
+ * cubic root of power-of-two side L0 (open boundaries: the smallest with
+ * L0 >= 1.25 x the largest extent, placed at lo - shift (L0 - extent) on the
+ * 2^-21 L0 grid; periodic: [0, box) after shifting all positions by
+ * shift x box and wrapping), 63-bit Morton keys of the 21-bit cell
+ * coordinates, a stable (key, index) sort, the cells of every level that hold
+ * particles and whose parent holds more than B, and FP64 masses and centres
+ * of mass summed children-first in ascending octant order.  The tree is
+ * rebuilt from scratch for every call, as in the paper (one build per local
+ * step).
+ *   pos   n x 3 positions (FP64).  Periodic positions must lie in [0, box).
+ *   mass  n masses (FP32, > 0).
+ *   out   receives the system handle.
+ * Errors: TPM_EINVAL (n < 1, n > 2^31 - 1, bad params), TPM_ENAN (non-finite
+ * position or mass), TPM_EBUDGET, TPM_ECUDA.
+ */
+int tpm_build_tree(tpm_ctx *ctx, const double *pos, const float *mass, int64_t n, const tpm_build_params *p,
+                   void *stream, tpm_sys *out);
+
+/*
+ * Long-range particle-mesh potential of a periodic system (Sec. 3.3, 3.4):
+ * CIC assignment of all mass onto pm_n^3 mesh points at x = i box / pm_n,
+ * FFT, multiplication by -4 pi G / k^2 exp(-k^2 r_s^2) / W(k)^2 with the CIC
+ * window W = prod_a sinc^2(k_a dx / 2) and the k = 0 mode removed (mean
+ * density subtracted), inverse FFT.  The mesh stays with the system until the
+ * next call or release; tpm_compute_forces with treepm = 1 interpolates from
+ * it.  Errors: TPM_EINVAL (open system, bad pm_n / asmth), TPM_ENOSYS_HANDLE,
+ * TPM_EBUDGET, TPM_ECUDA.
+ */
+int tpm_pm_long_range(tpm_ctx *ctx, tpm_sys s, const tpm_force_params *p, void *stream);
+
+/*
+ * Gravitational acceleration and potential on active particles (Sec. 3.1-3.4).
+ * Each active particle walks the tree from the root: with treepm, a node whose
+ * cube lies farther than a_cut r_s is skipped; a node is opened when the
+ * particle lies in the 1.2 L cube around the node centre (box_guard) or the
+ * criterion asks for it; an opened internal node hands over to its children,
+ * an opened leaf interacts particle by particle (never with the particle
+ * itself), and an unopened node contributes its monopole.  The pair law is
+ * the spline-softened Newtonian force (Sec. 3.2), times the short-range
+ * factor erfc(r/2r_s) + r/(sqrt(pi) r_s) exp(-r^2/4r_s^2) under TreePM, to
+ * which the mesh force (4-point finite differences, CIC interpolation) is then
+ * added.  Pair arithmetic is FP32 on positions taken relative to node and
+ * group centres in FP64.
+ *   active_ids  n_active indices into the particle order given at build time,
+ *               or NULL for all particles in that order (n_active must be n).
+ *   a_old       n_active |a| from the previous evaluation (relative criterion),
+ *               or NULL (only with TPM_CRIT_BH).
+ *   acc         out: n_active x 3 accelerations, in active_ids order.
+ *   pot         out: n_active potentials (may be NULL).  Periodic potentials
+ *               are defined up to a constant.
+ *   n_int       out: n_active particle-node + particle-particle interaction
+ *               counts (may be NULL): the cost factor g_i of Sec. 8.
+ * Errors: TPM_EINVAL, TPM_ENOSYS_HANDLE, TPM_ENAN (non-finite a_old),
+ * TPM_EBUDGET, TPM_ECUDA.
+ */
+int tpm_compute_forces(tpm_ctx *ctx, tpm_sys s, const uint32_t *active_ids, int64_t n_active, const float *a_old,
+                       const tpm_force_params *p, float *acc, float *pot, uint32_t *n_int, void *stream);
+
+/* Frees a resident system.  Waits for its outstanding work. */
+int tpm_release(tpm_ctx *ctx, tpm_sys s);
+
+/* Size and root of a resident system: particle count, node count, root corner
+ * x0[3] and side L0 (periodic: x0 = 0, L0 = box). */
+int tpm_tree_info(tpm_ctx *ctx, tpm_sys s, int64_t *n, int64_t *n_nodes, double *x0, double *L0);
+
+/*
+ * Host copies of a resident tree, for checking (synchronous).  Any pointer may
+ * be NULL.  Particle arrays have n entries in sorted order: key (Morton key of
+ * the 21-bit cell coordinates, x in bit 0, y bit 1, z bit 2 of each triplet),
+ * perm (original index).  Node arrays have n_nodes entries in depth-first
+ * pre-order (children in ascending octant): level, prefix (key >> 3 (21 -
+ * level)), first sorted particle, particle count, skip (index of the first
+ * node after the subtree), FP64 mass and centre of mass (n_nodes x 3).
+ * xtree (n x 3, original order) receives the positions the tree uses (after
+ * the periodic shift and wrap).
+ */
+int tpm_tree_export(tpm_ctx *ctx, tpm_sys s, uint64_t *key, uint32_t *perm, uint8_t *level, uint64_t *prefix,
+                    uint32_t *first, uint32_t *count, uint32_t *skip, double *mass, double *com, double *xtree);
+
+/* Host copy of the long-range mesh potential (pm_n^3 floats, C order x, y, z)
+ * of the last tpm_pm_long_range on s.  Synchronous. */
+int tpm_pm_export(tpm_ctx *ctx, tpm_sys s, float *phi, int64_t count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TREEPM_H */

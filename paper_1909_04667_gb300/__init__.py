@@ -1,0 +1,272 @@
+"""Python binding of libtreepm: the TreePM gravitational force on active
+particles (Weinberger, Springel & Pakmor, "The AREPO public code release",
+Sec. 3) on a GB300 GPU.
+
+This module only marshals arguments: every step of the force path runs in the
+CUDA kernels of ``libtreepm.so`` behind the C ABI of ``include/treepm.h``.
+PyTorch supplies device memory and the current stream.  The names follow the
+C functions: ``build_tree``, ``pm_long_range``, ``compute_forces``,
+``release``, ``tree_info``, ``tree_export``, ``pm_export``.
+
+There is no CPU fallback: if the library is missing or cannot be loaded,
+importing this module raises ``ImportError``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _build
+
+__all__ = ["Context", "System", "BuildParams", "ForceParams", "TreePMError", "lib_path", "CRIT_BH",
+           "CRIT_RELATIVE"]
+
+CRIT_BH = 0
+CRIT_RELATIVE = 1
+
+_STATUS = {0: "TPM_OK", -1: "TPM_EINVAL", -2: "TPM_EBUDGET", -3: "TPM_ENOSYS_HANDLE", -4: "TPM_ECUDA",
+           -5: "TPM_ETIMEDOUT", -6: "TPM_ENAN"}
+
+
+class TreePMError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (_STATUS.get(status, status), msg))
+        self.status = status
+
+
+class _BuildParams(C.Structure):
+    _fields_ = [("G", C.c_double), ("h", C.c_double), ("periodic", C.c_int32), ("box", C.c_double),
+                ("shift", C.c_double * 3), ("leaf_bucket", C.c_int32)]
+
+
+class _ForceParams(C.Structure):
+    _fields_ = [("crit", C.c_int32), ("theta", C.c_double), ("alpha", C.c_double), ("box_guard", C.c_int32),
+                ("treepm", C.c_int32), ("pm_n", C.c_int32), ("asmth", C.c_double), ("rcut", C.c_double)]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def _load():
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError("libtreepm.so is not built (%s); run __graft_entry__.build() or "
+                          "python -m paper_1909_04667_gb300._build" % path)
+    try:
+        lib = C.CDLL(path)
+    except OSError as e:
+        raise ImportError("cannot load %s: %s" % (path, e)) from e
+    i32, i64, vp, sz = C.c_int, C.c_int64, C.c_void_p, C.c_size_t
+    sig = {
+        "tpm_version": (i32, []),
+        "tpm_last_error": (C.c_char_p, []),
+        "tpm_create": (i32, [C.POINTER(vp), i32, sz]),
+        "tpm_destroy": (i32, [vp]),
+        "tpm_memory": (i32, [vp, C.POINTER(sz), C.POINTER(sz)]),
+        "tpm_build_tree": (i32, [vp, vp, vp, i64, C.POINTER(_BuildParams), vp, C.POINTER(C.c_uint64)]),
+        "tpm_pm_long_range": (i32, [vp, C.c_uint64, C.POINTER(_ForceParams), vp]),
+        "tpm_compute_forces": (i32, [vp, C.c_uint64, vp, i64, vp, C.POINTER(_ForceParams), vp, vp, vp, vp]),
+        "tpm_release": (i32, [vp, C.c_uint64]),
+        "tpm_tree_info": (i32, [vp, C.c_uint64, C.POINTER(i64), C.POINTER(i64), vp, vp]),
+        "tpm_tree_export": (i32, [vp, C.c_uint64] + [vp] * 10),
+        "tpm_pm_export": (i32, [vp, C.c_uint64, vp, i64]),
+        "tpm_launch_counts": (i32, [C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def _check(status: int):
+    if status != 0:
+        raise TreePMError(status, _lib.tpm_last_error().decode(errors="replace"))
+
+
+def _ptr(x):
+    """Address of a torch tensor (host or device) or numpy array; None -> NULL."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    raise TypeError("expected a torch tensor or numpy array, got %r" % type(x))
+
+
+def _stream(stream, device):
+    if stream is not None:
+        return stream if isinstance(stream, int) else stream.cuda_stream
+    import torch
+
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+@dataclass
+class BuildParams:
+    G: float = 1.0
+    h: float = 0.01
+    periodic: bool = False
+    box: float = 1.0
+    shift: tuple = (0.0, 0.0, 0.0)
+    leaf_bucket: int = 8
+
+    def _c(self):
+        return _BuildParams(self.G, self.h, int(self.periodic), self.box, (C.c_double * 3)(*self.shift),
+                            int(self.leaf_bucket))
+
+
+@dataclass
+class ForceParams:
+    crit: int = CRIT_BH
+    theta: float = 0.7
+    alpha: float = 0.0025
+    box_guard: bool = True
+    treepm: bool = False
+    pm_n: int = 256
+    asmth: float = 1.25
+    rcut: float = 4.5
+
+    def _c(self):
+        return _ForceParams(int(self.crit), self.theta, self.alpha, int(self.box_guard), int(self.treepm),
+                            int(self.pm_n), self.asmth, self.rcut)
+
+
+class Context:
+    """A libtreepm context on one CUDA device (``tpm_create``)."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 0):
+        h = C.c_void_p()
+        _check(_lib.tpm_create(C.byref(h), int(device), int(budget_bytes)))
+        self._h = h
+        self.device = int(device)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.tpm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def memory(self):
+        used, budget = C.c_size_t(), C.c_size_t()
+        _check(_lib.tpm_memory(self._h, C.byref(used), C.byref(budget)))
+        return used.value, budget.value
+
+    def build_tree(self, pos, mass, params: BuildParams, stream=None) -> "System":
+        """``tpm_build_tree``: pos (n, 3) float64, mass (n,) float32, on host or device."""
+        n = int(pos.shape[0])
+        if tuple(pos.shape) != (n, 3) or int(mass.shape[0]) != n:
+            raise ValueError("pos must be (n, 3) and mass (n,)")
+        _dtype_check(pos, "float64")
+        _dtype_check(mass, "float32")
+        out = C.c_uint64()
+        cp = params._c()
+        _check(_lib.tpm_build_tree(self._h, _ptr(pos), _ptr(mass), n, C.byref(cp), _stream(stream, self.device),
+                                   C.byref(out)))
+        return System(self, out.value, n, params)
+
+
+def _dtype_check(x, name):
+    dt = str(x.dtype).replace("torch.", "")
+    if dt != name:
+        raise TypeError("expected %s, got %s" % (name, dt))
+
+
+class System:
+    """A resident particle system (``tpm_sys``)."""
+
+    def __init__(self, ctx: Context, handle: int, n: int, params: BuildParams):
+        self.ctx, self.handle, self.n, self.params = ctx, handle, n, params
+
+    def release(self):
+        if self.handle:
+            _check(_lib.tpm_release(self.ctx._h, self.handle))
+            self.handle = 0
+
+    def pm_long_range(self, fp: ForceParams, stream=None):
+        cp = fp._c()
+        _check(_lib.tpm_pm_long_range(self.ctx._h, self.handle, C.byref(cp), _stream(stream, self.ctx.device)))
+
+    def compute_forces(self, active_ids=None, a_old=None, fp: ForceParams = None, acc=None, pot=None, n_int=None,
+                       stream=None, want_pot=True, want_nint=True):
+        """``tpm_compute_forces``.  Inputs and outputs may be torch tensors on
+        the device or on the host (or numpy arrays).  Missing outputs are
+        allocated on the device of the context as torch tensors."""
+        import torch
+
+        fp = fp or ForceParams()
+        n_act = self.n if active_ids is None else int(active_ids.shape[0])
+        if active_ids is not None and str(active_ids.dtype).replace("torch.", "") not in ("uint32", "int32"):
+            raise TypeError("active_ids must be 32-bit indices, got %s" % active_ids.dtype)
+        if a_old is not None:
+            _dtype_check(a_old, "float32")
+        dev = torch.device("cuda", self.ctx.device)
+        if acc is None:
+            acc = torch.empty((n_act, 3), dtype=torch.float32, device=dev)
+        if pot is None and want_pot:
+            pot = torch.empty(n_act, dtype=torch.float32, device=dev)
+        if n_int is None and want_nint:
+            n_int = torch.empty(n_act, dtype=torch.int32, device=dev)
+        cp = fp._c()
+        _check(_lib.tpm_compute_forces(self.ctx._h, self.handle, _ptr(active_ids), n_act, _ptr(a_old), C.byref(cp),
+                                       _ptr(acc), _ptr(pot), _ptr(n_int), _stream(stream, self.ctx.device)))
+        return acc, pot, n_int
+
+    def tree_info(self):
+        n, nn = C.c_int64(), C.c_int64()
+        x0 = np.zeros(3)
+        L0 = np.zeros(1)
+        _check(_lib.tpm_tree_info(self.ctx._h, self.handle, C.byref(n), C.byref(nn), x0.ctypes.data,
+                                  L0.ctypes.data))
+        return dict(n=n.value, n_nodes=nn.value, x0=x0, L0=float(L0[0]))
+
+    def tree_export(self) -> dict:
+        info = self.tree_info()
+        n, m = info["n"], info["n_nodes"]
+        out = dict(key=np.zeros(n, np.uint64), perm=np.zeros(n, np.uint32), level=np.zeros(m, np.uint8),
+                   prefix=np.zeros(m, np.uint64), first=np.zeros(m, np.uint32), count=np.zeros(m, np.uint32),
+                   skip=np.zeros(m, np.uint32), mass=np.zeros(m), com=np.zeros((m, 3)), xtree=np.zeros((n, 3)))
+        _check(_lib.tpm_tree_export(self.ctx._h, self.handle, *[out[k].ctypes.data for k in
+                                                                ("key", "perm", "level", "prefix", "first", "count",
+                                                                 "skip", "mass", "com", "xtree")]))
+        out.update(info)
+        return out
+
+    def pm_export(self, pm_n: int) -> np.ndarray:
+        phi = np.zeros(pm_n ** 3, np.float32)
+        _check(_lib.tpm_pm_export(self.ctx._h, self.handle, phi.ctypes.data, phi.size))
+        return phi.reshape(pm_n, pm_n, pm_n)
+
+
+def launch_counts():
+    """(own kernel launches, CUB primitive calls) since the library was loaded."""
+    k, c = C.c_uint64(), C.c_uint64()
+    _check(_lib.tpm_launch_counts(C.byref(k), C.byref(c)))
+    return k.value, c.value
+
+
+def version() -> int:
+    return int(_lib.tpm_version())

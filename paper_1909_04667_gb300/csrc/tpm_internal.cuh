@@ -1,0 +1,160 @@
+// Internal declarations shared by the libtreepm translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "treepm.h"
+
+namespace tpm {
+
+constexpr int kMaxLevel = 21;  // 21 bits per axis, 63-bit keys
+
+// ------------------------------------------------------------------ errors
+void set_error(const char *fmt, ...);
+void clear_error();
+
+#define TPM_CUDA(call)                                                                                   \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess) {                                                                         \
+            ::tpm::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+            return TPM_ECUDA;                                                                            \
+        }                                                                                                \
+    } while (0)
+
+#define TPM_CHECK(expr)            \
+    do {                           \
+        int s_ = (expr);           \
+        if (s_ != TPM_OK)          \
+            return s_;             \
+    } while (0)
+
+// ------------------------------------------------------------------ counters
+// Kernels of this library launched since load (own kernels; CUB primitive
+// invocations are counted separately, one per call).
+void count_launch(int k = 1);
+void count_cub_call(int k = 1);
+
+// ------------------------------------------------------------------ memory
+// Device memory drawn from the context's stream-ordered pool and counted
+// against its HBM budget.
+struct Ctx;
+
+struct DevAlloc {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+int ctx_alloc(Ctx *c, void **p, size_t bytes, cudaStream_t st);
+void ctx_free(Ctx *c, void *p, size_t bytes, cudaStream_t st);
+
+// A set of allocations released together (a system, or one call's scratch).
+struct AllocSet {
+    Ctx *ctx = nullptr;
+    std::vector<DevAlloc> list;
+    template <class T>
+    int get(T **p, size_t count, cudaStream_t st) {
+        size_t b = count * sizeof(T);
+        if (b == 0)
+            b = 16;
+        void *q = nullptr;
+        int s = ctx_alloc(ctx, &q, b, st);
+        if (s != TPM_OK)
+            return s;
+        list.push_back({q, b});
+        *p = static_cast<T *>(q);
+        return TPM_OK;
+    }
+    void release(cudaStream_t st) {
+        for (auto &a : list)
+            ctx_free(ctx, a.p, a.bytes, st);
+        list.clear();
+    }
+    size_t bytes() const {
+        size_t t = 0;
+        for (auto &a : list)
+            t += a.bytes;
+        return t;
+    }
+};
+
+// ------------------------------------------------------------------ system
+struct System {
+    uint64_t id = 0;
+    int64_t n = 0, nnodes = 0;
+    tpm_build_params bp{};
+    double x0[3] = {0, 0, 0}, L0 = 1.0;
+    int maxlevel = 0;
+    AllocSet mem;
+
+    // particles
+    double *pos = nullptr;   // n x 3 FP64 positions the tree uses (shifted / wrapped), original order
+    float *mass = nullptr;   // n, original order
+    uint64_t *key = nullptr; // n, sorted
+    uint32_t *perm = nullptr;  // sorted position -> original index
+    uint32_t *rank = nullptr;  // original index -> sorted position
+    float4 *spart = nullptr;   // n, sorted: (x - leaf centre) FP32, mass
+
+    // nodes, depth-first pre-order
+    float4 *ncen = nullptr;  // geometric centre relative to x0 (exact in FP32), side L
+    float4 *ncom = nullptr;  // centre of mass minus geometric centre (FP32), mass (FP32)
+    int4 *nlink = nullptr;   // skip, first particle, count, leaf flag
+    uint8_t *nlevel = nullptr;
+    uint64_t *nprefix = nullptr;
+    double *nmass = nullptr;  // FP64
+    double *ncomd = nullptr;  // FP64 centre of mass, n x 3
+
+    // long-range mesh
+    AllocSet pm_mem;
+    float *phi = nullptr;
+    int pm_n = 0;
+    double pm_rs = 0.0;
+    double pm_G = 0.0;
+};
+
+struct Ctx {
+    int device = 0;
+    int num_sms = 0;
+    size_t budget = 0;
+    size_t used = 0;
+    cudaMemPool_t pool = nullptr;
+    std::mutex mu;
+    std::unordered_map<uint64_t, System *> systems;
+    uint64_t next_id = 1;
+    // cached cuFFT plans (one pair per mesh size)
+    std::unordered_map<int, std::pair<cufftHandle, cufftHandle>> fft_plans;
+    std::unordered_map<int, size_t> fft_work_bytes;
+};
+
+// ------------------------------------------------------------------ stages
+// Tree build (keys, sort, levels, multipoles, pre-order tables): fills s.
+int build_tree_device(Ctx *c, System *s, const double *pos_in, const float *mass_in, cudaStream_t st);
+
+// Long-range mesh potential into s->phi.
+int pm_solve_device(Ctx *c, System *s, const tpm_force_params *p, cudaStream_t st);
+
+struct WalkRequest {
+    const uint32_t *sorted_idx;  // n_act sorted positions of the active particles, ascending
+    const uint32_t *slot;        // n_act output slots
+    const float *a_old;          // per slot (nullable)
+    int64_t n_act;
+    float *acc;                  // slot-major x 3
+    float *pot;                  // nullable
+    uint32_t *nint;              // nullable
+    int accumulate;              // 1: add to acc / pot instead of overwriting
+};
+
+int walk_device(Ctx *c, const System *s, const tpm_force_params *p, const WalkRequest &r, cudaStream_t st);
+
+// Adds the CIC-interpolated mesh force and potential to acc / pot.
+int pm_interp_device(Ctx *c, const System *s, const WalkRequest &r, cudaStream_t st);
+
+}  // namespace tpm

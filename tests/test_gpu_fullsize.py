@@ -1,0 +1,110 @@
+"""Full-size checks in the launch configuration bench.py times: the GPU
+computes every particle; the oracle recomputes a seeded sample one by one.
+
+Hernquist N = 2^20: geometric first force (theta = 0.5), then the relative
+criterion (alpha = 0.0025) against the previous |a|, leaf bucket 8.  The
+periodic 128^3 Zel'dovich box: PM 256^3, a_s = 1.25, a_cut = 4.5.
+"""
+import numpy as np
+import pytest
+
+import bench
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b, axis=1) / np.linalg.norm(b, axis=1)
+
+
+@pytest.fixture(scope="module")
+def tpm():
+    import paper_1909_04667_gb300 as m
+
+    return m
+
+
+def test_hernquist_full_size(oracle_mod, tpm):
+    import torch
+
+    dev = torch.device("cuda", 0)
+    cfg = bench.HERNQUIST
+    pos, mass = bench.hernquist_inputs()
+    n = len(pos)
+    shift = bench.root_shift(0, 2)
+    ctx = tpm.Context(0)
+    s = ctx.build_tree(torch.from_numpy(pos).to(dev), torch.from_numpy(mass).to(dev),
+                       tpm.BuildParams(G=cfg["G"], h=cfg["h"], shift=shift, leaf_bucket=cfg["bucket"]))
+    a_bh, _, n_bh = s.compute_forces(fp=tpm.ForceParams(crit=tpm.CRIT_BH, theta=cfg["theta"]))
+    a_old = torch.linalg.vector_norm(a_bh, dim=1).contiguous()
+    a_rel, _, n_rel = s.compute_forces(a_old=a_old, fp=tpm.ForceParams(crit=tpm.CRIT_RELATIVE, alpha=cfg["alpha"]))
+    a_bh, n_bh = a_bh.cpu().numpy().astype(np.float64), n_bh.cpu().numpy()
+    a_rel, n_rel = a_rel.cpu().numpy().astype(np.float64), n_rel.cpu().numpy()
+    s.release()
+    ctx.close()
+    tg = W.random_targets(n, 1024, 99)
+    tree = oracle_mod.Tree(pos, mass, bucket=cfg["bucket"], shift=shift)
+    o_bh, _, on_bh = tree.walk(tg, cfg["G"], cfg["h"], theta=cfg["theta"])
+    # the geometric pass: same decisions, FP32 vs FP64 arithmetic
+    e = rel(a_bh[tg], o_bh)
+    same = n_bh[tg] == on_bh
+    assert same.mean() >= 0.995 and np.percentile(e[same], 99) < 2e-5
+    # the relative pass, |a_old| from each side's own first pass
+    aold_o = np.linalg.norm(o_bh, axis=1).astype(np.float32)
+    o_rel, _, on_rel = tree.walk(tg, cfg["G"], cfg["h"], crit="rel", alpha=cfg["alpha"], a_old=aold_o)
+    e = rel(a_rel[tg], o_rel)
+    same = n_rel[tg] == on_rel
+    assert same.mean() >= 0.99 and np.percentile(e[same], 99) < 2e-5
+    # accuracy against the exact softened direct sum: the GPU matches the
+    # method's own floor (the oracle walk's error)
+    ad, _ = oracle_mod.direct(pos, mass, tg, cfg["G"], cfg["h"])
+    gpu_p99 = np.percentile(rel(a_rel[tg], ad), 99)
+    floor_p99 = np.percentile(rel(o_rel, ad), 99)
+    assert gpu_p99 <= 5e-3 and gpu_p99 <= 1.05 * floor_p99 + 1e-5
+
+
+def test_zeldovich_full_size(oracle_mod, tpm):
+    import torch
+
+    dev = torch.device("cuda", 0)
+    cfg = bench.ZELDOVICH
+    pos, mass = bench.zeldovich_inputs()
+    n = len(pos)
+    h = bench.zeldovich_h()
+    shift = bench.root_shift(0, 3)
+    common = dict(treepm=True, pm_n=cfg["pm_n"], asmth=cfg["asmth"], rcut=cfg["rcut"])
+    fp_bh = tpm.ForceParams(crit=tpm.CRIT_BH, theta=cfg["theta"], **common)
+    fp_rel = tpm.ForceParams(crit=tpm.CRIT_RELATIVE, alpha=cfg["alpha"], **common)
+    ctx = tpm.Context(0)
+    s = ctx.build_tree(torch.from_numpy(pos).to(dev), torch.from_numpy(mass).to(dev),
+                       tpm.BuildParams(G=cfg["G"], h=h, periodic=True, box=1.0, shift=shift,
+                                       leaf_bucket=cfg["bucket"]))
+    s.pm_long_range(fp_bh)
+    a_bh, _, _ = s.compute_forces(fp=fp_bh)
+    a_old = torch.linalg.vector_norm(a_bh, dim=1).contiguous()
+    a_rel, _, n_rel = s.compute_forces(a_old=a_old, fp=fp_rel)
+    a_rel, n_rel = a_rel.cpu().numpy().astype(np.float64), n_rel.cpu().numpy()
+    xtree = s.tree_export()["xtree"]
+    s.release()
+    ctx.close()
+    tg = W.random_targets(n, 256, 98)
+    rs = cfg["asmth"] / cfg["pm_n"]
+    tree = oracle_mod.Tree(pos, mass, bucket=cfg["bucket"], periodic=True, box=1.0, shift=shift)
+    phi = oracle_mod.pm_potential(xtree, mass, 1.0, cfg["pm_n"], rs)
+    a_l, _ = oracle_mod.pm_interpolate(phi, xtree[tg], 1.0)
+    o_bh, _, _ = tree.walk(tg, cfg["G"], h, theta=cfg["theta"], treepm=True, rs=rs, rcut=cfg["rcut"] * rs)
+    aold_o = np.linalg.norm(o_bh + a_l, axis=1).astype(np.float32)
+    o_s, _, on_rel = tree.walk(tg, cfg["G"], h, crit="rel", alpha=cfg["alpha"], a_old=aold_o, treepm=True, rs=rs,
+                               rcut=cfg["rcut"] * rs)
+    o_rel = o_s + a_l
+    e = rel(a_rel[tg], o_rel)
+    same = n_rel[tg] == on_rel
+    assert same.mean() >= 0.98 and np.percentile(e[same], 99) < 1e-4
+    # error against the exact periodic (Ewald) force: GPU at the method's floor
+    ae, _ = oracle_mod.ewald(pos, mass, tg, cfg["G"], 1.0)
+    gpu = rel(a_rel[tg], ae)
+    floor = rel(o_rel, ae)
+    print("periodic TreePM vs Ewald: GPU p50 %.3g p99 %.3g; oracle p50 %.3g p99 %.3g" % (
+        np.median(gpu), np.percentile(gpu, 99), np.median(floor), np.percentile(floor, 99)))
+    assert np.percentile(gpu, 99) <= 1.05 * np.percentile(floor, 99) + 1e-4

@@ -1,0 +1,274 @@
+"""GPU-vs-oracle parity through the C ABI (libtreepm via its thin binding).
+
+Tolerances:
+* tree structure (keys, permutation, node table) and FP64 node masses and
+  centres of mass: bit-exact -- both sides sum in the same fixed order with
+  correctly rounded FP64 operations;
+* forces: the GPU walk makes the same per-particle decisions as the oracle
+  walk but evaluates pairs in FP32 with FP32 accumulation.  Each pair term
+  carries a relative rounding error of a few 2^-24 ~ 1e-7 and a force sums
+  10^2..10^4 terms that partly cancel, so |da|/|a| stays near 1e-6; we
+  require p99 <= 2e-5 and max <= 2e-4 where the interaction sets agree.  An
+  opening decision whose margin is below FP32 resolution can flip (a node
+  accepted instead of opened): at most 0.5% of particles may differ in their
+  interaction count, and those stay within the method's own error (5e-3).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+P99_TOL = 2e-5
+MAX_TOL = 2e-4
+
+
+@pytest.fixture(scope="module")
+def tpm():
+    import paper_1909_04667_gb300 as m
+
+    return m
+
+
+@pytest.fixture(scope="module")
+def torch_dev():
+    import torch
+
+    assert torch.cuda.is_available()
+    return torch.device("cuda", 0)
+
+
+@pytest.fixture(scope="module")
+def ctx(tpm):
+    c = tpm.Context(0)
+    yield c
+    c.close()
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b, axis=1) / np.maximum(np.linalg.norm(b, axis=1), 1e-300)
+
+
+def to_dev(x, dev):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+
+
+def compare_forces(acc, ref, nint, nref, p99=P99_TOL, mx=MAX_TOL, flip_frac=0.005):
+    e = rel(acc, ref)
+    same = nint == nref
+    assert np.mean(~same) <= flip_frac, "interaction counts differ for %d particles" % np.sum(~same)
+    assert np.percentile(e[same], 99) <= p99, "p99 %.3g" % np.percentile(e[same], 99)
+    assert e[same].max() <= mx, "max %.3g" % e[same].max()
+    if (~same).any():
+        assert e[~same].max() <= 5e-3
+    return e
+
+
+def clustered(n, seed, dup=0):
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(-1, 1, (5, 3))
+    pos = c[rng.integers(0, 5, n)] + 0.03 * rng.standard_normal((n, 3)) ** 3
+    if dup:
+        pos[:dup] = pos[0]
+    return pos, np.full(n, 1.0 / n, np.float32)
+
+
+TREE_CASES = [
+    ("plummer8192_B1", lambda: W.plummer(8192, 1001), 1, False),
+    ("plummer8192_B8", lambda: W.plummer(8192, 1001), 8, False),
+    ("hernquist20000_B8", lambda: W.hernquist(20000, 5), 8, False),
+    ("clustered_dups_B4", lambda: clustered(3001, 7, dup=40), 4, False),
+    ("ragged33_B1", lambda: W.plummer(33, 9), 1, False),
+    ("single", lambda: W.plummer(1, 9), 1, False),
+    ("pair", lambda: W.plummer(2, 9), 1, False),
+    ("zeldovich32_B4", lambda: W.zeldovich(32, 3), 4, True),
+]
+
+
+@pytest.mark.parametrize("name,make,bucket,periodic", TREE_CASES, ids=[c[0] for c in TREE_CASES])
+def test_tree_bit_exact(oracle_mod, tpm, ctx, torch_dev, name, make, bucket, periodic):
+    pos, mass = make()
+    shift = tuple(W.root_shift(31))
+    bp = tpm.BuildParams(G=1.0, h=0.01, periodic=periodic, box=1.0, shift=shift, leaf_bucket=bucket)
+    s = ctx.build_tree(to_dev(pos, torch_dev), to_dev(mass, torch_dev), bp)
+    ex = s.tree_export()
+    s.release()
+    ref = oracle_mod.Tree(pos, mass, bucket=bucket, periodic=periodic, box=1.0, shift=shift)
+    rx = ref.export()
+    assert ex["n_nodes"] == ref.nnodes
+    np.testing.assert_array_equal(ex["x0"], ref.x0)
+    assert ex["L0"] == ref.L0
+    for k in ("key", "perm", "level", "prefix", "first", "count", "skip", "mass", "com", "xtree"):
+        np.testing.assert_array_equal(ex[k], rx[k], err_msg=k)
+
+
+def test_tree_host_inputs_same_as_device(tpm, ctx, torch_dev):
+    pos, mass = W.hernquist(5000, 12)
+    bp = tpm.BuildParams(G=1.0, h=0.005, shift=tuple(W.root_shift(2)), leaf_bucket=8)
+    a = ctx.build_tree(pos, mass, bp).tree_export()
+    b = ctx.build_tree(to_dev(pos, torch_dev), to_dev(mass, torch_dev), bp).tree_export()
+    for k in ("key", "perm", "prefix", "skip", "mass", "com"):
+        np.testing.assert_array_equal(a[k], b[k])
+
+
+@pytest.mark.parametrize("bucket", [1, 8, 16])
+def test_walk_bh_plummer(oracle_mod, tpm, ctx, torch_dev, bucket):
+    n = 8192
+    pos, mass = W.plummer(n, 1001)
+    shift = tuple(W.root_shift(1))
+    s = ctx.build_tree(to_dev(pos, torch_dev), to_dev(mass, torch_dev),
+                       tpm.BuildParams(G=1.0, h=0.01, shift=shift, leaf_bucket=bucket))
+    acc, pot, nint = s.compute_forces(fp=tpm.ForceParams(crit=tpm.CRIT_BH, theta=0.7))
+    acc, pot, nint = acc.cpu().numpy(), pot.cpu().numpy(), nint.cpu().numpy()
+    s.release()
+    tree = oracle_mod.Tree(pos, mass, bucket=bucket, shift=shift)
+    a_o, p_o, n_o = tree.walk(np.arange(n), 1.0, 0.01, theta=0.7)
+    compare_forces(acc.astype(np.float64), a_o, nint, n_o)
+    np.testing.assert_allclose(pot, p_o, rtol=2e-5)
+
+
+def test_walk_relative_hernquist(oracle_mod, tpm, ctx, torch_dev):
+    n = 1 << 16
+    pos, mass = W.hernquist(n, 1002)
+    shift = tuple(W.root_shift(2))
+    tree = oracle_mod.Tree(pos, mass, bucket=8, shift=shift)
+    a_bh, _, _ = tree.walk(np.arange(n), 1.0, 0.005, theta=0.5)
+    a_old = np.linalg.norm(a_bh, axis=1).astype(np.float32)
+    a_o, p_o, n_o = tree.walk(np.arange(n), 1.0, 0.005, crit="rel", alpha=0.0025, a_old=a_old)
+    s = ctx.build_tree(to_dev(pos, torch_dev), to_dev(mass, torch_dev),
+                       tpm.BuildParams(G=1.0, h=0.005, shift=shift, leaf_bucket=8))
+    acc, pot, nint = s.compute_forces(a_old=to_dev(a_old, torch_dev),
+                                      fp=tpm.ForceParams(crit=tpm.CRIT_RELATIVE, alpha=0.0025))
+    s.release()
+    compare_forces(acc.cpu().numpy().astype(np.float64), a_o, nint.cpu().numpy(), n_o)
+
+
+def test_active_subset_in_caller_order(oracle_mod, tpm, ctx, torch_dev):
+    n = 10000
+    pos, mass = W.plummer(n, 44)
+    shift = tuple(W.root_shift(4))
+    rng = np.random.default_rng(1)
+    ids = rng.choice(n, 1237, replace=False).astype(np.uint32)  # unsorted, ragged count
+    s = ctx.build_tree(to_dev(pos, torch_dev), to_dev(mass, torch_dev),
+                       tpm.BuildParams(G=2.0, h=0.02, shift=shift, leaf_bucket=4))
+    acc, pot, nint = s.compute_forces(active_ids=to_dev(ids, torch_dev), fp=tpm.ForceParams(theta=0.6))
+    tree = oracle_mod.Tree(pos, mass, bucket=4, shift=shift)
+    a_o, p_o, n_o = tree.walk(ids, 2.0, 0.02, theta=0.6)
+    compare_forces(acc.cpu().numpy().astype(np.float64), a_o, nint.cpu().numpy(), n_o)
+    # the same through host buffers (numpy in, numpy out)
+    acc_h = np.zeros((len(ids), 3), np.float32)
+    pot_h = np.zeros(len(ids), np.float32)
+    nint_h = np.zeros(len(ids), np.uint32)
+    s.compute_forces(active_ids=ids, fp=tpm.ForceParams(theta=0.6), acc=acc_h, pot=pot_h, n_int=nint_h)
+    np.testing.assert_array_equal(acc_h, acc.cpu().numpy())
+    np.testing.assert_array_equal(nint_h, nint.cpu().numpy().astype(np.uint32))
+    s.release()
+
+
+def test_walk_deterministic(tpm, ctx, torch_dev):
+    pos, mass = W.hernquist(30000, 3)
+    bp = tpm.BuildParams(G=1.0, h=0.005, shift=tuple(W.root_shift(3)), leaf_bucket=8)
+    outs = []
+    for _ in range(2):
+        s = ctx.build_tree(to_dev(pos, torch_dev), to_dev(mass, torch_dev), bp)
+        a, p, k = s.compute_forces(fp=tpm.ForceParams(theta=0.5))
+        outs.append((a.cpu().numpy(), p.cpu().numpy(), k.cpu().numpy()))
+        s.release()
+    for x, y in zip(outs[0], outs[1]):
+        np.testing.assert_array_equal(x, y)
+
+
+def test_theta_zero_is_direct_sum(oracle_mod, tpm, ctx, torch_dev):
+    n = 3000
+    pos, mass = W.plummer(n, 8)
+    s = ctx.build_tree(to_dev(pos, torch_dev), to_dev(mass, torch_dev),
+                       tpm.BuildParams(G=1.0, h=0.01, shift=(0.3, 0.6, 0.1), leaf_bucket=8))
+    acc, pot, nint = s.compute_forces(fp=tpm.ForceParams(theta=1e-9))
+    s.release()
+    assert np.all(nint.cpu().numpy() == n - 1)
+    ad, pd = oracle_mod.direct(pos, mass, np.arange(n), 1.0, 0.01)
+    e = rel(acc.cpu().numpy().astype(np.float64), ad)
+    assert np.percentile(e, 99) < P99_TOL and e.max() < MAX_TOL
+
+
+def test_edge_cases(tpm, ctx, torch_dev):
+    # one particle: no interaction at all
+    s = ctx.build_tree(np.array([[0.5, 0.5, 0.5]]), np.array([1.0], np.float32), tpm.BuildParams())
+    a, p, k = s.compute_forces(fp=tpm.ForceParams())
+    assert np.all(a.cpu().numpy() == 0) and k.cpu().numpy()[0] == 0
+    # an empty active set is a no-op
+    s.compute_forces(active_ids=np.zeros(0, np.uint32), fp=tpm.ForceParams())
+    s.release()
+    # coincident particles share one level-21 leaf and feel no force from each other
+    pos = np.zeros((6, 3))
+    pos[3:] = [[1.0, 0, 0], [0, 1.0, 0], [0, 0, 1.0]]
+    s = ctx.build_tree(pos, np.full(6, 1 / 6, np.float32), tpm.BuildParams(leaf_bucket=1))
+    a, p, k = s.compute_forces(fp=tpm.ForceParams(theta=1e-9))
+    assert np.all(np.isfinite(a.cpu().numpy())) and list(k.cpu().numpy()[:3]) == [5, 5, 5]
+    s.release()
+
+
+def test_errors(tpm, ctx):
+    E = tpm.TreePMError
+    pos, mass = W.plummer(100, 1)
+    s = ctx.build_tree(pos, mass, tpm.BuildParams())
+    with pytest.raises(E, match="TPM_EINVAL"):  # relative criterion without a_old
+        s.compute_forces(fp=tpm.ForceParams(crit=tpm.CRIT_RELATIVE))
+    with pytest.raises(E, match="TPM_EINVAL"):  # out-of-range id (host)
+        s.compute_forces(active_ids=np.array([5, 100], np.uint32), fp=tpm.ForceParams())
+    with pytest.raises(E, match="TPM_ENAN"):
+        s.compute_forces(active_ids=np.array([1], np.uint32), a_old=np.array([np.nan], np.float32),
+                         fp=tpm.ForceParams(crit=tpm.CRIT_RELATIVE))
+    with pytest.raises(E, match="TPM_EINVAL"):  # treepm on an open system
+        s.compute_forces(fp=tpm.ForceParams(treepm=True))
+    bad = pos.copy()
+    bad[3, 1] = np.inf
+    with pytest.raises(E, match="TPM_ENAN"):
+        ctx.build_tree(bad, mass, tpm.BuildParams())
+    with pytest.raises(E, match="TPM_EINVAL"):  # periodic positions outside [0, box)
+        ctx.build_tree(pos, mass, tpm.BuildParams(periodic=True, box=1.0))
+    s.release()
+    with pytest.raises(E, match="TPM_ENOSYS_HANDLE"):
+        s.handle = 12345
+        s.release()
+
+
+def test_budget_admission_has_no_side_effects(tpm):
+    small = tpm.Context(0, budget_bytes=8 << 20)
+    pos, mass = W.hernquist(200000, 2)
+    used0, _ = small.memory()
+    with pytest.raises(tpm.TreePMError, match="TPM_EBUDGET"):
+        small.build_tree(pos, mass, tpm.BuildParams())
+    assert small.memory()[0] == used0
+    ok = small.build_tree(*W.plummer(1000, 2), tpm.BuildParams())
+    ok.release()
+    small.close()
+
+
+def test_periodic_treepm_matches_oracle(oracle_mod, tpm, ctx, torch_dev):
+    ng_part, ng = 32, 64
+    pos, mass = W.zeldovich(ng_part, 1003)
+    n = len(pos)
+    shift = tuple(W.root_shift(3))
+    h = (1.0 / ng_part) / 40
+    fp = tpm.ForceParams(crit=tpm.CRIT_BH, theta=0.5, treepm=True, pm_n=ng, asmth=1.25, rcut=4.5)
+    s = ctx.build_tree(to_dev(pos, torch_dev), to_dev(mass, torch_dev),
+                       tpm.BuildParams(G=1.0, h=h, periodic=True, box=1.0, shift=shift, leaf_bucket=8))
+    s.pm_long_range(fp)
+    phi_gpu = s.pm_export(ng).astype(np.float64)
+    tg = np.arange(0, n, 7).astype(np.uint32)
+    acc, pot, nint = s.compute_forces(active_ids=to_dev(tg, torch_dev), fp=fp)
+    xtree = s.tree_export()["xtree"]
+    s.release()
+    # mesh potential (computed in the shifted frame the tree uses)
+    rs = 1.25 / ng
+    phi_o = oracle_mod.pm_potential(xtree, mass, 1.0, ng, rs)
+    assert np.abs(phi_gpu - phi_o).max() < 1e-5 * np.abs(phi_o).max()
+    # short-range walk + long-range mesh, element by element
+    tree = oracle_mod.Tree(pos, mass, bucket=8, periodic=True, box=1.0, shift=shift)
+    a_s, p_s, n_o = tree.walk(tg, 1.0, h, theta=0.5, treepm=True, rs=rs, rcut=4.5 * rs)
+    a_l, p_l = oracle_mod.pm_interpolate(phi_o, xtree[tg], 1.0)
+    compare_forces(acc.cpu().numpy().astype(np.float64), a_s + a_l, nint.cpu().numpy(), n_o, p99=1e-4, mx=1e-3)
