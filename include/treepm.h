@@ -171,6 +171,34 @@ int tpm_pm_long_range(tpm_ctx *ctx, tpm_sys s, const tpm_force_params *p, void *
 int tpm_compute_forces(tpm_ctx *ctx, tpm_sys s, const uint32_t *active_ids, int64_t n_active, const float *a_old,
                        const tpm_force_params *p, float *acc, float *pot, uint32_t *n_int, void *stream);
 
+/*
+ * tpm_compute_forces without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot let a library
+ * allocate device memory inside their time-step loop -- programs that have
+ * already given the device memory to their own allocator, or that must not
+ * pay for (or risk failing) an allocation at every step.  The per-call
+ * scratch of tpm_compute_forces (the active set sorted into key order and
+ * the sort's temporary storage) lives instead in one fixed-size device array
+ * inside the library, about 6 MiB, which every GPU that loads the library
+ * holds until the process exits.
+ *   Same arguments and results as tpm_compute_forces, except:
+ *   - active_ids is required and n_active must lie in [1, TPM_NOALLOC_MAX_ACTIVE];
+ *     larger sets are rejected with TPM_EINVAL;
+ *   - every array (active_ids, a_old, acc, pot, n_int) must be device memory
+ *     (host arrays would need staging buffers): TPM_EINVAL otherwise;
+ *   - the call is stream-ordered and never synchronises.
+ * The first call on a device looks up the array's device address (it loads
+ * the library's device code on that device), so make that first call before
+ * any stream capture.  All calls share the one array, which keeps the last
+ * call's contents: two calls whose work overlaps on the GPU (different
+ * streams, or different contexts on one device) race on it and must be
+ * ordered by the caller.
+ */
+#define TPM_NOALLOC_MAX_ACTIVE (1 << 18)
+int tpm_compute_forces_noalloc(tpm_ctx *ctx, tpm_sys s, const uint32_t *active_ids, int64_t n_active,
+                               const float *a_old, const tpm_force_params *p, float *acc, float *pot,
+                               uint32_t *n_int, void *stream);
+
 /* Frees a resident system.  Waits for its outstanding work. */
 int tpm_release(tpm_ctx *ctx, tpm_sys s);
 

@@ -26,6 +26,7 @@ __all__ = ["Context", "System", "BuildParams", "ForceParams", "TreePMError", "li
 
 CRIT_BH = 0
 CRIT_RELATIVE = 1
+NOALLOC_MAX_ACTIVE = 1 << 18  # TPM_NOALLOC_MAX_ACTIVE
 
 _STATUS = {0: "TPM_OK", -1: "TPM_EINVAL", -2: "TPM_EBUDGET", -3: "TPM_ENOSYS_HANDLE", -4: "TPM_ECUDA",
            -5: "TPM_ETIMEDOUT", -6: "TPM_ENAN"}
@@ -75,6 +76,8 @@ def _load():
         "tpm_tree_export": (i32, [vp, C.c_uint64] + [vp] * 10),
         "tpm_pm_export": (i32, [vp, C.c_uint64, vp, i64]),
         "tpm_launch_counts": (i32, [C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
+        "tpm_compute_forces_noalloc": (i32, [vp, C.c_uint64, vp, i64, vp, C.POINTER(_ForceParams), vp, vp, vp,
+                                             vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -233,6 +236,20 @@ class System:
         cp = fp._c()
         _check(_lib.tpm_compute_forces(self.ctx._h, self.handle, _ptr(active_ids), n_act, _ptr(a_old), C.byref(cp),
                                        _ptr(acc), _ptr(pot), _ptr(n_int), _stream(stream, self.ctx.device)))
+        return acc, pot, n_int
+
+    def compute_forces_noalloc(self, active_ids, acc, a_old=None, fp: ForceParams = None, pot=None, n_int=None,
+                               stream=None):
+        """``tpm_compute_forces_noalloc``: the same evaluation without any
+        device allocation, for callers that cannot let the library allocate.
+        Every array must already live on the device (the caller allocates
+        acc, pot and n_int); at most ``NOALLOC_MAX_ACTIVE`` active particles."""
+        fp = fp or ForceParams()
+        n_act = int(active_ids.shape[0])
+        cp = fp._c()
+        _check(_lib.tpm_compute_forces_noalloc(self.ctx._h, self.handle, _ptr(active_ids), n_act, _ptr(a_old),
+                                               C.byref(cp), _ptr(acc), _ptr(pot), _ptr(n_int),
+                                               _stream(stream, self.ctx.device)))
         return acc, pot, n_int
 
     def tree_info(self):

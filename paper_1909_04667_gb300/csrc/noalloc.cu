@@ -1,0 +1,180 @@
+// tpm_compute_forces_noalloc: force evaluation on an active subset that
+// allocates no device memory.
+//
+// tpm_compute_forces draws its per-call scratch (the active set sorted into
+// key order, and the sort's temporary storage) from the context's memory
+// pool.  Some callers cannot let a library allocate device memory in the
+// middle of their time-step loop: programs that have already handed the
+// device memory to their own allocator, or that must not pay for an
+// allocation (and the failure mode that comes with it) at every step.  This
+// entry point keeps that scratch in one file-scope device array instead, of
+// fixed size, which every GPU that loads the library holds until the process
+// exits.  The caller still passes the inputs and outputs, all in device
+// memory.
+#include <cub/cub.cuh>
+
+#include <mutex>
+
+#include "tpm_internal.cuh"
+
+namespace tpm {
+namespace {
+
+constexpr int64_t kMaxActive = TPM_NOALLOC_MAX_ACTIVE;
+constexpr size_t kIdsBytes = (size_t)kMaxActive * sizeof(uint32_t);
+constexpr size_t kFlagBytes = 256;
+constexpr size_t kSortTempBytes = size_t(2) << 20;  // CUB radix-sort temporary storage
+constexpr size_t kScratchBytes = 4 * kIdsBytes + kFlagBytes + kSortTempBytes;
+
+// The shared scratch: keys, values, sorted keys, sorted values, an error flag
+// and the sort's temporary storage.  Host code must not pass this symbol to a
+// kernel -- on the host it only names a stand-in; its device address comes
+// from cudaGetSymbolAddress (see scratch_on_device).
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_setup_mu;
+void *g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of g_scratch on `device` (which must be current).  Looked up
+// once per device; the first call on a device therefore calls
+// cudaGetSymbolAddress, which loads the library's device code there.
+int scratch_on_device(int device, unsigned char **out) {
+    if (device < 0 || device >= kMaxDevices) {
+        set_error("device %d out of range for the no-allocation scratch", device);
+        return TPM_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(g_setup_mu);
+    if (!g_scratch_ptr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+        if (e != cudaSuccess || !p) {
+            set_error("cudaGetSymbolAddress of the no-allocation scratch failed: %s", cudaGetErrorString(e));
+            return TPM_ECUDA;
+        }
+        g_scratch_ptr[device] = p;
+    }
+    *out = static_cast<unsigned char *>(g_scratch_ptr[device]);
+    return TPM_OK;
+}
+
+__global__ void k_noalloc_active_keys(const uint32_t *__restrict__ ids, int64_t n_act,
+                                      const uint32_t *__restrict__ rank, int64_t n, uint32_t *__restrict__ keys,
+                                      uint32_t *__restrict__ vals, int *__restrict__ bad) {
+    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= n_act)
+        return;
+    uint32_t id = ids[k];
+    if (id >= (uint64_t)n) {
+        atomicOr(bad, 1);
+        id = 0;
+    }
+    keys[k] = rank[id];
+    vals[k] = (uint32_t)k;
+}
+
+bool on_device(const void *p) {
+    if (!p)
+        return true;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+}  // namespace tpm
+
+using namespace tpm;
+
+extern "C" int tpm_compute_forces_noalloc(tpm_ctx *h, tpm_sys sid, const uint32_t *active_ids, int64_t n_active,
+                                          const float *a_old, const tpm_force_params *p, float *acc, float *pot,
+                                          uint32_t *n_int, void *stream) {
+    clear_error();
+    if (!h || !active_ids || !acc || !p) {
+        set_error("null argument (active_ids, acc and params are required)");
+        return TPM_EINVAL;
+    }
+    if (n_active < 1 || n_active > kMaxActive) {
+        set_error("n_active = %lld outside [1, %lld], the fixed size of the no-allocation scratch",
+                  (long long)n_active, (long long)kMaxActive);
+        return TPM_EINVAL;
+    }
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    System *s = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        auto it = c->systems.find(sid);
+        if (it != c->systems.end())
+            s = it->second;
+    }
+    if (!s) {
+        set_error("unknown system handle %llu", (unsigned long long)sid);
+        return TPM_ENOSYS_HANDLE;
+    }
+    if (p->crit != TPM_CRIT_BH && p->crit != TPM_CRIT_RELATIVE) {
+        set_error("crit must be TPM_CRIT_BH or TPM_CRIT_RELATIVE");
+        return TPM_EINVAL;
+    }
+    if (p->crit == TPM_CRIT_RELATIVE && !a_old) {
+        set_error("the relative criterion needs a_old");
+        return TPM_EINVAL;
+    }
+    if ((p->treepm != 0) != (s->bp.periodic != 0)) {
+        set_error("treepm forces need a periodic system and periodic systems need treepm");
+        return TPM_EINVAL;
+    }
+    if (p->treepm && (!s->phi || s->pm_n != p->pm_n)) {
+        set_error("no long-range mesh for these parameters: call tpm_pm_long_range first");
+        return TPM_EINVAL;
+    }
+    TPM_CUDA(cudaSetDevice(c->device));
+    if (!on_device(active_ids) || !on_device(a_old) || !on_device(acc) || !on_device(pot) || !on_device(n_int)) {
+        set_error("all arrays must be device memory: host arrays would need staging buffers");
+        return TPM_EINVAL;
+    }
+    unsigned char *base = nullptr;
+    TPM_CHECK(scratch_on_device(c->device, &base));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    uint32_t *keys = reinterpret_cast<uint32_t *>(base);
+    uint32_t *vals = reinterpret_cast<uint32_t *>(base + kIdsBytes);
+    uint32_t *skeys = reinterpret_cast<uint32_t *>(base + 2 * kIdsBytes);
+    uint32_t *svals = reinterpret_cast<uint32_t *>(base + 3 * kIdsBytes);
+    int *bad = reinterpret_cast<int *>(base + 4 * kIdsBytes);
+    void *sort_tmp = base + 4 * kIdsBytes + kFlagBytes;
+
+    int bits = 1;
+    while ((int64_t(1) << bits) < s->n)
+        bits++;
+    size_t need = 0;
+    TPM_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, need, keys, skeys, vals, svals, (int)n_active, 0, bits, st));
+    if (need > kSortTempBytes) {
+        set_error("sort needs %zu bytes of temporary storage, the no-allocation scratch has %zu", need,
+                  kSortTempBytes);
+        return TPM_EINVAL;
+    }
+    // the scratch keeps the previous call's contents: the error flag must start at zero
+    TPM_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
+    k_noalloc_active_keys<<<(unsigned)((n_active + 255) / 256), 256, 0, st>>>(active_ids, n_active, s->rank, s->n,
+                                                                             keys, vals, bad);
+    count_launch();
+    TPM_CUDA(cudaGetLastError());
+    TPM_CUDA(cub::DeviceRadixSort::SortPairs(sort_tmp, need, keys, skeys, vals, svals, (int)n_active, 0, bits, st));
+    count_cub_call();
+
+    WalkRequest r{};
+    r.sorted_idx = skeys;
+    r.slot = svals;
+    r.a_old = p->crit == TPM_CRIT_RELATIVE ? a_old : nullptr;
+    r.n_act = n_active;
+    r.acc = acc;
+    r.pot = pot;
+    r.nint = n_int;
+    if (p->treepm) {
+        TPM_CHECK(pm_interp_device(c, s, r, st));
+        r.accumulate = 1;
+    }
+    return walk_device(c, s, p, r, st);
+}
