@@ -199,6 +199,12 @@ int tpm_compute_forces_noalloc(tpm_ctx *ctx, tpm_sys s, const uint32_t *active_i
                                const float *a_old, const tpm_force_params *p, float *acc, float *pot,
                                uint32_t *n_int, void *stream);
 
+/* Waits for `stream` and reports errors that device work recorded for system
+ * s since the last check (then clears them): TPM_EINVAL if a device-side
+ * active id was out of range (its outputs hold particle 0's values), TPM_ECUDA
+ * if the walk's candidate stack overflowed; TPM_OK otherwise. */
+int tpm_sync_status(tpm_ctx *ctx, tpm_sys s, void *stream);
+
 /* Frees a resident system.  Waits for its outstanding work. */
 int tpm_release(tpm_ctx *ctx, tpm_sys s);
 

@@ -72,6 +72,7 @@ def _load():
         "tpm_pm_long_range": (i32, [vp, C.c_uint64, C.POINTER(_ForceParams), vp]),
         "tpm_compute_forces": (i32, [vp, C.c_uint64, vp, i64, vp, C.POINTER(_ForceParams), vp, vp, vp, vp]),
         "tpm_release": (i32, [vp, C.c_uint64]),
+        "tpm_sync_status": (i32, [vp, C.c_uint64, vp]),
         "tpm_tree_info": (i32, [vp, C.c_uint64, C.POINTER(i64), C.POINTER(i64), vp, vp]),
         "tpm_tree_export": (i32, [vp, C.c_uint64] + [vp] * 10),
         "tpm_pm_export": (i32, [vp, C.c_uint64, vp, i64]),
@@ -251,6 +252,11 @@ class System:
                                                C.byref(cp), _ptr(acc), _ptr(pot), _ptr(n_int),
                                                _stream(stream, self.ctx.device)))
         return acc, pot, n_int
+
+    def sync_status(self, stream=None):
+        """``tpm_sync_status``: wait for the stream and raise if device work
+        recorded an error for this system."""
+        _check(_lib.tpm_sync_status(self.ctx._h, self.handle, _stream(stream, self.ctx.device)))
 
     def tree_info(self):
         n, nn = C.c_int64(), C.c_int64()

@@ -8,8 +8,11 @@
 //   1. root cube and 21-bit integer cell coordinates -> 63-bit Morton keys
 //   2. stable radix sort of (key, particle index)
 //   3. level by level, every cell holding more than B particles is split into
-//      its non-empty octants (binary search of the sorted keys), children in
-//      ascending octant order
+//      its non-empty octants: eight threads per cell find the eight octant
+//      boundaries in the sorted keys at once, and one atomic per cell
+//      reserves its children (contiguous, in ascending octant order); the
+//      level ranges stay on the device, so no host round trip is needed
+//      between levels
 //   4. FP64 masses and mass-weighted positions summed bottom-up, children in
 //      ascending octant order and a leaf's particles in sorted order, with
 //      explicit round-to-nearest operations (no contraction), so the result
@@ -82,7 +85,9 @@ __global__ void k_prepare(const double *__restrict__ pin, const float *__restric
             atomicOr(bad, 4);
         mout[i] = m;
     }
-    // warp-level min / max, then one atomic per warp
+    // warp-level min / max, then one atomic per block
+    __shared__ long long red[2][3][32];
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int a = 0; a < 3; a++) {
         long long l = have ? lo[a] : LLONG_MAX, h = have ? hi[a] : LLONG_MIN;
@@ -91,9 +96,20 @@ __global__ void k_prepare(const double *__restrict__ pin, const float *__restric
             h = max(h, __shfl_xor_sync(0xffffffffu, h, o));
         }
         if ((threadIdx.x & 31) == 0) {
-            atomicMin(&bbox[a], l);
-            atomicMax(&bbox[3 + a], h);
+            red[0][a][w] = l;
+            red[1][a][w] = h;
         }
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        const int a = threadIdx.x;
+        long long l = LLONG_MAX, h = LLONG_MIN;
+        for (int i = 0; i < nw; i++) {
+            l = min(l, red[0][a][i]);
+            h = max(h, red[1][a][i]);
+        }
+        atomicMin(&bbox[a], l);
+        atomicMax(&bbox[3 + a], h);
     }
 }
 
@@ -118,13 +134,65 @@ __device__ __forceinline__ uint32_t compact3(uint64_t v) {
     return (uint32_t)v;
 }
 
+// Device-side bookkeeping of one build.
+struct BuildState {
+    long long bbox[6];
+    int bad;
+    int overflow;
+    unsigned total;  // nodes reserved so far
+    int maxlevel;
+    unsigned lstart[kMaxLevel + 2];
+    unsigned lcount[kMaxLevel + 2];
+    double x0[3];
+    double L0;
+    double scale;  // 2^21 / L0
+};
+
+__device__ double pow2_ceil_d(double x) {
+    int e;
+    const double f = frexp(x, &e);
+    return (f == 0.5) ? ldexp(1.0, e - 1) : ldexp(1.0, e);
+}
+
+// Root cube (one thread): periodic [0, box); open boundaries: the smallest
+// power of two L0 >= 1.25 x the largest extent, x0 = lo - shift (L0 - extent)
+// rounded down to the 2^-21 L0 grid.  Round-to-nearest operations only.
+__global__ void k_root(BuildState *__restrict__ st, int periodic, double box, double s0, double s1, double s2) {
+    if (threadIdx.x != 0)
+        return;
+    if (periodic) {
+        st->x0[0] = st->x0[1] = st->x0[2] = 0.0;
+        st->L0 = box;
+    } else {
+        double lo[3], hi[3], ext = 0.0;
+        for (int a = 0; a < 3; a++) {
+            lo[a] = from_ordered_bits(st->bbox[a]);
+            hi[a] = from_ordered_bits(st->bbox[3 + a]);
+            ext = fmax(ext, __dsub_rn(hi[a], lo[a]));
+        }
+        if (!(ext > 0.0))
+            ext = 1.0;
+        const double L0 = pow2_ceil_d(__dmul_rn(1.25, ext));
+        const double unit = ldexp(L0, -kMaxLevel);
+        const double sh[3] = {s0, s1, s2};
+        for (int a = 0; a < 3; a++) {
+            const double slack = __dsub_rn(L0, __dsub_rn(hi[a], lo[a]));
+            const double x0 = __dsub_rn(lo[a], __dmul_rn(sh[a], slack));
+            st->x0[a] = __dmul_rn(floor(__ddiv_rn(x0, unit)), unit);
+        }
+        st->L0 = L0;
+    }
+    st->scale = __ddiv_rn(ldexp(1.0, kMaxLevel), st->L0);
+}
+
 // K1: Morton keys of the 21-bit cell coordinates q = floor((x - x0) 2^21 / L0).
-__global__ void k_keys(const double *__restrict__ pos, int64_t n, double x0, double y0, double z0, double scale,
+__global__ void k_keys(const double *__restrict__ pos, int64_t n, const BuildState *__restrict__ st,
                        uint64_t *__restrict__ key, uint32_t *__restrict__ idx) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n)
         return;
-    const double o[3] = {x0, y0, z0};
+    const double o[3] = {st->x0[0], st->x0[1], st->x0[2]};
+    const double scale = st->scale;
     uint64_t k = 0;
 #pragma unroll
     for (int a = 0; a < 3; a++) {
@@ -165,72 +233,96 @@ struct LevelArrays {
     uint64_t *prefix;
 };
 
-// K3a: number of non-empty octants of each cell of one level that is split.
-__global__ void k_count_children(const uint64_t *__restrict__ key, LevelArrays b, int64_t ls, int64_t lc, int level,
-                                 int bucket, uint32_t *__restrict__ nch) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= lc)
+__global__ void k_level0(LevelArrays b, BuildState *__restrict__ st, int64_t n) {
+    if (threadIdx.x != 0)
         return;
-    int64_t node = ls + i;
-    uint32_t f = b.first[node], c = b.count[node];
-    if ((int)c <= bucket || level >= kMaxLevel) {
-        nch[i] = 0;
-        return;
-    }
-    int shift = 3 * (kMaxLevel - level - 1);
-    uint64_t base = b.prefix[node] << 3;
-    uint32_t lo = f, end = f + c, k = 0;
-    for (int o = 0; o < 8; o++) {
-        uint32_t hi = (o == 7) ? end : lower_bound_key(key, lo, end, (base | (uint64_t)(o + 1)) << shift);
-        k += hi > lo;
-        lo = hi;
-    }
-    nch[i] = k;
+    b.first[0] = 0;
+    b.count[0] = (uint32_t)n;
+    b.level[0] = 0;
+    b.prefix[0] = 0;
+    st->total = 1;
+    st->lstart[0] = 0;
+    st->lcount[0] = 1;
+    st->maxlevel = 0;
 }
 
-// K3b: writes the children of one level (ascending octant) and each cell's
-// child range.
-__global__ void k_emit_children(const uint64_t *__restrict__ key, LevelArrays b, int64_t ls, int64_t lc, int level,
-                                int bucket, const uint32_t *__restrict__ offs, int64_t next_start) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= lc)
-        return;
-    int64_t node = ls + i;
-    uint32_t f = b.first[node], c = b.count[node];
-    if ((int)c <= bucket || level >= kMaxLevel) {
-        b.child[node] = 0;
-        b.nchild[node] = 0;
-        return;
-    }
-    int shift = 3 * (kMaxLevel - level - 1);
-    uint64_t base = b.prefix[node] << 3;
-    int64_t out = next_start + offs[i];
-    b.child[node] = (uint32_t)out;
-    uint32_t lo = f, end = f + c, k = 0;
-    for (int o = 0; o < 8; o++) {
-        uint32_t hi = (o == 7) ? end : lower_bound_key(key, lo, end, (base | (uint64_t)(o + 1)) << shift);
-        if (hi > lo) {
-            int64_t ch = out + k;
+// K3: splits every cell of one level that holds more than B particles (and is
+// above the depth cap) into its non-empty octants.  Eight consecutive threads
+// serve one cell: thread o finds where octant o starts in the cell's key
+// range; the cell's first thread reserves the children with one atomic.
+__global__ void k_split_level(const uint64_t *__restrict__ key, LevelArrays b, BuildState *__restrict__ st, int level,
+                              int bucket, unsigned cap) {
+    const unsigned ls = st->lstart[level], lc = st->lcount[level];
+    const int lane = threadIdx.x & 31;
+    const unsigned gmask = 0xffu << (lane & 24);
+    const int o = lane & 7;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)lc * 8; t += stride) {
+        const unsigned node = ls + (unsigned)(t >> 3);
+        const uint32_t f = b.first[node], c = b.count[node];
+        const bool split = (int)c > bucket && level < kMaxLevel;
+        if (!split) {
+            if (o == 0) {
+                b.child[node] = 0;
+                b.nchild[node] = 0;
+            }
+            continue;
+        }
+        const int shift = 3 * (kMaxLevel - level - 1);
+        const uint64_t base = b.prefix[node] << 3;
+        const uint32_t lo = (o == 0) ? f : lower_bound_key(key, f, f + c, (base | (uint64_t)o) << shift);
+        uint32_t hi = __shfl_down_sync(gmask, lo, 1, 8);
+        if (o == 7)
+            hi = f + c;
+        const bool nonempty = hi > lo;
+        const unsigned bm = (__ballot_sync(gmask, nonempty) >> (lane & 24)) & 0xffu;
+        const unsigned nch = __popc(bm);
+        unsigned first_child = 0;
+        if (o == 0)
+            first_child = atomicAdd(&st->total, nch);
+        first_child = __shfl_sync(gmask, first_child, 0, 8);
+        if (first_child + nch > cap) {  // out of node space: the host rebuilds with more
+            if (o == 0) {
+                st->overflow = 1;
+                b.child[node] = 0;
+                b.nchild[node] = 0;
+            }
+            continue;
+        }
+        if (nonempty) {
+            const unsigned ch = first_child + __popc(bm & ((1u << o) - 1u));
             b.first[ch] = lo;
             b.count[ch] = hi - lo;
             b.level[ch] = (uint8_t)(level + 1);
             b.prefix[ch] = base | (uint64_t)o;
-            k++;
         }
-        lo = hi;
+        if (o == 0) {
+            b.child[node] = first_child;
+            b.nchild[node] = nch;
+        }
     }
-    b.nchild[node] = k;
+}
+
+// The children reserved while splitting level l form level l + 1.
+__global__ void k_level_bounds(BuildState *__restrict__ st, int level, unsigned cap) {
+    if (threadIdx.x != 0)
+        return;
+    const unsigned start = st->lstart[level] + st->lcount[level];
+    const unsigned total = min(st->total, cap);
+    st->lstart[level + 1] = start;
+    st->lcount[level + 1] = total > start ? total - start : 0u;
+    if (total > start)
+        st->maxlevel = level + 1;
 }
 
 // K4: FP64 monopoles of one level, children first (ascending octant), a
 // leaf's particles in sorted order; explicit round-to-nearest adds / muls.
-__global__ void k_multipole(LevelArrays b, int64_t ls, int64_t lc, const uint32_t *__restrict__ perm,
-                            const double *__restrict__ pos, const float *__restrict__ mass, double *__restrict__ M,
-                            double *__restrict__ S) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= lc)
-        return;
-    int64_t node = ls + i;
+__global__ void k_multipole(LevelArrays b, const BuildState *__restrict__ st, int level,
+                            const uint32_t *__restrict__ perm, const double *__restrict__ pos,
+                            const float *__restrict__ mass, double *__restrict__ M, double *__restrict__ S) {
+    const unsigned ls = st->lstart[level], lc = st->lcount[level];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < lc; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t node = ls + i;
     double m = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
     uint32_t nc = b.nchild[node];
     if (nc == 0) {
@@ -256,6 +348,7 @@ __global__ void k_multipole(LevelArrays b, int64_t ls, int64_t lc, const uint32_
     S[3 * node] = sx;
     S[3 * node + 1] = sy;
     S[3 * node + 2] = sz;
+    }
 }
 
 __global__ void k_preorder_keys(LevelArrays b, int64_t total, uint64_t *__restrict__ okey, uint32_t *__restrict__ oval) {
@@ -315,6 +408,28 @@ __global__ void k_finalize(LevelArrays b, const uint64_t *__restrict__ pkey, con
     o.comd[3 * p + 2] = cz;
 }
 
+// Breadth-first node records for the group walk (same values as the pre-order
+// tables; children of a node are contiguous in this order).
+__global__ void k_finalize_bfs(LevelArrays b, int64_t total, const double *__restrict__ M,
+                               const double *__restrict__ S, double x0, double y0, double z0, double L0,
+                               float4 *__restrict__ bcen, float4 *__restrict__ bcom, int4 *__restrict__ blink) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= total)
+        return;
+    const int lvl = b.level[i];
+    const uint64_t pre = b.prefix[i];
+    const double m = M[i];
+    const double cx = __ddiv_rn(S[3 * i], m), cy = __ddiv_rn(S[3 * i + 1], m), cz = __ddiv_rn(S[3 * i + 2], m);
+    const double half = ldexp(L0, -(lvl + 1));
+    const double rx = (double)(2 * (uint64_t)compact3(pre) + 1) * half;
+    const double ry = (double)(2 * (uint64_t)compact3(pre >> 1) + 1) * half;
+    const double rz = (double)(2 * (uint64_t)compact3(pre >> 2) + 1) * half;
+    bcen[i] = make_float4((float)rx, (float)ry, (float)rz, (float)(2.0 * half));
+    bcom[i] = make_float4((float)__dsub_rn(cx, __dadd_rn(x0, rx)), (float)__dsub_rn(cy, __dadd_rn(y0, ry)),
+                          (float)__dsub_rn(cz, __dadd_rn(z0, rz)), (float)m);
+    blink[i] = make_int4((int)b.child[i], (int)b.nchild[i], (int)b.first[i], (int)b.count[i]);
+}
+
 // Leaf particles relative to their leaf centre (FP64 difference -> FP32).
 __global__ void k_leaf_particles(const float4 *__restrict__ cen, const int4 *__restrict__ link, int64_t total,
                                  const uint32_t *__restrict__ perm, const double *__restrict__ pos,
@@ -333,12 +448,6 @@ __global__ void k_leaf_particles(const float4 *__restrict__ cen, const int4 *__r
         spart[s] = make_float4((float)__dsub_rn(pos[3 * j], ax), (float)__dsub_rn(pos[3 * j + 1], ay),
                                (float)__dsub_rn(pos[3 * j + 2], az), mass[j]);
     }
-}
-
-double pow2_ceil(double x) {
-    int e;
-    double f = std::frexp(x, &e);
-    return (f == 0.5) ? std::ldexp(1.0, e - 1) : std::ldexp(1.0, e);
 }
 
 }  // namespace
@@ -360,84 +469,46 @@ int build_tree_device(Ctx *c, System *s, const double *pos_in, const float *mass
     TPM_CHECK(s->mem.get(&s->perm, n, st));
     TPM_CHECK(s->mem.get(&s->rank, n, st));
     TPM_CHECK(s->mem.get(&s->spart, n, st));
+    TPM_CHECK(s->mem.get(&s->err, 1, st));
+    TPM_CUDA(cudaMemsetAsync(s->err, 0, sizeof(int), st));
 
-    // ---- prepare, bounding box
-    long long *bbox;
-    int *bad;
-    TPM_CHECK(tmp.get(&bbox, 6, st));
-    TPM_CHECK(tmp.get(&bad, 1, st));
-    long long init[6] = {LLONG_MAX, LLONG_MAX, LLONG_MAX, LLONG_MIN, LLONG_MIN, LLONG_MIN};
-    long long *h_bbox;
-    TPM_CUDA(cudaMallocHost(&h_bbox, 8 * sizeof(long long)));
+    BuildState *dst;
+    TPM_CHECK(tmp.get(&dst, 1, st));
+    BuildState *hst;
+    TPM_CUDA(cudaMallocHost(&hst, sizeof(BuildState)));
     struct HostGuard {
         void *p;
         ~HostGuard() { cudaFreeHost(p); }
-    } hg{h_bbox};
-    memcpy(h_bbox, init, sizeof init);
-    TPM_CUDA(cudaMemcpyAsync(bbox, h_bbox, 6 * sizeof(long long), cudaMemcpyHostToDevice, st));
-    TPM_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
+    } hg{hst};
+    memset(hst, 0, sizeof(BuildState));
+    for (int a = 0; a < 3; a++) {
+        hst->bbox[a] = LLONG_MAX;
+        hst->bbox[3 + a] = LLONG_MIN;
+    }
+    TPM_CUDA(cudaMemcpyAsync(dst, hst, sizeof(BuildState), cudaMemcpyHostToDevice, st));
+    const unsigned grid = (unsigned)(c->num_sms * 8);
+
+    // ---- prepare, bounding box, root, keys, sort
     k_prepare<<<blocks_for(n), kThreads, 0, st>>>(pos_in, mass_in, n, s->bp.periodic, s->bp.box, s->bp.shift[0],
-                                                   s->bp.shift[1], s->bp.shift[2], s->pos, s->mass, bbox, bad);
+                                                   s->bp.shift[1], s->bp.shift[2], s->pos, s->mass, dst->bbox,
+                                                   &dst->bad);
     count_launch();
     TPM_CUDA(cudaGetLastError());
-    TPM_CUDA(cudaMemcpyAsync(h_bbox, bbox, 6 * sizeof(long long), cudaMemcpyDeviceToHost, st));
-    TPM_CUDA(cudaMemcpyAsync(h_bbox + 6, bad, sizeof(int), cudaMemcpyDeviceToHost, st));
-    TPM_CUDA(cudaStreamSynchronize(st));
-    int badv = (int)(h_bbox[6] & 0xffffffff);
-    if (badv & 1) {
-        set_error("non-finite position");
-        return TPM_ENAN;
-    }
-    if (badv & 4) {
-        set_error("masses must be finite and > 0");
-        return TPM_ENAN;
-    }
-    if (badv & 2) {
-        set_error("periodic positions must lie in [0, box)");
-        return TPM_EINVAL;
-    }
-
-    // ---- root
-    if (s->bp.periodic) {
-        s->x0[0] = s->x0[1] = s->x0[2] = 0.0;
-        s->L0 = s->bp.box;
-    } else {
-        double lo[3], hi[3], ext = 0.0;
-        for (int a = 0; a < 3; a++) {
-            lo[a] = from_ordered_bits(h_bbox[a]);
-            hi[a] = from_ordered_bits(h_bbox[3 + a]);
-            ext = std::max(ext, hi[a] - lo[a]);
-        }
-        if (!(ext > 0.0))
-            ext = 1.0;
-        double L0 = pow2_ceil(1.25 * ext);
-        double unit = std::ldexp(L0, -kMaxLevel);
-        for (int a = 0; a < 3; a++) {
-            double slack = L0 - (hi[a] - lo[a]);
-            double x0 = lo[a] - s->bp.shift[a] * slack;
-            s->x0[a] = std::floor(x0 / unit) * unit;
-        }
-        s->L0 = L0;
-    }
-
-    // ---- keys and sort
+    k_root<<<1, 32, 0, st>>>(dst, s->bp.periodic, s->bp.box, s->bp.shift[0], s->bp.shift[1], s->bp.shift[2]);
+    count_launch();
+    TPM_CUDA(cudaGetLastError());
     uint64_t *key_raw;
     uint32_t *idx_raw;
     TPM_CHECK(tmp.get(&key_raw, n, st));
     TPM_CHECK(tmp.get(&idx_raw, n, st));
-    double scale = std::ldexp(1.0, kMaxLevel) / s->L0;
-    k_keys<<<blocks_for(n), kThreads, 0, st>>>(s->pos, n, s->x0[0], s->x0[1], s->x0[2], scale, key_raw, idx_raw);
+    k_keys<<<blocks_for(n), kThreads, 0, st>>>(s->pos, n, dst, key_raw, idx_raw);
     count_launch();
     TPM_CUDA(cudaGetLastError());
     size_t sort_bytes = 0;
     TPM_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, sort_bytes, key_raw, s->key, idx_raw, s->perm, (int)n, 0,
                                              3 * kMaxLevel, st));
-    // the scan over one level reuses the same scratch
-    size_t scan_bytes = 0;
-    TPM_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, scan_bytes, (uint32_t *)nullptr, (uint32_t *)nullptr, (int)n, st));
     void *cub_tmp;
-    size_t cub_bytes = std::max(sort_bytes, scan_bytes);
-    TPM_CHECK(tmp.get((char **)&cub_tmp, cub_bytes, st));
+    TPM_CHECK(tmp.get((char **)&cub_tmp, sort_bytes, st));
     TPM_CUDA(cub::DeviceRadixSort::SortPairs(cub_tmp, sort_bytes, key_raw, s->key, idx_raw, s->perm, (int)n, 0,
                                              3 * kMaxLevel, st));
     count_cub_call();
@@ -445,88 +516,73 @@ int build_tree_device(Ctx *c, System *s, const double *pos_in, const float *mass
     count_launch();
     TPM_CUDA(cudaGetLastError());
 
-    // ---- levels (breadth-first arrays)
-    int64_t cap = 2 * n + 1024;
+    // ---- levels and monopoles, all on the device; retried with more node
+    // space in the rare case the first guess is too small
+    unsigned cap = (unsigned)std::min<int64_t>(2 * n + 1024, 0x7fffffffLL);
     LevelArrays b{};
-    AllocSet bfs;
-    bfs.ctx = c;
-    struct BfsGuard {
+    double *M = nullptr, *S = nullptr;
+    AllocSet lv;
+    lv.ctx = c;
+    struct LvGuard {
         AllocSet &t;
         cudaStream_t st;
-        ~BfsGuard() { t.release(st); }
-    } bguard{bfs, st};
-    auto alloc_bfs = [&](int64_t capacity, LevelArrays &out) -> int {
-        TPM_CHECK(bfs.get(&out.first, capacity, st));
-        TPM_CHECK(bfs.get(&out.count, capacity, st));
-        TPM_CHECK(bfs.get(&out.child, capacity, st));
-        TPM_CHECK(bfs.get(&out.nchild, capacity, st));
-        TPM_CHECK(bfs.get(&out.level, capacity, st));
-        TPM_CHECK(bfs.get(&out.prefix, capacity, st));
-        return TPM_OK;
-    };
-    TPM_CHECK(alloc_bfs(cap, b));
-    uint32_t *nch, *offs;
-    TPM_CHECK(tmp.get(&nch, n + 1, st));
-    TPM_CHECK(tmp.get(&offs, n + 1, st));
-    {
-        uint32_t zero = 0, cnt = (uint32_t)n;
-        uint8_t l0 = 0;
-        uint64_t p0 = 0;
-        TPM_CUDA(cudaMemcpyAsync(b.first, &zero, 4, cudaMemcpyHostToDevice, st));
-        TPM_CUDA(cudaMemcpyAsync(b.count, &cnt, 4, cudaMemcpyHostToDevice, st));
-        TPM_CUDA(cudaMemcpyAsync(b.level, &l0, 1, cudaMemcpyHostToDevice, st));
-        TPM_CUDA(cudaMemcpyAsync(b.prefix, &p0, 8, cudaMemcpyHostToDevice, st));
-    }
-    std::vector<int64_t> lstart{0}, lcount{1};
-    uint32_t *h_tot = (uint32_t *)h_bbox;  // reuse pinned scratch
-    for (int level = 0;; level++) {
-        int64_t ls = lstart.back(), lc = lcount.back();
-        k_count_children<<<blocks_for(lc), kThreads, 0, st>>>(s->key, b, ls, lc, level, B, nch);
+        ~LvGuard() { t.release(st); }
+    } lguard{lv, st};
+    for (int attempt = 0;; attempt++) {
+        lv.release(st);
+        TPM_CHECK(lv.get(&b.first, cap, st));
+        TPM_CHECK(lv.get(&b.count, cap, st));
+        TPM_CHECK(lv.get(&b.child, cap, st));
+        TPM_CHECK(lv.get(&b.nchild, cap, st));
+        TPM_CHECK(lv.get(&b.level, cap, st));
+        TPM_CHECK(lv.get(&b.prefix, cap, st));
+        TPM_CHECK(lv.get(&M, cap, st));
+        TPM_CHECK(lv.get(&S, 3 * (size_t)cap, st));
+        TPM_CUDA(cudaMemsetAsync(&dst->overflow, 0, sizeof(int), st));
+        k_level0<<<1, 32, 0, st>>>(b, dst, n);
         count_launch();
-        TPM_CUDA(cudaGetLastError());
-        size_t sb = scan_bytes;
-        TPM_CUDA(cub::DeviceScan::ExclusiveSum(cub_tmp, sb, nch, offs, (int)lc, st));
-        count_cub_call();
-        TPM_CUDA(cudaMemcpyAsync(h_tot, offs + lc - 1, 4, cudaMemcpyDeviceToHost, st));
-        TPM_CUDA(cudaMemcpyAsync(h_tot + 1, nch + lc - 1, 4, cudaMemcpyDeviceToHost, st));
-        TPM_CUDA(cudaStreamSynchronize(st));
-        int64_t total = (int64_t)h_tot[0] + (int64_t)h_tot[1];
-        int64_t next = ls + lc;
-        if (next + total > cap) {
-            int64_t ncap = std::max(next + total, cap + cap / 2);
-            LevelArrays nb{};
-            TPM_CHECK(alloc_bfs(ncap, nb));
-            TPM_CUDA(cudaMemcpyAsync(nb.first, b.first, next * 4, cudaMemcpyDeviceToDevice, st));
-            TPM_CUDA(cudaMemcpyAsync(nb.count, b.count, next * 4, cudaMemcpyDeviceToDevice, st));
-            TPM_CUDA(cudaMemcpyAsync(nb.child, b.child, next * 4, cudaMemcpyDeviceToDevice, st));
-            TPM_CUDA(cudaMemcpyAsync(nb.nchild, b.nchild, next * 4, cudaMemcpyDeviceToDevice, st));
-            TPM_CUDA(cudaMemcpyAsync(nb.level, b.level, next, cudaMemcpyDeviceToDevice, st));
-            TPM_CUDA(cudaMemcpyAsync(nb.prefix, b.prefix, next * 8, cudaMemcpyDeviceToDevice, st));
-            b = nb;
-            cap = ncap;
+        for (int level = 0; level <= kMaxLevel; level++) {
+            k_split_level<<<grid, kThreads, 0, st>>>(s->key, b, dst, level, B, cap);
+            count_launch();
+            if (level < kMaxLevel) {
+                k_level_bounds<<<1, 32, 0, st>>>(dst, level, cap);
+                count_launch();
+            }
         }
-        k_emit_children<<<blocks_for(lc), kThreads, 0, st>>>(s->key, b, ls, lc, level, B, offs, next);
-        count_launch();
         TPM_CUDA(cudaGetLastError());
-        if (total == 0)
+        for (int level = kMaxLevel; level >= 0; level--) {
+            k_multipole<<<grid, kThreads, 0, st>>>(b, dst, level, s->perm, s->pos, s->mass, M, S);
+            count_launch();
+        }
+        TPM_CUDA(cudaGetLastError());
+        TPM_CUDA(cudaMemcpyAsync(hst, dst, sizeof(BuildState), cudaMemcpyDeviceToHost, st));
+        TPM_CUDA(cudaStreamSynchronize(st));
+        if (hst->bad & 1) {
+            set_error("non-finite position");
+            return TPM_ENAN;
+        }
+        if (hst->bad & 4) {
+            set_error("masses must be finite and > 0");
+            return TPM_ENAN;
+        }
+        if (hst->bad & 2) {
+            set_error("periodic positions must lie in [0, box)");
+            return TPM_EINVAL;
+        }
+        if (!hst->overflow)
             break;
-        lstart.push_back(next);
-        lcount.push_back(total);
+        if (attempt >= 2 || hst->total >= 0x7fffffffu) {
+            set_error("tree node space overflow (%u nodes needed)", hst->total);
+            return TPM_ECUDA;
+        }
+        cap = (unsigned)std::min<uint64_t>((uint64_t)hst->total * 2 + 1024, 0x7fffffffULL);
     }
-    const int64_t nn = lstart.back() + lcount.back();
+    for (int a = 0; a < 3; a++)
+        s->x0[a] = hst->x0[a];
+    s->L0 = hst->L0;
+    const int64_t nn = hst->total;
     s->nnodes = nn;
-    s->maxlevel = (int)lstart.size() - 1;
-
-    // ---- multipoles, deepest level first
-    double *M, *S;
-    TPM_CHECK(tmp.get(&M, nn, st));
-    TPM_CHECK(tmp.get(&S, 3 * nn, st));
-    for (int level = (int)lstart.size() - 1; level >= 0; level--) {
-        int64_t lc = lcount[level];
-        k_multipole<<<blocks_for(lc), kThreads, 0, st>>>(b, lstart[level], lc, s->perm, s->pos, s->mass, M, S);
-        count_launch();
-        TPM_CUDA(cudaGetLastError());
-    }
+    s->maxlevel = hst->maxlevel;
 
     // ---- pre-order
     uint64_t *okey, *pkey;
@@ -541,7 +597,7 @@ int build_tree_device(Ctx *c, System *s, const double *pos_in, const float *mass
     size_t sb2 = 0;
     TPM_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, sb2, okey, pkey, oval, pre2bfs, (int)nn, 0, 37, st));
     void *cub_tmp2 = cub_tmp;
-    if (sb2 > cub_bytes)
+    if (sb2 > sort_bytes)
         TPM_CHECK(tmp.get((char **)&cub_tmp2, sb2, st));
     TPM_CUDA(cub::DeviceRadixSort::SortPairs(cub_tmp2, sb2, okey, pkey, oval, pre2bfs, (int)nn, 0, 37, st));
     count_cub_call();
@@ -555,6 +611,13 @@ int build_tree_device(Ctx *c, System *s, const double *pos_in, const float *mass
     TPM_CHECK(s->mem.get(&s->ncomd, 3 * nn, st));
     NodeOut o{s->ncen, s->ncom, s->nlink, s->nlevel, s->nprefix, s->nmass, s->ncomd};
     k_finalize<<<blocks_for(nn), kThreads, 0, st>>>(b, pkey, pre2bfs, nn, M, S, s->x0[0], s->x0[1], s->x0[2], s->L0, o);
+    count_launch();
+    TPM_CUDA(cudaGetLastError());
+    TPM_CHECK(s->mem.get(&s->bcen, nn, st));
+    TPM_CHECK(s->mem.get(&s->bcom, nn, st));
+    TPM_CHECK(s->mem.get(&s->blink, nn, st));
+    k_finalize_bfs<<<blocks_for(nn), kThreads, 0, st>>>(b, nn, M, S, s->x0[0], s->x0[1], s->x0[2], s->L0, s->bcen,
+                                                        s->bcom, s->blink);
     count_launch();
     TPM_CUDA(cudaGetLastError());
     k_leaf_particles<<<blocks_for(nn), kThreads, 0, st>>>(s->ncen, s->nlink, nn, s->perm, s->pos, s->mass, s->x0[0],

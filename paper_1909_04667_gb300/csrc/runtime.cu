@@ -434,15 +434,12 @@ int tpm_compute_forces(tpm_ctx *h, tpm_sys sid, const uint32_t *active_ids, int6
     r.nint = d_nint;
     if (d_ids) {
         uint32_t *keys, *vals, *sk, *sv;
-        int *bad;
         TPM_CHECK(tmp.get(&keys, n_active, st));
         TPM_CHECK(tmp.get(&vals, n_active, st));
         TPM_CHECK(tmp.get(&sk, n_active, st));
         TPM_CHECK(tmp.get(&sv, n_active, st));
-        TPM_CHECK(tmp.get(&bad, 1, st));
-        TPM_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
         k_active_keys<<<(unsigned)((n_active + 255) / 256), 256, 0, st>>>(d_ids, n_active, s->rank, s->n, keys, vals,
-                                                                         bad);
+                                                                         s->err);
         count_launch();
         TPM_CUDA(cudaGetLastError());
         size_t sb = 0;
@@ -479,6 +476,35 @@ int tpm_compute_forces(tpm_ctx *h, tpm_sys sid, const uint32_t *active_ids, int6
     if (sync || staged)
         TPM_CUDA(cudaStreamSynchronize(st));
     return TPM_OK;
+}
+
+int tpm_sync_status(tpm_ctx *h, tpm_sys sid, void *stream) {
+    clear_error();
+    if (!h) {
+        set_error("null ctx");
+        return TPM_EINVAL;
+    }
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    System *s = find(c, sid);
+    if (!s) {
+        set_error("unknown system handle %llu", (unsigned long long)sid);
+        return TPM_ENOSYS_HANDLE;
+    }
+    TPM_CUDA(cudaSetDevice(c->device));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int word = 0;
+    TPM_CUDA(cudaMemcpyAsync(&word, s->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TPM_CUDA(cudaStreamSynchronize(st));
+    if (word == 0)
+        return TPM_OK;
+    TPM_CUDA(cudaMemsetAsync(s->err, 0, sizeof(int), st));
+    TPM_CUDA(cudaStreamSynchronize(st));
+    if (word & 1) {
+        set_error("an active id was out of range (its outputs are those of particle 0)");
+        return TPM_EINVAL;
+    }
+    set_error("the walk's candidate stack overflowed (device status %d)", word);
+    return TPM_ECUDA;
 }
 
 int tpm_release(tpm_ctx *h, tpm_sys sid) {

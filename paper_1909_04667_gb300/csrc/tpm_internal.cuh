@@ -107,10 +107,20 @@ struct System {
     float4 *ncen = nullptr;  // geometric centre relative to x0 (exact in FP32), side L
     float4 *ncom = nullptr;  // centre of mass minus geometric centre (FP32), mass (FP32)
     int4 *nlink = nullptr;   // skip, first particle, count, leaf flag
+    // the same nodes in breadth-first order (children of a node contiguous), for
+    // the group walk: centre + side, centre of mass offset + mass, and
+    // (first child, child count, first particle, particle count)
+    float4 *bcen = nullptr;
+    float4 *bcom = nullptr;
+    int4 *blink = nullptr;
     uint8_t *nlevel = nullptr;
     uint64_t *nprefix = nullptr;
     double *nmass = nullptr;  // FP64
     double *ncomd = nullptr;  // FP64 centre of mass, n x 3
+
+    // device status word: bit 0 an active id was out of range, bit 1 the group
+    // walk's candidate stack overflowed (read and cleared by tpm_sync_status)
+    int *err = nullptr;
 
     // long-range mesh
     AllocSet pm_mem;

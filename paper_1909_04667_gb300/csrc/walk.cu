@@ -22,6 +22,9 @@
 // particles as FP32 offsets from their node centre, so every pair vector is
 // a sum of small, accurately rounded terms and the pair arithmetic runs in
 // FP32 with FP32 accumulation.
+#include <cstdlib>
+#include <cstring>
+
 #include "tpm_internal.cuh"
 
 namespace tpm {
@@ -167,13 +170,13 @@ __global__ void __launch_bounds__(kWalkThreads)
         const float4 O = __ldg(&ncom[n]);
         const int4 Lk = __ldg(&nlink[n]);
         const bool act = n >= skip_until;
-        float dcx = C.x - gcx, dcy = C.y - gcy, dcz = C.z - gcz;  // exact
-        if (PERIODIC) {
-            dcx = wrap_min_image(dcx, k);
-            dcy = wrap_min_image(dcy, k);
-            dcz = wrap_min_image(dcz, k);
+        const float dcx = C.x - gcx, dcy = C.y - gcy, dcz = C.z - gcz;  // exact
+        float px = xox - dcx, py = xoy - dcy, pz = xoz - dcz;  // particle relative to node centre
+        if (PERIODIC) {  // nearest image of the node centre as seen from this particle
+            px = wrap_min_image(px, k);
+            py = wrap_min_image(py, k);
+            pz = wrap_min_image(pz, k);
         }
-        const float px = xox - dcx, py = xoy - dcy, pz = xoz - dcz;  // particle relative to node centre
         const float L = C.w;
         float rx = O.x - px, ry = O.y - py, rz = O.z - pz;  // particle -> centre of mass
         if (PERIODIC && L > k.bigL) {
@@ -252,14 +255,528 @@ __global__ void __launch_bounds__(kWalkThreads)
         nint[out] = cnt;
 }
 
+// ======================================================================
+// Group walk.
+//
+// The lane walk above pays ~50 warp instructions for every node it visits,
+// however few lanes need the node.  Most visited nodes, though, get the same
+// answer from every particle of a compact group: far nodes are accepted by
+// all, nearby ones opened by all, and with TreePM distant ones skipped by all.
+// The group walk therefore decides each candidate node once for the whole
+// group, one node per lane, from the group's bounding box with conservative
+// bounds (a node is "accepted by all" only if the criterion accepts it even
+// for the box point closest to its centre of mass, and so on), and keeps the
+// per-particle decision only for the nodes where the bounds leave doubt:
+// those are resolved lane by lane exactly as in the lane walk.  The decisions
+// -- hence every particle's interaction set -- are the per-particle walk's.
+// Accepted nodes and opened leaves go to a per-warp list in shared memory,
+// tagged with the lanes they apply to, and the lanes then sweep the list in a
+// tight loop of pair terms.  Candidates come from a per-warp stack of child
+// ranges (children are contiguous in breadth-first order).
+// ======================================================================
+constexpr int kGroupWarps = 4;
+constexpr int kStackCap = 256;
+constexpr int kStackSafe = kStackCap - 64;  // above this, take one candidate at a time
+constexpr int kNodeFlush = 64;              // sweep once this many node entries are queued
+constexpr int kNodeCap = kNodeFlush + 64;   // one batch adds at most 64
+constexpr int kLeafFlush = 32;
+constexpr int kLeafCap = kLeafFlush + 64;
+constexpr uint32_t kLeafWrap = 0x80000000u, kLeafCount = 0x7fffffffu;
+enum { kSkip = 0, kAccept = 1, kOpen = 2, kMixed = 3, kNone = 4 };
+
+struct GroupShared {
+    uint2 stack[kStackCap];  // (first child, lane mask)
+    uint8_t scount[kStackCap];
+    float4 nsrc[kNodeCap];   // accepted node: centre of mass (group frame) + mass
+    uint32_t nmask[kNodeCap];
+    uint8_t nwrap[kNodeCap];
+    float4 lsrc[kLeafCap];   // opened leaf: centre (group frame) + first particle
+    uint2 lmeta[kLeafCap];   // lane mask, wrap flag | particle count
+    uint2 cand[32];          // (node, lane mask)
+};
+
+// Conservative decision for all particles inside [lo, hi] (group frame).
+template <bool PERIODIC, bool RELATIVE, bool TREEPM>
+__device__ __forceinline__ int classify_group(float4 C, float4 O, float gcx, float gcy, float gcz, float lox,
+                                              float loy, float loz, float hix, float hiy, float hiz, float thr_min,
+                                              float thr_max, bool wide, const WalkConsts &k, float &dcx, float &dcy,
+                                              float &dcz) {
+    dcx = C.x - gcx;
+    dcy = C.y - gcy;
+    dcz = C.z - gcz;
+    if (PERIODIC) {
+        dcx = wrap_min_image(dcx, k);
+        dcy = wrap_min_image(dcy, k);
+        dcz = wrap_min_image(dcz, k);
+    }
+    const float L = C.w, M = O.w;
+    if (PERIODIC && (wide || L > k.bigL))
+        return kMixed;  // the group-centred image may not be every particle's nearest one
+    const float up = 1.0f + 1e-5f, dn = 1.0f - 1e-5f;
+    // range of (particle - node centre) over the box, per axis
+    const float ax0 = lox - dcx, ax1 = hix - dcx, ay0 = loy - dcy, ay1 = hiy - dcy, az0 = loz - dcz, az1 = hiz - dcz;
+    const float nx = fmaxf(fmaxf(ax0, -ax1), 0.0f), ny = fmaxf(fmaxf(ay0, -ay1), 0.0f),
+                nz = fmaxf(fmaxf(az0, -az1), 0.0f);  // nearest |p - c|
+    const float fx = fmaxf(fabsf(ax0), fabsf(ax1)), fy = fmaxf(fabsf(ay0), fabsf(ay1)),
+                fz = fmaxf(fabsf(az0), fabsf(az1));  // farthest |p - c|
+    if (TREEPM) {
+        const float hL = 0.5f * L;
+        const float ex = fmaxf(nx - hL, 0.0f), ey = fmaxf(ny - hL, 0.0f), ez = fmaxf(nz - hL, 0.0f);
+        if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) > k.rcut2 * up)
+            return kSkip;
+        const float gx = fmaxf(fx - hL, 0.0f), gy = fmaxf(fy - hL, 0.0f), gz = fmaxf(fz - hL, 0.0f);
+        if (fmaf(gx, gx, fmaf(gy, gy, gz * gz)) > k.rcut2 * dn)
+            return kMixed;  // some particles may see the node beyond the cutoff
+    }
+    const float gl = 0.6f * L;
+    const bool guard_all = k.box_guard && fmaxf(fx, fmaxf(fy, fz)) <= gl * dn;
+    const bool guard_none = !k.box_guard || fmaxf(nx, fmaxf(ny, nz)) > gl * up;
+    // range of (particle - centre of mass)
+    const float cx = dcx + O.x, cy = dcy + O.y, cz = dcz + O.z;
+    const float bx0 = lox - cx, bx1 = hix - cx, by0 = loy - cy, by1 = hiy - cy, bz0 = loz - cz, bz1 = hiz - cz;
+    const float mx = fmaxf(fmaxf(bx0, -bx1), 0.0f), my = fmaxf(fmaxf(by0, -by1), 0.0f),
+                mz = fmaxf(fmaxf(bz0, -bz1), 0.0f);
+    const float Mx = fmaxf(fabsf(bx0), fabsf(bx1)), My = fmaxf(fabsf(by0), fabsf(by1)),
+                Mz = fmaxf(fabsf(bz0), fabsf(bz1));
+    const float dmin2 = fmaf(mx, mx, fmaf(my, my, mz * mz));
+    const float dmax2 = fmaf(Mx, Mx, fmaf(My, My, Mz * Mz));
+    bool open_all, acc_all;
+    if (RELATIVE) {
+        const float q = M * L * L;
+        open_all = q > thr_max * dmax2 * dmax2 * up;
+        acc_all = q <= thr_min * dmin2 * dmin2 * dn;
+    } else {
+        const float q = L * L;
+        open_all = q > k.thr_const * dmax2 * up;
+        acc_all = q <= k.thr_const * dmin2 * dn;
+    }
+    if (guard_all || open_all)
+        return kOpen;
+    if (guard_none && acc_all)
+        return kAccept;
+    return kMixed;
+}
+
+// Monopole of mass m at offset (rx, ry, rz) for r2 >= h2 (Newtonian, no split).
+__device__ __forceinline__ void newton_term(float rx, float ry, float rz, float r2, float m, float &ax, float &ay,
+                                            float &az, float &ph) {
+    const float ri = rsqrtf(r2);
+    const float mr = m * ri;
+    const float mr3 = mr * ri * ri;
+    ax = fmaf(mr3, rx, ax);
+    ay = fmaf(mr3, ry, ay);
+    az = fmaf(mr3, rz, az);
+    ph -= mr;
+}
+
+// Node entries accepted by every particle of the group sit at the front of the
+// node queue: no lane masks; two entries per step, one softening vote per
+// step, so that the two pair terms interleave.
+template <bool PERIODIC, bool TREEPM>
+__device__ __forceinline__ void sweep_full(const GroupShared &sh, int nf, float xox, float xoy, float xoz,
+                                           const WalkConsts &k, float &ax, float &ay, float &az, float &ph) {
+    int e = 0;
+    for (; e + 1 < nf; e += 2) {
+        const float4 A = sh.nsrc[e], B = sh.nsrc[e + 1];
+        float ax0 = A.x - xox, ay0 = A.y - xoy, az0 = A.z - xoz;
+        float ax1 = B.x - xox, ay1 = B.y - xoy, az1 = B.z - xoz;
+        if (PERIODIC && (sh.nwrap[e] | sh.nwrap[e + 1])) {
+            ax0 = wrap_min_image(ax0, k);
+            ay0 = wrap_min_image(ay0, k);
+            az0 = wrap_min_image(az0, k);
+            ax1 = wrap_min_image(ax1, k);
+            ay1 = wrap_min_image(ay1, k);
+            az1 = wrap_min_image(az1, k);
+        }
+        const float r20 = fmaf(ax0, ax0, fmaf(ay0, ay0, az0 * az0));
+        const float r21 = fmaf(ax1, ax1, fmaf(ay1, ay1, az1 * az1));
+        if (!TREEPM && __all_sync(0xffffffffu, fminf(r20, r21) >= k.h2)) {
+            newton_term(ax0, ay0, az0, r20, A.w, ax, ay, az, ph);
+            newton_term(ax1, ay1, az1, r21, B.w, ax, ay, az, ph);
+        } else {
+            pair_term<TREEPM>(ax0, ay0, az0, r20, A.w, k, ax, ay, az, ph);
+            pair_term<TREEPM>(ax1, ay1, az1, r21, B.w, k, ax, ay, az, ph);
+        }
+    }
+    if (e < nf) {
+        const float4 A = sh.nsrc[e];
+        float rx = A.x - xox, ry = A.y - xoy, rz = A.z - xoz;
+        if (PERIODIC && sh.nwrap[e]) {
+            rx = wrap_min_image(rx, k);
+            ry = wrap_min_image(ry, k);
+            rz = wrap_min_image(rz, k);
+        }
+        pair_term<TREEPM>(rx, ry, rz, fmaf(rx, rx, fmaf(ry, ry, rz * rz)), A.w, k, ax, ay, az, ph);
+    }
+}
+
+// Node entries for a subset of the lanes sit at the back of the node queue
+// (indices [kNodeCap - np, kNodeCap)): lanes not tagged add a zero mass.
+template <bool PERIODIC, bool TREEPM>
+__device__ __forceinline__ void sweep_partial(const GroupShared &sh, int np, unsigned lanebit, float xox, float xoy,
+                                              float xoz, const WalkConsts &k, float &ax, float &ay, float &az,
+                                              float &ph, uint32_t &cnt) {
+    for (int e = kNodeCap - np; e < kNodeCap; e++) {
+        const float4 E = sh.nsrc[e];
+        const bool mine = (sh.nmask[e] & lanebit) != 0u;
+        float rx = E.x - xox, ry = E.y - xoy, rz = E.z - xoz;
+        if (PERIODIC && sh.nwrap[e]) {
+            rx = wrap_min_image(rx, k);
+            ry = wrap_min_image(ry, k);
+            rz = wrap_min_image(rz, k);
+        }
+        float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+        r2 = mine ? r2 : 1.0f;  // a lane not tagged may sit on the node: keep rsqrt finite
+        const float m = mine ? E.w : 0.0f;
+        cnt += mine ? 1u : 0u;
+        if (!TREEPM && __all_sync(0xffffffffu, r2 >= k.h2))
+            newton_term(rx, ry, rz, r2, m, ax, ay, az, ph);
+        else
+            pair_term<TREEPM>(rx, ry, rz, r2, m, k, ax, ay, az, ph);
+    }
+}
+
+// Sweeps the queued opened leaves, particle by particle.
+template <bool PERIODIC, bool TREEPM>
+__device__ __forceinline__ void sweep_leaves(const GroupShared &sh, int nl, unsigned lanebit, uint32_t self,
+                                             float xox, float xoy, float xoz, const float4 *__restrict__ spart,
+                                             const WalkConsts &k, float &ax, float &ay, float &az, float &ph,
+                                             uint32_t &cnt) {
+    for (int e = 0; e < nl; e++) {
+        const float4 E = sh.lsrc[e];
+        const uint2 Mt = sh.lmeta[e];
+        const bool mine = (Mt.x & lanebit) != 0u;
+        const bool wr = PERIODIC && (Mt.y & kLeafWrap);
+        // subtract the small particle-to-leaf-centre vector first so that close
+        // pairs keep their precision
+        float px = xox - E.x, py = xoy - E.y, pz = xoz - E.z;
+        if (wr) {
+            px = wrap_min_image(px, k);
+            py = wrap_min_image(py, k);
+            pz = wrap_min_image(pz, k);
+        }
+        const int j0 = __float_as_int(E.w);
+        const int j1 = j0 + (int)(Mt.y & kLeafCount);
+        for (int jj = j0; jj < j1; jj++) {
+            const float4 P = __ldg(&spart[jj]);
+            float qx = P.x - px, qy = P.y - py, qz = P.z - pz;
+            if (wr) {
+                qx = wrap_min_image(qx, k);
+                qy = wrap_min_image(qy, k);
+                qz = wrap_min_image(qz, k);
+            }
+            const float q2 = fmaf(qx, qx, fmaf(qy, qy, qz * qz));
+            if (mine && (uint32_t)jj != self && (!TREEPM || q2 <= k.rcut2)) {
+                pair_term<TREEPM>(qx, qy, qz, q2, P.w, k, ax, ay, az, ph);
+                cnt++;
+            }
+        }
+    }
+}
+
+template <bool PERIODIC, bool RELATIVE, bool TREEPM>
+__global__ void __launch_bounds__(kGroupWarps * 32)
+    k_walk_group(const float4 *__restrict__ bcen, const float4 *__restrict__ bcom, const int4 *__restrict__ blink,
+                 const float4 *__restrict__ spart, const uint64_t *__restrict__ key,
+                 const uint32_t *__restrict__ perm, const double *__restrict__ pos, double x0, double y0, double z0,
+                 double L0, const uint32_t *__restrict__ sidx, const uint32_t *__restrict__ slot,
+                 const float *__restrict__ a_old, int64_t n_act, WalkConsts k, float *__restrict__ acc,
+                 float *__restrict__ pot, uint32_t *__restrict__ nint, int accumulate, int *__restrict__ err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    GroupShared &sh = reinterpret_cast<GroupShared *>(smem_raw)[threadIdx.x >> 5];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lanebit = 1u << lane;
+    const unsigned lt_mask = lanebit - 1u;
+    const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane);
+    if (g0 >= n_act)
+        return;  // whole warp
+    const int64_t gi = g0 + lane;
+    const bool valid = gi < n_act;
+    const int64_t glast = min(g0 + 31, n_act - 1);
+    const uint32_t s = sidx ? sidx[valid ? gi : g0] : (uint32_t)(valid ? gi : g0);
+    const uint32_t s_first = sidx ? sidx[g0] : (uint32_t)g0;
+    const uint32_t s_last = sidx ? sidx[glast] : (uint32_t)glast;
+    const uint32_t out = slot ? slot[valid ? gi : g0] : perm[s];
+
+    // group frame: centre of the smallest key cell holding the first and last particle
+    const uint64_t kf = key[s_first], kl = key[s_last];
+    const uint64_t kx = kf ^ kl;
+    const int glevel = kx ? min((__clzll(kx) - 1) / 3, kMaxLevel) : kMaxLevel;
+    const uint64_t gpre = kf >> (3 * (kMaxLevel - glevel));
+    const double ghalf = ldexp(L0, -(glevel + 1));
+    const double gcx_d = (double)(2 * (uint64_t)compact3w(gpre) + 1) * ghalf;
+    const double gcy_d = (double)(2 * (uint64_t)compact3w(gpre >> 1) + 1) * ghalf;
+    const double gcz_d = (double)(2 * (uint64_t)compact3w(gpre >> 2) + 1) * ghalf;
+    const float gcx = (float)gcx_d, gcy = (float)gcy_d, gcz = (float)gcz_d;
+    const uint32_t j = perm[s];
+    const float xox = (float)(pos[3 * j] - (x0 + gcx_d));
+    const float xoy = (float)(pos[3 * j + 1] - (y0 + gcy_d));
+    const float xoz = (float)(pos[3 * j + 2] - (z0 + gcz_d));
+    float thr = k.thr_const;
+    if (RELATIVE)
+        thr = valid ? k.alpha_over_G * fabsf(a_old[out]) : 0.0f;
+
+    // group bounding box and criterion thresholds over the valid lanes
+    const float inf = __int_as_float(0x7f800000);
+    float lox = valid ? xox : inf, loy = valid ? xoy : inf, loz = valid ? xoz : inf;
+    float hix = valid ? xox : -inf, hiy = valid ? xoy : -inf, hiz = valid ? xoz : -inf;
+    float tmin = valid ? thr : inf, tmax = valid ? thr : 0.0f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lox = fminf(lox, __shfl_xor_sync(FULL, lox, o));
+        loy = fminf(loy, __shfl_xor_sync(FULL, loy, o));
+        loz = fminf(loz, __shfl_xor_sync(FULL, loz, o));
+        hix = fmaxf(hix, __shfl_xor_sync(FULL, hix, o));
+        hiy = fmaxf(hiy, __shfl_xor_sync(FULL, hiy, o));
+        hiz = fmaxf(hiz, __shfl_xor_sync(FULL, hiz, o));
+        if (RELATIVE) {
+            tmin = fminf(tmin, __shfl_xor_sync(FULL, tmin, o));
+            tmax = fmaxf(tmax, __shfl_xor_sync(FULL, tmax, o));
+        }
+    }
+    bool wide = false;
+    if (PERIODIC) {
+        const float ext = fmaxf(fmaxf(fmaxf(-lox, hix), fmaxf(-loy, hiy)), fmaxf(-loz, hiz));
+        wide = ext > 0.125f * k.box;
+    }
+    const unsigned valid_mask = __ballot_sync(FULL, valid);
+
+    float ax = 0.f, ay = 0.f, az = 0.f, ph = 0.f;
+    uint32_t cnt = 0;
+    if (lane == 0) {
+        sh.stack[0] = make_uint2(0u, valid_mask);  // the root, breadth-first index 0
+        sh.scount[0] = 1;
+    }
+    int sn = 1, nf = 0, np = 0, nl = 0;
+    __syncwarp();
+    while (sn > 0) {
+        // ---- take up to 32 candidates from the top child ranges
+        const int cap = sn > kStackSafe ? 1 : 32;
+        const int idx = sn - 1 - lane;
+        uint2 R = make_uint2(0u, 0u);
+        int c = 0;
+        if (idx >= 0) {
+            R = sh.stack[idx];
+            c = sh.scount[idx];
+        }
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o)
+                incl += v;
+        }
+        const int excl = incl - c;
+        const bool take = idx >= 0 && c > 0 && excl < cap;
+        const bool whole = take && incl <= cap;
+        const int ntake = take ? min(c, cap - excl) : 0;
+        for (int t = 0; t < ntake; t++)
+            sh.cand[excl + t] = make_uint2(R.x + (uint32_t)t, R.y);
+        const int nwhole = __popc(__ballot_sync(FULL, whole));
+        const int ncand = min(__shfl_sync(FULL, incl, 31), cap);
+        if (take && !whole) {  // the partly taken range stays on top
+            sh.stack[idx].x = R.x + (uint32_t)ntake;
+            sh.scount[idx] = (uint8_t)(c - ntake);
+        }
+        sn -= nwhole;
+        __syncwarp();
+
+        // ---- one candidate per lane: decide for the whole group
+        int cls = kNone;
+        uint32_t nmask = 0;
+        float4 C = make_float4(0.f, 0.f, 0.f, 0.f), O = C;
+        int4 Lk = make_int4(0, 0, 0, 0);
+        float dcx = 0.f, dcy = 0.f, dcz = 0.f;
+        if (lane < ncand) {
+            const uint2 cd = sh.cand[lane];
+            nmask = cd.y;
+            C = __ldg(&bcen[cd.x]);
+            O = __ldg(&bcom[cd.x]);
+            Lk = __ldg(&blink[cd.x]);
+            cls = classify_group<PERIODIC, RELATIVE, TREEPM>(C, O, gcx, gcy, gcz, lox, loy, loz, hix, hiy, hiz, tmin,
+                                                             tmax, wide, k, dcx, dcy, dcz);
+        }
+        __syncwarp();
+        const bool is_leaf = Lk.y == 0;
+        const bool wrapf = PERIODIC && (wide || C.w > k.bigL);
+        const bool e_acc = cls == kAccept, e_leaf = cls == kOpen && is_leaf, e_push = cls == kOpen && !is_leaf;
+        const bool e_full = e_acc && nmask == valid_mask;
+        const unsigned bf = __ballot_sync(FULL, e_full);
+        const unsigned bq = __ballot_sync(FULL, e_acc && !e_full);
+        if (e_acc) {
+            const int at = e_full ? nf + __popc(bf & lt_mask) : kNodeCap - 1 - np - __popc(bq & lt_mask);
+            sh.nsrc[at] = make_float4(dcx + O.x, dcy + O.y, dcz + O.z, O.w);
+            sh.nmask[at] = nmask;
+            sh.nwrap[at] = wrapf ? 1 : 0;
+        }
+        nf += __popc(bf);
+        np += __popc(bq);
+        const unsigned bl = __ballot_sync(FULL, e_leaf);
+        if (e_leaf) {
+            const int at = nl + __popc(bl & lt_mask);
+            sh.lsrc[at] = make_float4(dcx, dcy, dcz, __int_as_float(Lk.z));
+            sh.lmeta[at] = make_uint2(nmask, (wrapf ? kLeafWrap : 0u) | (uint32_t)Lk.w);
+        }
+        nl += __popc(bl);
+        const unsigned bp = __ballot_sync(FULL, e_push);
+        if (e_push) {
+            const int at = sn + __popc(bp & lt_mask);
+            if (at < kStackCap) {
+                sh.stack[at] = make_uint2((uint32_t)Lk.x, nmask);
+                sh.scount[at] = (uint8_t)Lk.y;
+            } else {
+                atomicOr(err, 2);
+            }
+        }
+        sn = min(sn + __popc(bp), kStackCap);
+
+        // ---- nodes the bounds could not decide: per-particle decisions; the
+        // node's record comes from the lane that classified it
+        unsigned mixed = __ballot_sync(FULL, cls == kMixed);
+        while (mixed) {
+            const int t = __ffs(mixed) - 1;
+            mixed &= mixed - 1;
+            const uint32_t mm = __shfl_sync(FULL, nmask, t);
+            const float MCx = __shfl_sync(FULL, C.x, t), MCy = __shfl_sync(FULL, C.y, t),
+                        MCz = __shfl_sync(FULL, C.z, t), L = __shfl_sync(FULL, C.w, t);
+            const float MOx = __shfl_sync(FULL, O.x, t), MOy = __shfl_sync(FULL, O.y, t),
+                        MOz = __shfl_sync(FULL, O.z, t), MOm = __shfl_sync(FULL, O.w, t);
+            const int Lx = __shfl_sync(FULL, Lk.x, t), Ly = __shfl_sync(FULL, Lk.y, t),
+                      Lz = __shfl_sync(FULL, Lk.z, t), Lw = __shfl_sync(FULL, Lk.w, t);
+            const bool act = (mm & lanebit) != 0u;
+            const float dx = MCx - gcx, dy = MCy - gcy, dz = MCz - gcz;  // exact
+            float px = xox - dx, py = xoy - dy, pz = xoz - dz;
+            if (PERIODIC) {
+                px = wrap_min_image(px, k);
+                py = wrap_min_image(py, k);
+                pz = wrap_min_image(pz, k);
+            }
+            float rx = MOx - px, ry = MOy - py, rz = MOz - pz;
+            if (PERIODIC && L > k.bigL) {
+                rx = wrap_min_image(rx, k);
+                ry = wrap_min_image(ry, k);
+                rz = wrap_min_image(rz, k);
+            }
+            const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+            bool far = false;
+            if (TREEPM) {
+                const float ex = fmaxf(fabsf(px) - 0.5f * L, 0.0f), ey = fmaxf(fabsf(py) - 0.5f * L, 0.0f),
+                            ez = fmaxf(fabsf(pz) - 0.5f * L, 0.0f);
+                far = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) > k.rcut2;
+            }
+            const float gl = 0.6f * L;
+            const bool guard = k.box_guard && fabsf(px) <= gl && fabsf(py) <= gl && fabsf(pz) <= gl;
+            const bool crit = RELATIVE ? (MOm * L * L > thr * r2 * r2) : (L * L > thr * r2);
+            const bool open = act && !far && (guard || crit);
+            const unsigned am = __ballot_sync(FULL, act && !far && !open);
+            const unsigned om = __ballot_sync(FULL, open);
+            float wx = dx, wy = dy, wz = dz;  // node centre, group-centred nearest image
+            if (PERIODIC) {
+                wx = wrap_min_image(wx, k);
+                wy = wrap_min_image(wy, k);
+                wz = wrap_min_image(wz, k);
+            }
+            const bool wflag = PERIODIC && (wide || L > k.bigL);
+            if (am) {
+                const bool full = am == valid_mask;
+                const int at = full ? nf : kNodeCap - 1 - np;
+                if (lane == 0) {
+                    sh.nsrc[at] = make_float4(wx + MOx, wy + MOy, wz + MOz, MOm);
+                    sh.nmask[at] = am;
+                    sh.nwrap[at] = wflag ? 1 : 0;
+                }
+                nf += full ? 1 : 0;
+                np += full ? 0 : 1;
+            }
+            if (om) {
+                if (Ly > 0) {
+                    if (lane == 0) {
+                        if (sn < kStackCap) {
+                            sh.stack[sn] = make_uint2((uint32_t)Lx, om);
+                            sh.scount[sn] = (uint8_t)Ly;
+                        } else {
+                            atomicOr(err, 2);
+                        }
+                    }
+                    sn = min(sn + 1, kStackCap);
+                } else {
+                    if (lane == 0) {
+                        sh.lsrc[nl] = make_float4(wx, wy, wz, __int_as_float(Lz));
+                        sh.lmeta[nl] = make_uint2(om, (wflag ? kLeafWrap : 0u) | (uint32_t)Lw);
+                    }
+                    nl++;
+                }
+            }
+        }
+        __syncwarp();
+        if (nf + np >= kNodeFlush) {
+            sweep_full<PERIODIC, TREEPM>(sh, nf, xox, xoy, xoz, k, ax, ay, az, ph);
+            sweep_partial<PERIODIC, TREEPM>(sh, np, lanebit, xox, xoy, xoz, k, ax, ay, az, ph, cnt);
+            cnt += valid ? (uint32_t)nf : 0u;
+            nf = np = 0;
+        }
+        if (nl >= kLeafFlush) {
+            sweep_leaves<PERIODIC, TREEPM>(sh, nl, lanebit, s, xox, xoy, xoz, spart, k, ax, ay, az, ph, cnt);
+            nl = 0;
+        }
+        __syncwarp();
+    }
+    sweep_full<PERIODIC, TREEPM>(sh, nf, xox, xoy, xoz, k, ax, ay, az, ph);
+    sweep_partial<PERIODIC, TREEPM>(sh, np, lanebit, xox, xoy, xoz, k, ax, ay, az, ph, cnt);
+    cnt += (uint32_t)nf;
+    sweep_leaves<PERIODIC, TREEPM>(sh, nl, lanebit, s, xox, xoy, xoz, spart, k, ax, ay, az, ph, cnt);
+    if (!valid)
+        return;
+    const float G = k.G;
+    if (accumulate) {
+        acc[3 * (size_t)out] += G * ax;
+        acc[3 * (size_t)out + 1] += G * ay;
+        acc[3 * (size_t)out + 2] += G * az;
+        if (pot)
+            pot[out] += G * ph;
+    } else {
+        acc[3 * (size_t)out] = G * ax;
+        acc[3 * (size_t)out + 1] = G * ay;
+        acc[3 * (size_t)out + 2] = G * az;
+        if (pot)
+            pot[out] = G * ph;
+    }
+    if (nint)
+        nint[out] = cnt;
+}
+
 template <bool P, bool R, bool T>
-void launch(const System *s, const WalkRequest &r, const WalkConsts &k, cudaStream_t st) {
+void launch(const System *s, const WalkRequest &r, const WalkConsts &k, bool lanes, int *err, cudaStream_t st) {
     const int64_t warps = (r.n_act + 31) / 32;
-    const int64_t blocks = (warps * 32 + kWalkThreads - 1) / kWalkThreads;
-    k_walk<P, R, T><<<(unsigned)blocks, kWalkThreads, 0, st>>>(
-        s->ncen, s->ncom, s->nlink, s->spart, s->key, s->perm, s->pos, s->x0[0], s->x0[1], s->x0[2], s->L0,
-        (int)s->nnodes, r.sorted_idx, r.slot, r.a_old, r.n_act, k, r.acc, r.pot, r.nint, r.accumulate);
-    count_launch();
+    if (lanes) {
+        const int64_t blocks = (warps * 32 + kWalkThreads - 1) / kWalkThreads;
+        k_walk<P, R, T><<<(unsigned)blocks, kWalkThreads, 0, st>>>(
+            s->ncen, s->ncom, s->nlink, s->spart, s->key, s->perm, s->pos, s->x0[0], s->x0[1], s->x0[2], s->L0,
+            (int)s->nnodes, r.sorted_idx, r.slot, r.a_old, r.n_act, k, r.acc, r.pot, r.nint, r.accumulate);
+        count_launch();
+    } else {
+        const int64_t blocks = (warps + kGroupWarps - 1) / kGroupWarps;
+        const size_t smem = kGroupWarps * sizeof(GroupShared);
+        k_walk_group<P, R, T><<<(unsigned)blocks, kGroupWarps * 32, smem, st>>>(
+            s->bcen, s->bcom, s->blink, s->spart, s->key, s->perm, s->pos, s->x0[0], s->x0[1], s->x0[2], s->L0,
+            r.sorted_idx, r.slot, r.a_old, r.n_act, k, r.acc, r.pot, r.nint, r.accumulate, err);
+        count_launch();
+    }
+}
+
+// Kernel choice: the group walk for open boundaries, the lane walk for the
+// short-range TreePM walk (there the cutoff sphere cuts through most groups,
+// so the group bounds rarely decide and the lane walk is faster).  TPM_WALK=
+// lanes or group forces one for comparison; both make the same per-particle
+// decisions.
+int walk_override() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("TPM_WALK");
+        v = (e && strcmp(e, "lanes") == 0) ? 1 : (e && strcmp(e, "group") == 0) ? 2 : 0;
+    }
+    return v;
 }
 
 }  // namespace
@@ -286,14 +803,17 @@ int walk_device(Ctx *, const System *s, const tpm_force_params *p, const WalkReq
         k.inv2rs = (float)(1.0 / (2.0 * rs));
     }
     const bool per = s->bp.periodic != 0, rel = p->crit == TPM_CRIT_RELATIVE, tpm = p->treepm != 0;
+    const int ov = walk_override();
+    const bool lanes = ov == 1 || (ov == 0 && tpm);
+    int *err = s->err;
     if (!per && !rel && !tpm)
-        launch<false, false, false>(s, r, k, st);
+        launch<false, false, false>(s, r, k, lanes, err, st);
     else if (!per && rel && !tpm)
-        launch<false, true, false>(s, r, k, st);
+        launch<false, true, false>(s, r, k, lanes, err, st);
     else if (per && !rel && tpm)
-        launch<true, false, true>(s, r, k, st);
+        launch<true, false, true>(s, r, k, lanes, err, st);
     else if (per && rel && tpm)
-        launch<true, true, true>(s, r, k, st);
+        launch<true, true, true>(s, r, k, lanes, err, st);
     else {
         set_error("unsupported walk mode (periodic systems need treepm = 1, open systems treepm = 0)");
         return TPM_EINVAL;

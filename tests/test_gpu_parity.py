@@ -122,6 +122,7 @@ def test_walk_bh_plummer(oracle_mod, tpm, ctx, torch_dev, bucket):
     s = ctx.build_tree(to_dev(pos, torch_dev), to_dev(mass, torch_dev),
                        tpm.BuildParams(G=1.0, h=0.01, shift=shift, leaf_bucket=bucket))
     acc, pot, nint = s.compute_forces(fp=tpm.ForceParams(crit=tpm.CRIT_BH, theta=0.7))
+    s.sync_status()
     acc, pot, nint = acc.cpu().numpy(), pot.cpu().numpy(), nint.cpu().numpy()
     s.release()
     tree = oracle_mod.Tree(pos, mass, bucket=bucket, shift=shift)
@@ -272,3 +273,68 @@ def test_periodic_treepm_matches_oracle(oracle_mod, tpm, ctx, torch_dev):
     a_s, p_s, n_o = tree.walk(tg, 1.0, h, theta=0.5, treepm=True, rs=rs, rcut=4.5 * rs)
     a_l, p_l = oracle_mod.pm_interpolate(phi_o, xtree[tg], 1.0)
     compare_forces(acc.cpu().numpy().astype(np.float64), a_s + a_l, nint.cpu().numpy(), n_o, p99=1e-4, mx=1e-3)
+
+
+LANE_SCRIPT = r"""
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+import paper_1909_04667_gb300 as tpm, workloads as W
+dev = torch.device('cuda', 0)
+ctx = tpm.Context(0)
+out = {}
+pos, mass = W.hernquist(50000, 8)
+s = ctx.build_tree(torch.from_numpy(pos).to(dev), torch.from_numpy(mass).to(dev),
+                   tpm.BuildParams(G=1.0, h=0.005, shift=tuple(W.root_shift(8)), leaf_bucket=8))
+a, p, n = s.compute_forces(fp=tpm.ForceParams(theta=0.5))
+s.sync_status()
+out['acc'], out['nint'] = a.cpu().numpy(), n.cpu().numpy()
+pos, mass = W.zeldovich(32, 5)
+fp = tpm.ForceParams(theta=0.5, treepm=True, pm_n=64, asmth=1.25, rcut=4.5)
+s = ctx.build_tree(torch.from_numpy(pos).to(dev), torch.from_numpy(mass).to(dev),
+                   tpm.BuildParams(G=1.0, h=1e-3, periodic=True, box=1.0, shift=tuple(W.root_shift(9)), leaf_bucket=8))
+s.pm_long_range(fp)
+ids = torch.from_numpy(np.arange(0, len(pos), 3).astype(np.int32)).to(dev)
+a, p, n = s.compute_forces(active_ids=ids, fp=fp)
+s.sync_status()
+out['pacc'], out['pnint'] = a.cpu().numpy(), n.cpu().numpy()
+np.savez(sys.argv[2], **out)
+"""
+
+
+def test_group_walk_matches_lane_walk(tmp_path):
+    # two kernels, the same per-particle decisions: the default group walk and
+    # the lane walk (TPM_WALK=lanes) must give the same interaction counts and
+    # forces within FP32 summation-order differences
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = tmp_path / "walk.py"
+    script.write_text(LANE_SCRIPT)
+    outs = []
+    for mode in ("group", "lanes"):
+        env = dict(os.environ)
+        env["TPM_WALK"] = mode
+        out = tmp_path / (mode + ".npz")
+        subprocess.run([sys.executable, str(script), root, str(out)], check=True, env=env, timeout=600)
+        outs.append(np.load(out))
+    g, l = outs
+    for acc, nint in (("acc", "nint"), ("pacc", "pnint")):  # open boundaries, periodic TreePM subset
+        assert np.mean(g[nint] != l[nint]) < 1e-3
+        same = g[nint] == l[nint]
+        e = rel(g[acc].astype(np.float64), l[acc].astype(np.float64))
+        assert np.percentile(e[same], 99) < P99_TOL and e[same].max() < MAX_TOL
+
+
+def test_sync_status_reports_device_errors(tpm, ctx, torch_dev):
+    pos, mass = W.plummer(500, 4)
+    s = ctx.build_tree(to_dev(pos, torch_dev), to_dev(mass, torch_dev), tpm.BuildParams())
+    s.compute_forces(fp=tpm.ForceParams())
+    s.sync_status()  # clean
+    bad = to_dev(np.array([3, 7, 9999], np.uint32), torch_dev)  # device ids are checked on the device
+    s.compute_forces(active_ids=bad, fp=tpm.ForceParams())
+    with pytest.raises(tpm.TreePMError, match="out of range"):
+        s.sync_status()
+    s.sync_status()  # the word was cleared
+    s.release()
