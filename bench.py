@@ -365,7 +365,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
     ap.add_argument("--no-periodic", action="store_true", help="skip the periodic TreePM measurement")
+    ap.add_argument("--bucket", type=int, default=None, help="leaf bucket B of the headline workload")
     args = ap.parse_args()
+    if args.bucket:
+        HERNQUIST["bucket"] = args.bucket
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

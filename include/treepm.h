@@ -199,6 +199,67 @@ int tpm_compute_forces_noalloc(tpm_ctx *ctx, tpm_sys s, const uint32_t *active_i
                                const float *a_old, const tpm_force_params *p, float *acc, float *pot,
                                uint32_t *n_int, void *stream);
 
+/*
+ * Batched evaluation (hierarchical time-step batching, serving).  The paper
+ * integrates with local power-of-two time steps (Sec. 7.2): each substep
+ * evaluates forces only for the particles of the active time bins, from the
+ * full mass distribution (Sec. 7.3); a force server likewise sees many small
+ * requests.  A plan holds all the scratch of a batch, so a batched call only
+ * enqueues device work -- no allocation, no host synchronisation -- and a
+ * sequence of batched calls can be captured in a CUDA graph.  All requests
+ * of one call run in one persistent walk launch: resident warps take groups
+ * of at most G consecutive (key-ordered) particles of any request from a
+ * device work queue.  Open-boundary systems only.
+ */
+typedef struct tpm_plan tpm_plan;
+
+/* Flag: each request's ids are already in the key order of its tree (as
+ * produced by cutting an active set sorted by tree rank); skips the sort. */
+#define TPM_BATCH_PRESORTED 1u
+
+/* Creates a plan for batches of at most max_ids ids in max_requests
+ * requests (memory drawn from ctx's budget: about 40 B per id + 300 B per
+ * request).  Errors: TPM_EINVAL, TPM_EBUDGET, TPM_ECUDA. */
+int tpm_plan_create(tpm_ctx *ctx, int64_t max_ids, int64_t max_requests, tpm_plan **plan);
+
+/* Frees a plan (waits for the device). */
+int tpm_plan_destroy(tpm_ctx *ctx, tpm_plan *plan);
+
+/* Walk group size G in [8, 32] (default 32) and its current value. */
+int tpm_plan_set_group_size(tpm_plan *plan, int group_size);
+int tpm_plan_group_size(const tpm_plan *plan);
+
+/*
+ * Forces for n_req requests in one launch.  Request r evaluates
+ * tpm_compute_forces for system systems[r] with params[r] on the ids
+ * ids[offsets[r] .. offsets[r+1]) (offsets: host array of n_req + 1, starting
+ * at 0, non-decreasing).  ids, a_old (per id, required if any request uses the
+ * relative criterion), acc (3 per id), pot and n_int (per id, may be NULL) are
+ * DEVICE arrays indexed by position in ids.  systems and params are host
+ * arrays; they are copied into the plan during the call.  Stream-ordered;
+ * never synchronises except to wait until the previous call on the plan has
+ * copied its host arguments (skipped while `stream` is being captured).
+ * Device-side errors (out-of-range ids) surface in tpm_plan_sync_status.
+ * Errors: TPM_EINVAL (sizes beyond the plan, periodic systems, host arrays),
+ * TPM_ENOSYS_HANDLE, TPM_ECUDA.
+ */
+int tpm_compute_forces_batch(tpm_ctx *ctx, tpm_plan *plan, int64_t n_req, const tpm_sys *systems,
+                             const int64_t *offsets, const tpm_force_params *params, const uint32_t *ids,
+                             const float *a_old, float *acc, float *pot, uint32_t *n_int, uint32_t flags,
+                             void *stream);
+
+/* Waits for `stream`; reports and clears device-side errors of the plan's
+ * batches (TPM_EINVAL: an id out of range; TPM_ECUDA: walk stack overflow). */
+int tpm_plan_sync_status(tpm_ctx *ctx, tpm_plan *plan, void *stream);
+
+/* Times the batch for G in {8, 16, 32} (reps timed runs each, after one
+ * warm-up), keeps the fastest in the plan and returns it with its median
+ * time in milliseconds.  Synchronises.  Arguments as tpm_compute_forces_batch. */
+int tpm_plan_autotune(tpm_ctx *ctx, tpm_plan *plan, int64_t n_req, const tpm_sys *systems, const int64_t *offsets,
+                      const tpm_force_params *params, const uint32_t *ids, const float *a_old, float *acc,
+                      float *pot, uint32_t *n_int, uint32_t flags, int reps, void *stream, int *best_group,
+                      float *best_ms);
+
 /* Waits for `stream` and reports errors that device work recorded for system
  * s since the last check (then clears them): TPM_EINVAL if a device-side
  * active id was out of range (its outputs hold particle 0's values), TPM_ECUDA

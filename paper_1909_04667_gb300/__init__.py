@@ -21,8 +21,8 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["Context", "System", "BuildParams", "ForceParams", "TreePMError", "lib_path", "CRIT_BH",
-           "CRIT_RELATIVE"]
+__all__ = ["Context", "System", "Plan", "BuildParams", "ForceParams", "TreePMError", "lib_path", "CRIT_BH",
+           "CRIT_RELATIVE", "BATCH_PRESORTED"]
 
 CRIT_BH = 0
 CRIT_RELATIVE = 1
@@ -79,6 +79,14 @@ def _load():
         "tpm_launch_counts": (i32, [C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)]),
         "tpm_compute_forces_noalloc": (i32, [vp, C.c_uint64, vp, i64, vp, C.POINTER(_ForceParams), vp, vp, vp,
                                              vp]),
+        "tpm_plan_create": (i32, [vp, i64, i64, C.POINTER(vp)]),
+        "tpm_plan_destroy": (i32, [vp, vp]),
+        "tpm_plan_set_group_size": (i32, [vp, i32]),
+        "tpm_plan_group_size": (i32, [vp]),
+        "tpm_compute_forces_batch": (i32, [vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, C.c_uint32, vp]),
+        "tpm_plan_sync_status": (i32, [vp, vp, vp]),
+        "tpm_plan_autotune": (i32, [vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, C.c_uint32, i32, vp,
+                                    C.POINTER(i32), C.POINTER(C.c_float)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -148,6 +156,77 @@ class ForceParams:
                             int(self.pm_n), self.asmth, self.rcut)
 
 
+BATCH_PRESORTED = 1
+
+
+class Plan:
+    """Scratch for batched evaluations (``tpm_plan_create``): many requests,
+    on one or several resident systems, in one persistent walk launch.  A
+    batched call allocates nothing and can be captured in a CUDA graph."""
+
+    def __init__(self, ctx: "Context", max_ids: int, max_requests: int):
+        h = C.c_void_p()
+        _check(_lib.tpm_plan_create(ctx._h, int(max_ids), int(max_requests), C.byref(h)))
+        self.ctx, self._h, self.max_ids, self.max_requests = ctx, h, int(max_ids), int(max_requests)
+        self._keep = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.tpm_plan_destroy(self.ctx._h, self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def group_size(self) -> int:
+        return int(_lib.tpm_plan_group_size(self._h))
+
+    @group_size.setter
+    def group_size(self, g: int):
+        _check(_lib.tpm_plan_set_group_size(self._h, int(g)))
+
+    def _args(self, systems, offsets, params):
+        n_req = len(systems)
+        sys_arr = (C.c_uint64 * n_req)(*[s.handle for s in systems])
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        if len(off) != n_req + 1:
+            raise ValueError("offsets must have len(systems) + 1 entries")
+        if isinstance(params, ForceParams):
+            params = [params] * n_req
+        par = (_ForceParams * n_req)(*[p._c() for p in params])
+        self._keep = (sys_arr, off, par)  # the call copies them; keep them alive through it
+        return n_req, sys_arr, off, par
+
+    def compute_forces_batch(self, systems, offsets, params, ids, acc, a_old=None, pot=None, n_int=None,
+                             presorted: bool = False, stream=None):
+        """``tpm_compute_forces_batch``: request r covers ids[offsets[r]:offsets[r+1]]
+        of ``systems[r]`` with ``params[r]`` (or one ForceParams for all).
+        ids, a_old, acc, pot, n_int are device tensors indexed by position."""
+        n_req, sys_arr, off, par = self._args(systems, offsets, params)
+        _check(_lib.tpm_compute_forces_batch(self.ctx._h, self._h, n_req, sys_arr, off.ctypes.data, par, _ptr(ids),
+                                             _ptr(a_old), _ptr(acc), _ptr(pot), _ptr(n_int),
+                                             BATCH_PRESORTED if presorted else 0, _stream(stream, self.ctx.device)))
+        return acc, pot, n_int
+
+    def autotune(self, systems, offsets, params, ids, acc, a_old=None, pot=None, n_int=None, presorted=False,
+                 reps: int = 3, stream=None):
+        """``tpm_plan_autotune``: keeps the fastest group size; returns (G, ms)."""
+        n_req, sys_arr, off, par = self._args(systems, offsets, params)
+        g, ms = C.c_int(), C.c_float()
+        _check(_lib.tpm_plan_autotune(self.ctx._h, self._h, n_req, sys_arr, off.ctypes.data, par, _ptr(ids),
+                                      _ptr(a_old), _ptr(acc), _ptr(pot), _ptr(n_int),
+                                      BATCH_PRESORTED if presorted else 0, int(reps),
+                                      _stream(stream, self.ctx.device), C.byref(g), C.byref(ms)))
+        return g.value, ms.value
+
+    def sync_status(self, stream=None):
+        _check(_lib.tpm_plan_sync_status(self.ctx._h, self._h, _stream(stream, self.ctx.device)))
+
+
 class Context:
     """A libtreepm context on one CUDA device (``tpm_create``)."""
 
@@ -178,6 +257,9 @@ class Context:
         used, budget = C.c_size_t(), C.c_size_t()
         _check(_lib.tpm_memory(self._h, C.byref(used), C.byref(budget)))
         return used.value, budget.value
+
+    def create_plan(self, max_ids: int, max_requests: int) -> Plan:
+        return Plan(self, max_ids, max_requests)
 
     def build_tree(self, pos, mass, params: BuildParams, stream=None) -> "System":
         """``tpm_build_tree``: pos (n, 3) float64, mass (n,) float32, on host or device."""

@@ -164,6 +164,15 @@ struct WalkRequest {
 
 int walk_device(Ctx *c, const System *s, const tpm_force_params *p, const WalkRequest &r, cudaStream_t st);
 
+// Batched walk (open boundaries): request descriptors are opaque records of
+// batch_req_bytes() bytes filled by fill_batch_req; groups are (start, count,
+// request, 0) over the sorted active list.
+size_t batch_req_bytes();
+void fill_batch_req(void *dst, const System *s, const tpm_force_params *p);
+int launch_walk_batch(Ctx *c, const void *reqs, const uint4 *groups, const unsigned *n_groups, unsigned *next,
+                      const uint32_t *sidx, const uint32_t *slot, const float *a_old, float *acc, float *pot,
+                      uint32_t *nint, int *err, cudaStream_t st);
+
 // Adds the CIC-interpolated mesh force and potential to acc / pot.
 int pm_interp_device(Ctx *c, const System *s, const WalkRequest &r, cudaStream_t st);
 

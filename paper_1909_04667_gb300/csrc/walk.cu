@@ -370,69 +370,108 @@ __device__ __forceinline__ void newton_term(float rx, float ry, float rz, float 
 }
 
 // Node entries accepted by every particle of the group sit at the front of the
-// node queue: no lane masks; two entries per step, one softening vote per
-// step, so that the two pair terms interleave.
+// node queue: no lane masks, straight-line Newtonian terms four at a time.
+// An entry closer than the softening length h contributes nothing in this
+// pass (its mass is zeroed, its distance replaced by h so rsqrt stays finite)
+// and gets its spline term in a second pass, taken only when some lane met
+// such an entry.
 template <bool PERIODIC, bool TREEPM>
 __device__ __forceinline__ void sweep_full(const GroupShared &sh, int nf, float xox, float xoy, float xoz,
                                            const WalkConsts &k, float &ax, float &ay, float &az, float &ph) {
-    int e = 0;
-    for (; e + 1 < nf; e += 2) {
-        const float4 A = sh.nsrc[e], B = sh.nsrc[e + 1];
-        float ax0 = A.x - xox, ay0 = A.y - xoy, az0 = A.z - xoz;
-        float ax1 = B.x - xox, ay1 = B.y - xoy, az1 = B.z - xoz;
-        if (PERIODIC && (sh.nwrap[e] | sh.nwrap[e + 1])) {
-            ax0 = wrap_min_image(ax0, k);
-            ay0 = wrap_min_image(ay0, k);
-            az0 = wrap_min_image(az0, k);
-            ax1 = wrap_min_image(ax1, k);
-            ay1 = wrap_min_image(ay1, k);
-            az1 = wrap_min_image(az1, k);
+    if (TREEPM || PERIODIC) {
+        for (int e = 0; e < nf; e++) {
+            const float4 A = sh.nsrc[e];
+            float rx = A.x - xox, ry = A.y - xoy, rz = A.z - xoz;
+            if (PERIODIC && sh.nwrap[e]) {
+                rx = wrap_min_image(rx, k);
+                ry = wrap_min_image(ry, k);
+                rz = wrap_min_image(rz, k);
+            }
+            pair_term<TREEPM>(rx, ry, rz, fmaf(rx, rx, fmaf(ry, ry, rz * rz)), A.w, k, ax, ay, az, ph);
         }
-        const float r20 = fmaf(ax0, ax0, fmaf(ay0, ay0, az0 * az0));
-        const float r21 = fmaf(ax1, ax1, fmaf(ay1, ay1, az1 * az1));
-        if (!TREEPM && __all_sync(0xffffffffu, fminf(r20, r21) >= k.h2)) {
-            newton_term(ax0, ay0, az0, r20, A.w, ax, ay, az, ph);
-            newton_term(ax1, ay1, az1, r21, B.w, ax, ay, az, ph);
-        } else {
-            pair_term<TREEPM>(ax0, ay0, az0, r20, A.w, k, ax, ay, az, ph);
-            pair_term<TREEPM>(ax1, ay1, az1, r21, B.w, k, ax, ay, az, ph);
+        return;
+    }
+    bool soft = false;
+    int e = 0;
+    for (; e + 3 < nf; e += 4) {
+        float4 A[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+            A[u] = sh.nsrc[e + u];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const float rx = A[u].x - xox, ry = A[u].y - xoy, rz = A[u].z - xoz;
+            const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+            const bool sf = r2 < k.h2;
+            soft |= sf;
+            newton_term(rx, ry, rz, sf ? k.h2 : r2, sf ? 0.0f : A[u].w, ax, ay, az, ph);
         }
     }
-    if (e < nf) {
+    for (; e < nf; e++) {
         const float4 A = sh.nsrc[e];
-        float rx = A.x - xox, ry = A.y - xoy, rz = A.z - xoz;
-        if (PERIODIC && sh.nwrap[e]) {
-            rx = wrap_min_image(rx, k);
-            ry = wrap_min_image(ry, k);
-            rz = wrap_min_image(rz, k);
+        const float rx = A.x - xox, ry = A.y - xoy, rz = A.z - xoz;
+        const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+        const bool sf = r2 < k.h2;
+        soft |= sf;
+        newton_term(rx, ry, rz, sf ? k.h2 : r2, sf ? 0.0f : A.w, ax, ay, az, ph);
+    }
+    if (__any_sync(0xffffffffu, soft)) {
+        for (int q = 0; q < nf; q++) {
+            const float4 A = sh.nsrc[q];
+            const float rx = A.x - xox, ry = A.y - xoy, rz = A.z - xoz;
+            const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+            if (r2 < k.h2)
+                pair_term<false>(rx, ry, rz, r2, A.w, k, ax, ay, az, ph);
         }
-        pair_term<TREEPM>(rx, ry, rz, fmaf(rx, rx, fmaf(ry, ry, rz * rz)), A.w, k, ax, ay, az, ph);
     }
 }
 
 // Node entries for a subset of the lanes sit at the back of the node queue
-// (indices [kNodeCap - np, kNodeCap)): lanes not tagged add a zero mass.
+// (indices [kNodeCap - np, kNodeCap)): a lane not tagged adds a zero mass
+// (with r2 replaced by h2, since such a lane may sit on the node), and
+// entries inside the softening length are repaired as in sweep_full.
 template <bool PERIODIC, bool TREEPM>
 __device__ __forceinline__ void sweep_partial(const GroupShared &sh, int np, unsigned lanebit, float xox, float xoy,
                                               float xoz, const WalkConsts &k, float &ax, float &ay, float &az,
                                               float &ph, uint32_t &cnt) {
-    for (int e = kNodeCap - np; e < kNodeCap; e++) {
+    const int e0 = kNodeCap - np;
+    if (TREEPM || PERIODIC) {
+        for (int e = e0; e < kNodeCap; e++) {
+            const float4 E = sh.nsrc[e];
+            const bool mine = (sh.nmask[e] & lanebit) != 0u;
+            float rx = E.x - xox, ry = E.y - xoy, rz = E.z - xoz;
+            if (PERIODIC && sh.nwrap[e]) {
+                rx = wrap_min_image(rx, k);
+                ry = wrap_min_image(ry, k);
+                rz = wrap_min_image(rz, k);
+            }
+            const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+            cnt += mine ? 1u : 0u;
+            pair_term<TREEPM>(rx, ry, rz, mine ? r2 : 1.0f, mine ? E.w : 0.0f, k, ax, ay, az, ph);
+        }
+        return;
+    }
+    bool soft = false;
+#pragma unroll 2
+    for (int e = e0; e < kNodeCap; e++) {
         const float4 E = sh.nsrc[e];
         const bool mine = (sh.nmask[e] & lanebit) != 0u;
-        float rx = E.x - xox, ry = E.y - xoy, rz = E.z - xoz;
-        if (PERIODIC && sh.nwrap[e]) {
-            rx = wrap_min_image(rx, k);
-            ry = wrap_min_image(ry, k);
-            rz = wrap_min_image(rz, k);
-        }
-        float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-        r2 = mine ? r2 : 1.0f;  // a lane not tagged may sit on the node: keep rsqrt finite
-        const float m = mine ? E.w : 0.0f;
+        const float rx = E.x - xox, ry = E.y - xoy, rz = E.z - xoz;
+        const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+        const bool sf = r2 < k.h2;
+        soft |= mine && sf;
+        const bool use = mine && !sf;
         cnt += mine ? 1u : 0u;
-        if (!TREEPM && __all_sync(0xffffffffu, r2 >= k.h2))
-            newton_term(rx, ry, rz, r2, m, ax, ay, az, ph);
-        else
-            pair_term<TREEPM>(rx, ry, rz, r2, m, k, ax, ay, az, ph);
+        newton_term(rx, ry, rz, use ? r2 : k.h2, use ? E.w : 0.0f, ax, ay, az, ph);
+    }
+    if (__any_sync(0xffffffffu, soft)) {
+        for (int e = e0; e < kNodeCap; e++) {
+            const float4 E = sh.nsrc[e];
+            const float rx = E.x - xox, ry = E.y - xoy, rz = E.z - xoz;
+            const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+            if ((sh.nmask[e] & lanebit) && r2 < k.h2)
+                pair_term<false>(rx, ry, rz, r2, E.w, k, ax, ay, az, ph);
+        }
     }
 }
 
@@ -474,26 +513,41 @@ __device__ __forceinline__ void sweep_leaves(const GroupShared &sh, int nl, unsi
     }
 }
 
+// A tree as the group walk sees it (breadth-first node records, leaf
+// particles, keys and positions).
+struct TreeView {
+    const float4 *bcen, *bcom;
+    const int4 *blink;
+    const float4 *spart;
+    const uint64_t *key;
+    const uint32_t *perm;
+    const double *pos;
+    double x0, y0, z0, L0;
+};
+
+// Walks the tree for the group of gcount <= 32 active particles at positions
+// [g0, g0 + gcount) of the sorted active list (one per lane).
 template <bool PERIODIC, bool RELATIVE, bool TREEPM>
-__global__ void __launch_bounds__(kGroupWarps * 32)
-    k_walk_group(const float4 *__restrict__ bcen, const float4 *__restrict__ bcom, const int4 *__restrict__ blink,
-                 const float4 *__restrict__ spart, const uint64_t *__restrict__ key,
-                 const uint32_t *__restrict__ perm, const double *__restrict__ pos, double x0, double y0, double z0,
-                 double L0, const uint32_t *__restrict__ sidx, const uint32_t *__restrict__ slot,
-                 const float *__restrict__ a_old, int64_t n_act, WalkConsts k, float *__restrict__ acc,
-                 float *__restrict__ pot, uint32_t *__restrict__ nint, int accumulate, int *__restrict__ err) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    GroupShared &sh = reinterpret_cast<GroupShared *>(smem_raw)[threadIdx.x >> 5];
+__device__ __forceinline__ void group_walk(const TreeView &T, const WalkConsts &k, GroupShared &sh,
+                                           const uint32_t *__restrict__ sidx, const uint32_t *__restrict__ slot,
+                                           int64_t g0, int gcount, const float *__restrict__ a_old,
+                                           float *__restrict__ acc, float *__restrict__ pot,
+                                           uint32_t *__restrict__ nint, int accumulate, int *__restrict__ err) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const unsigned lanebit = 1u << lane;
     const unsigned lt_mask = lanebit - 1u;
-    const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane);
-    if (g0 >= n_act)
-        return;  // whole warp
+    const double x0 = T.x0, y0 = T.y0, z0 = T.z0, L0 = T.L0;
+    const float4 *__restrict__ bcen = T.bcen;
+    const float4 *__restrict__ bcom = T.bcom;
+    const int4 *__restrict__ blink = T.blink;
+    const float4 *__restrict__ spart = T.spart;
+    const uint64_t *__restrict__ key = T.key;
+    const uint32_t *__restrict__ perm = T.perm;
+    const double *__restrict__ pos = T.pos;
     const int64_t gi = g0 + lane;
-    const bool valid = gi < n_act;
-    const int64_t glast = min(g0 + 31, n_act - 1);
+    const bool valid = lane < gcount;
+    const int64_t glast = g0 + gcount - 1;
     const uint32_t s = sidx ? sidx[valid ? gi : g0] : (uint32_t)(valid ? gi : g0);
     const uint32_t s_first = sidx ? sidx[g0] : (uint32_t)g0;
     const uint32_t s_last = sidx ? sidx[glast] : (uint32_t)glast;
@@ -746,6 +800,62 @@ __global__ void __launch_bounds__(kGroupWarps * 32)
         nint[out] = cnt;
 }
 
+
+// One warp per group of `gsize` consecutive active particles.
+template <bool PERIODIC, bool RELATIVE, bool TREEPM>
+__global__ void __launch_bounds__(kGroupWarps * 32)
+    k_walk_group(TreeView T, const uint32_t *__restrict__ sidx, const uint32_t *__restrict__ slot,
+                 const float *__restrict__ a_old, int64_t n_act, int gsize, WalkConsts k, float *__restrict__ acc,
+                 float *__restrict__ pot, uint32_t *__restrict__ nint, int accumulate, int *__restrict__ err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    GroupShared &sh = reinterpret_cast<GroupShared *>(smem_raw)[threadIdx.x >> 5];
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t g0 = warp * gsize;
+    if (g0 >= n_act)
+        return;  // whole warp
+    const int gcount = (int)min((int64_t)gsize, n_act - g0);
+    group_walk<PERIODIC, RELATIVE, TREEPM>(T, k, sh, sidx, slot, g0, gcount, a_old, acc, pot, nint, accumulate, err);
+}
+
+// One request of a batch: which tree, with which constants and criterion.
+struct BatchReq {
+    TreeView T;
+    WalkConsts k;
+    int relative;
+};
+
+// Persistent batch walk: resident warps take groups (start, count, request)
+// from a device work queue until it is empty; groups of one launch may
+// belong to different requests and different trees.
+template <bool PERIODIC, bool TREEPM>
+__global__ void __launch_bounds__(kGroupWarps * 32)
+    k_walk_batch(const BatchReq *__restrict__ reqs, const uint4 *__restrict__ groups,
+                 const unsigned *__restrict__ n_groups, unsigned *__restrict__ next, const uint32_t *__restrict__ sidx,
+                 const uint32_t *__restrict__ slot, const float *__restrict__ a_old, float *__restrict__ acc,
+                 float *__restrict__ pot, uint32_t *__restrict__ nint, int *__restrict__ err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    GroupShared &sh = reinterpret_cast<GroupShared *>(smem_raw)[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const unsigned total = *n_groups;
+    for (;;) {
+        unsigned g = 0;
+        if (lane == 0)
+            g = atomicAdd(next, 1u);
+        g = __shfl_sync(0xffffffffu, g, 0);
+        if (g >= total)
+            break;
+        const uint4 G = groups[g];
+        const BatchReq &R = reqs[G.z];
+        const TreeView T = R.T;
+        const WalkConsts k = R.k;
+        if (R.relative)
+            group_walk<PERIODIC, true, TREEPM>(T, k, sh, sidx, slot, G.x, (int)G.y, a_old, acc, pot, nint, 0, err);
+        else
+            group_walk<PERIODIC, false, TREEPM>(T, k, sh, sidx, slot, G.x, (int)G.y, a_old, acc, pot, nint, 0, err);
+        __syncwarp();
+    }
+}
+
 template <bool P, bool R, bool T>
 void launch(const System *s, const WalkRequest &r, const WalkConsts &k, bool lanes, int *err, cudaStream_t st) {
     const int64_t warps = (r.n_act + 31) / 32;
@@ -758,9 +868,9 @@ void launch(const System *s, const WalkRequest &r, const WalkConsts &k, bool lan
     } else {
         const int64_t blocks = (warps + kGroupWarps - 1) / kGroupWarps;
         const size_t smem = kGroupWarps * sizeof(GroupShared);
+        TreeView tv{s->bcen, s->bcom, s->blink, s->spart, s->key, s->perm, s->pos, s->x0[0], s->x0[1], s->x0[2], s->L0};
         k_walk_group<P, R, T><<<(unsigned)blocks, kGroupWarps * 32, smem, st>>>(
-            s->bcen, s->bcom, s->blink, s->spart, s->key, s->perm, s->pos, s->x0[0], s->x0[1], s->x0[2], s->L0,
-            r.sorted_idx, r.slot, r.a_old, r.n_act, k, r.acc, r.pot, r.nint, r.accumulate, err);
+            tv, r.sorted_idx, r.slot, r.a_old, r.n_act, 32, k, r.acc, r.pot, r.nint, r.accumulate, err);
         count_launch();
     }
 }
@@ -779,11 +889,7 @@ int walk_override() {
     return v;
 }
 
-}  // namespace
-
-int walk_device(Ctx *, const System *s, const tpm_force_params *p, const WalkRequest &r, cudaStream_t st) {
-    if (r.n_act == 0)
-        return TPM_OK;
+WalkConsts make_consts(const System *s, const tpm_force_params *p) {
     WalkConsts k{};
     const double h = s->bp.h;
     k.h2 = (float)(h * h);
@@ -802,6 +908,43 @@ int walk_device(Ctx *, const System *s, const tpm_force_params *p, const WalkReq
         k.rcut2 = (float)(rc * rc);
         k.inv2rs = (float)(1.0 / (2.0 * rs));
     }
+    return k;
+}
+
+}  // namespace
+
+size_t batch_req_bytes() { return sizeof(BatchReq); }
+
+void fill_batch_req(void *dst, const System *s, const tpm_force_params *p) {
+    BatchReq r{};
+    r.T = TreeView{s->bcen, s->bcom, s->blink, s->spart, s->key, s->perm, s->pos, s->x0[0], s->x0[1], s->x0[2], s->L0};
+    r.k = make_consts(s, p);
+    r.relative = p->crit == TPM_CRIT_RELATIVE ? 1 : 0;
+    memcpy(dst, &r, sizeof r);
+}
+
+int launch_walk_batch(Ctx *c, const void *reqs, const uint4 *groups, const unsigned *n_groups, unsigned *next,
+                      const uint32_t *sidx, const uint32_t *slot, const float *a_old, float *acc, float *pot,
+                      uint32_t *nint, int *err, cudaStream_t st) {
+    const size_t smem = kGroupWarps * sizeof(GroupShared);
+    static int blocks_per_sm = 0;
+    if (!blocks_per_sm) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_walk_batch<false, false>,
+                                                          kGroupWarps * 32, smem) != cudaSuccess ||
+            blocks_per_sm < 1)
+            blocks_per_sm = 1;
+    }
+    k_walk_batch<false, false><<<(unsigned)(c->num_sms * blocks_per_sm), kGroupWarps * 32, smem, st>>>(
+        static_cast<const BatchReq *>(reqs), groups, n_groups, next, sidx, slot, a_old, acc, pot, nint, err);
+    count_launch();
+    TPM_CUDA(cudaGetLastError());
+    return TPM_OK;
+}
+
+int walk_device(Ctx *, const System *s, const tpm_force_params *p, const WalkRequest &r, cudaStream_t st) {
+    if (r.n_act == 0)
+        return TPM_OK;
+    const WalkConsts k = make_consts(s, p);
     const bool per = s->bp.periodic != 0, rel = p->crit == TPM_CRIT_RELATIVE, tpm = p->treepm != 0;
     const int ov = walk_override();
     const bool lanes = ov == 1 || (ov == 0 && tpm);

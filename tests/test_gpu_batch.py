@@ -1,0 +1,153 @@
+"""Batched evaluation (tpm_compute_forces_batch) against per-request calls.
+
+Each request of a batch must get what tpm_compute_forces gives for that
+request alone: the same per-particle decisions (interaction counts equal up to
+FP32 margin flips, at most 0.5%) and forces within the FP32 tolerance of the
+parity tests -- only the grouping of particles into warps, hence the order of
+FP32 summation, differs.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+P99_TOL = 2e-5
+MAX_TOL = 2e-4
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b, axis=1) / np.maximum(np.linalg.norm(b, axis=1), 1e-300)
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    import paper_1909_04667_gb300 as tpm
+
+    dev = torch.device("cuda", 0)
+    ctx = tpm.Context(0)
+    p1, m1 = W.plummer(20000, 5)
+    p2, m2 = W.hernquist(60000, 6)
+    s1 = ctx.build_tree(torch.from_numpy(p1).to(dev), torch.from_numpy(m1).to(dev),
+                        tpm.BuildParams(G=1.0, h=0.01, shift=tuple(W.root_shift(5)), leaf_bucket=8))
+    s2 = ctx.build_tree(torch.from_numpy(p2).to(dev), torch.from_numpy(m2).to(dev),
+                        tpm.BuildParams(G=1.0, h=0.005, shift=tuple(W.root_shift(6)), leaf_bucket=8))
+    # |a_old| from a geometric pass
+    aold = {}
+    for s in (s1, s2):
+        a, _, _ = s.compute_forces(fp=tpm.ForceParams(theta=0.5))
+        aold[s.handle] = torch.linalg.vector_norm(a, dim=1).contiguous()
+    rng = np.random.default_rng(3)
+    reqs = []
+    for r in range(9):  # uneven sizes, both systems, both criteria, unsorted ids
+        s = (s1, s2)[r % 2]
+        size = int(rng.integers(1, 5000)) if r != 4 else 1
+        ids = rng.choice(s.n, size, replace=False).astype(np.int32)
+        fp = tpm.ForceParams(theta=0.6) if r % 3 else tpm.ForceParams(crit=tpm.CRIT_RELATIVE, alpha=0.002)
+        reqs.append((s, ids, fp))
+    yield tpm, torch, dev, ctx, reqs, aold
+    ctx.close()
+
+
+def batch_inputs(torch, dev, reqs, aold):
+    ids = np.concatenate([r[1] for r in reqs])
+    off = np.concatenate([[0], np.cumsum([len(r[1]) for r in reqs])])
+    a_old = torch.cat([aold[s.handle][torch.from_numpy(i.astype(np.int64)).to(dev)] for s, i, _ in reqs])
+    return torch.from_numpy(ids).to(dev), off, a_old
+
+
+def reference(tpm, torch, dev, reqs, aold):
+    out = []
+    for s, ids, fp in reqs:
+        ti = torch.from_numpy(ids).to(dev)
+        a, p, n = s.compute_forces(active_ids=ti, a_old=aold[s.handle][ti.long()].contiguous(), fp=fp)
+        out.append((a.cpu().numpy(), p.cpu().numpy(), n.cpu().numpy()))
+    return out
+
+
+def check(ref, acc, pot, nint, off):
+    for r, (a, p, n) in enumerate(ref):
+        sl = slice(off[r], off[r + 1])
+        same = nint[sl] == n
+        assert np.mean(~same) <= 0.005 or (~same).sum() <= 1
+        e = rel(acc[sl].astype(np.float64), a.astype(np.float64))
+        assert np.percentile(e[same], 99) <= P99_TOL and e[same].max() <= MAX_TOL
+        np.testing.assert_allclose(pot[sl][same], p[same], rtol=P99_TOL)
+
+
+@pytest.mark.parametrize("group", [32, 16, 8])
+def test_batch_matches_per_request_calls(env, group):
+    tpm, torch, dev, ctx, reqs, aold = env
+    ids, off, a_old = batch_inputs(torch, dev, reqs, aold)
+    plan = ctx.create_plan(int(off[-1]) + 100, 16)
+    plan.group_size = group
+    acc = torch.empty((len(ids), 3), device=dev)
+    pot = torch.empty(len(ids), device=dev)
+    nint = torch.empty(len(ids), dtype=torch.int32, device=dev)
+    plan.compute_forces_batch([r[0] for r in reqs], off, [r[2] for r in reqs], ids, acc, a_old=a_old, pot=pot,
+                              n_int=nint)
+    plan.sync_status()
+    check(reference(tpm, torch, dev, reqs, aold), acc.cpu().numpy(), pot.cpu().numpy(), nint.cpu().numpy(), off)
+    plan.close()
+
+
+def test_batch_presorted_and_graph_replay(env):
+    tpm, torch, dev, ctx, reqs, aold = env
+    # ids in each tree's key order: the presorted flag skips the sort
+    sorted_reqs = []
+    for s, ids, fp in reqs:
+        perm = s.tree_export()["perm"]
+        rank = np.empty(s.n, np.int64)
+        rank[perm] = np.arange(s.n)
+        sorted_reqs.append((s, ids[np.argsort(rank[ids])], fp))
+    ids, off, a_old = batch_inputs(torch, dev, sorted_reqs, aold)
+    plan = ctx.create_plan(int(off[-1]), len(reqs))
+    acc = torch.zeros((len(ids), 3), device=dev)
+    nint = torch.zeros(len(ids), dtype=torch.int32, device=dev)
+    args = ([r[0] for r in sorted_reqs], off, [r[2] for r in sorted_reqs], ids, acc)
+    plan.compute_forces_batch(*args, a_old=a_old, n_int=nint, presorted=True)
+    torch.cuda.synchronize()
+    eager = (acc.cpu().numpy().copy(), nint.cpu().numpy().copy())
+    ref = reference(tpm, torch, dev, sorted_reqs, aold)
+    for r, (a, p, n) in enumerate(ref):
+        sl = slice(off[r], off[r + 1])
+        assert np.mean(eager[1][sl] != n) <= 0.005 or (eager[1][sl] != n).sum() <= 1
+    # capture the batched call in a CUDA graph and replay it
+    g = torch.cuda.CUDAGraph()
+    acc.zero_()
+    nint.zero_()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            plan.compute_forces_batch(*args, a_old=a_old, n_int=nint, presorted=True)
+    torch.cuda.current_stream().wait_stream(s)
+    for _ in range(2):
+        acc.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(acc.cpu().numpy(), eager[0])
+        np.testing.assert_array_equal(nint.cpu().numpy(), eager[1])
+    plan.sync_status()
+    plan.close()
+
+
+def test_autotune_and_errors(env):
+    tpm, torch, dev, ctx, reqs, aold = env
+    ids, off, a_old = batch_inputs(torch, dev, reqs, aold)
+    plan = ctx.create_plan(int(off[-1]), len(reqs))
+    acc = torch.empty((len(ids), 3), device=dev)
+    g, ms = plan.autotune([r[0] for r in reqs], off, [r[2] for r in reqs], ids, acc, a_old=a_old, reps=2)
+    assert g in (8, 16, 32) and plan.group_size == g and ms > 0
+    with pytest.raises(tpm.TreePMError, match="TPM_EINVAL"):  # more requests than the plan holds
+        plan.compute_forces_batch([reqs[0][0]] * (len(reqs) + 1), np.zeros(len(reqs) + 2, np.int64),
+                                  tpm.ForceParams(), ids, acc)
+    bad = ids.clone()
+    bad[0] = 10 ** 9
+    plan.compute_forces_batch([r[0] for r in reqs], off, [r[2] for r in reqs], bad, acc, a_old=a_old)
+    with pytest.raises(tpm.TreePMError, match="out of range"):
+        plan.sync_status()
+    plan.close()
