@@ -39,6 +39,9 @@ FLOPS_PER_INTERACTION = 20  # monopole pair term, FP32 (offset 3, r^2 5 flops...
 
 # ------------------------------------------------------------------ configs
 HERNQUIST = dict(n=1 << 20, seed=W.CONFIG_SEEDS[2], h=0.005, G=1.0, bucket=8, theta=0.5, alpha=0.0025)
+SERVING = dict(seed=W.CONFIG_SEEDS[5], n_systems=48, n_requests=600, rate=200.0, nmin=1 << 12, nmax=1 << 20,
+               overcommit=1.5, bytes_per_particle=118, round_ids=1 << 21)
+TIMEBINS = dict(nbins=8, seed=W.CONFIG_SEEDS[4], req_lo=64, req_hi=65536)
 ZELDOVICH = dict(ngrid=128, seed=W.CONFIG_SEEDS[3], pm_n=256, asmth=1.25, rcut=4.5, G=1.0, bucket=8, theta=0.5,
                  alpha=0.005)
 
@@ -214,8 +217,10 @@ def run_ours(args, rank, world):
     # ---------------- periodic TreePM box (128^3, PM 256^3)
     periodic = None if args.no_periodic else run_periodic(ctx, tpm, torch, dev, stream, flush,
                                                           max(2, min(args.steps, 5)))
+    batching = None if args.no_batching else run_batching(ctx, tpm, torch, dev, stream, pos_d, mass_d)
 
     ctx.close()
+    serving = None if args.no_serving else run_serving(tpm, torch, dev)
     pk, pk_kind = peaks()
     sm_max = pk.get("sm_max_mhz", 2070.0)
     fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
@@ -246,7 +251,165 @@ def run_ours(args, rank, world):
         cub_calls=int(c1 - c0),
         clocks=clocks,
         periodic_treepm=periodic,
+        batching=batching,
+        serving=serving,
     )
+
+
+def timebin_requests(perm, bins, seed):
+    """Requests of one 2^(nbins-1)-substep cycle: each substep's active set
+    (bins >= the substep's lowest active bin), in key order, cut into
+    log-uniform request sizes.  Returns (ids, offsets, substep of each request)."""
+    nb = TIMEBINS["nbins"]
+    keyed_bins = bins[perm]
+    ids, sizes, subs = [], [], []
+    for step in range(1 << (nb - 1)):
+        act = perm[keyed_bins >= W.substep_active_bins(step, nb)]
+        sz = W.request_sizes(len(act), seed + step, TIMEBINS["req_lo"], TIMEBINS["req_hi"])
+        ids.append(act)
+        sizes.append(sz)
+        subs += [step] * len(sz)
+    ids = np.concatenate(ids).astype(np.int32)
+    off = np.concatenate([[0], np.cumsum(np.concatenate(sizes))])
+    return ids, off, np.asarray(subs)
+
+
+def run_batching(ctx, tpm, torch, dev, stream, pos_d, mass_d, reps=3):
+    """Hierarchical time-step batching on the Hernquist 2^20 set: one tree, the
+    requests of one 128-substep cycle as (a) one compute_forces call each and
+    (b) one autotuned batch captured in a CUDA graph."""
+    cfg = HERNQUIST
+    n = pos_d.shape[0]
+    sy = ctx.build_tree(pos_d, mass_d, tpm.BuildParams(G=cfg["G"], h=cfg["h"], shift=root_shift(7, 4),
+                                                       leaf_bucket=cfg["bucket"]))
+    a, _, _ = sy.compute_forces(fp=tpm.ForceParams(crit=tpm.CRIT_BH, theta=cfg["theta"]))
+    a_full = torch.linalg.vector_norm(a, dim=1).contiguous()
+    perm = sy.tree_export()["perm"].astype(np.int64)
+    pos = pos_d.cpu().numpy()
+    bins = W.timebins(pos, TIMEBINS["seed"], TIMEBINS["nbins"])
+    ids, off, subs = timebin_requests(perm, bins, TIMEBINS["seed"])
+    n_ids, n_req = len(ids), len(off) - 1
+    ids_d = torch.from_numpy(ids).to(dev)
+    aold = a_full[ids_d.long()].contiguous()
+    acc = torch.empty((n_ids, 3), device=dev)
+    pot = torch.empty(n_ids, device=dev)
+    nint = torch.empty(n_ids, dtype=torch.int32, device=dev)
+    fp = tpm.ForceParams(crit=tpm.CRIT_RELATIVE, alpha=cfg["alpha"])
+    # (a) one call per request
+    def per_request():
+        for r in range(n_req):
+            lo, hi = int(off[r]), int(off[r + 1])
+            sy.compute_forces(active_ids=ids_d[lo:hi], a_old=aold[lo:hi], fp=fp, acc=acc[lo:hi], pot=pot[lo:hi],
+                              n_int=nint[lo:hi])
+    per_request()
+    torch.cuda.synchronize()
+    t_req = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        per_request()
+        torch.cuda.synchronize()
+        t_req.append((time.perf_counter() - t0) * 1e3)
+    ref = acc.cpu().numpy().copy()
+    # (b) one batch per cycle, autotuned, in a CUDA graph
+    plan = ctx.create_plan(n_ids, n_req)
+    systems = [sy] * n_req
+    g_best, ms_tune = plan.autotune(systems, off, fp, ids_d, acc, a_old=aold, pot=pot, n_int=nint, presorted=True,
+                                    reps=2)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side):
+            plan.compute_forces_batch(systems, off, fp, ids_d, acc, a_old=aold, pot=pot, n_int=nint,
+                                      presorted=True)
+    torch.cuda.current_stream().wait_stream(side)
+    graph.replay()
+    torch.cuda.synchronize()
+    t_b = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        graph.replay()
+        torch.cuda.synchronize()
+        t_b.append((time.perf_counter() - t0) * 1e3)
+    plan.sync_status()
+    got = acc.cpu().numpy()
+    e = np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    inter = int(nint.to(torch.int64).sum().item())
+    plan.close()
+    sy.release()
+    ms_req, ms_b = statistics.median(t_req), statistics.median(t_b)
+    return {"workload": "hernquist_n2^20_timebins8_cycle128_requests64-65536", "forces_per_cycle": n_ids,
+            "requests_per_cycle": n_req, "interactions_per_force": inter / n_ids,
+            "per_request_launches": {"ms_per_cycle": ms_req, "forces_per_s": n_ids / (ms_req * 1e-3)},
+            "batched_graph": {"ms_per_cycle": ms_b, "forces_per_s": n_ids / (ms_b * 1e-3), "group_size": g_best,
+                              "launch": "one persistent walk per cycle, captured in a CUDA graph"},
+            "speedup": ms_req / ms_b, "max_rel_diff_vs_per_request": float(e.max())}
+
+
+def serving_workload(torch):
+    """Catalogue (host particles, pinned), and the request stream."""
+    cfg = SERVING
+    cat = W.serving_catalogue(cfg["n_systems"], cfg["seed"], cfg["nmin"], cfg["nmax"])
+    parts = {}
+    for spec in cat:
+        pos, mass = spec.particles()
+        parts[spec.sid] = (torch.from_numpy(pos).pin_memory(), torch.from_numpy(mass).pin_memory(), spec)
+    rng = np.random.Generator(np.random.PCG64(cfg["seed"] + 1))
+    arrivals = W.poisson_arrivals(cfg["n_requests"], cfg["rate"], cfg["seed"] + 2)
+    reqs = []
+    for k, t in enumerate(arrivals):
+        sid = int(rng.integers(0, len(cat)))
+        n = cat[sid].n
+        m = max(1, int(n * rng.uniform(0.01, 1.0)))
+        reqs.append((k, sid, np.sort(rng.choice(n, m, replace=False)).astype(np.int32), float(t)))
+    footprint = sum(s.n for s in cat) * cfg["bytes_per_particle"]
+    return cat, parts, reqs, footprint
+
+
+def run_serving(tpm, torch, dev):
+    """Continuous-batching server vs one call per request, on the same budget."""
+    from paper_1909_04667_gb300.serve import ForceServer, ServeRequest, serve_per_request
+
+    cfg = SERVING
+    cat, parts, reqs, footprint = serving_workload(torch)
+    # resident trees ~118 B per particle; the budget holds 1/1.5 of the
+    # catalogue plus the round plan (~30 B per id) and the largest build's peak
+    budget = int(footprint / cfg["overcommit"]) + 30 * cfg["round_ids"] + (200 << 20)
+
+    def source(sid):
+        pos, mass, spec = parts[sid]
+        return pos, mass, tpm.BuildParams(G=1.0, h=spec.h, shift=tuple(W.root_shift(spec.seed)), leaf_bucket=8)
+
+    def make():
+        return [ServeRequest(k, sid, ids, t) for k, sid, ids, t in reqs]
+
+    def stats(out, wall):
+        lat = np.array([r.latency for r in out]) * 1e3
+        forces = sum(len(r.ids) for r in out)
+        return {"forces_per_s": forces / wall, "latency_ms_p50": float(np.percentile(lat, 50)),
+                "latency_ms_p99": float(np.percentile(lat, 99)), "makespan_s": wall,
+                "relative_criterion_share": float(np.mean([r.criterion == tpm.CRIT_RELATIVE for r in out]))}
+
+    res = {}
+    ctx = tpm.Context(dev.index, budget_bytes=budget)
+    srv = ForceServer(ctx, source, max_round_ids=cfg["round_ids"], max_round_requests=512, policy="adaptive")
+    srv.serve(make()[:20], realtime=False)  # warm-up (builds, module loading)
+    srv.close()
+    srv = ForceServer(ctx, source, max_round_ids=cfg["round_ids"], max_round_requests=512, policy="adaptive")
+    t0 = time.perf_counter()
+    out = srv.serve(make(), realtime=True)
+    res["continuous_batching"] = dict(stats(out, time.perf_counter() - t0), builds=srv.builds,
+                                      evictions=srv.evictions)
+    srv.close()
+    t0 = time.perf_counter()
+    out = serve_per_request(ctx, source, make(), policy="adaptive", realtime=True)
+    res["per_request"] = stats(out, time.perf_counter() - t0)
+    ctx.close()
+    res.update(workload="serving_%d_systems_N2^12-2^20_poisson%dHz_%d_requests" % (
+        cfg["n_systems"], int(cfg["rate"]), cfg["n_requests"]), hbm_budget_bytes=budget,
+        catalogue_bytes=footprint)
+    return res
 
 
 def run_periodic(ctx, tpm, torch, dev, stream, flush, steps):
@@ -366,6 +529,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
     ap.add_argument("--no-periodic", action="store_true", help="skip the periodic TreePM measurement")
     ap.add_argument("--bucket", type=int, default=None, help="leaf bucket B of the headline workload")
+    ap.add_argument("--no-batching", action="store_true", help="skip the time-bin batching measurement")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     args = ap.parse_args()
     if args.bucket:
         HERNQUIST["bucket"] = args.bucket

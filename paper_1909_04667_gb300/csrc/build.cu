@@ -518,7 +518,8 @@ int build_tree_device(Ctx *c, System *s, const double *pos_in, const float *mass
 
     // ---- levels and monopoles, all on the device; retried with more node
     // space in the rare case the first guess is too small
-    unsigned cap = (unsigned)std::min<int64_t>(2 * n + 1024, 0x7fffffffLL);
+    // node space: ~0.4 n nodes for B = 8, ~1.5 n for B = 1; an overflow retries
+    unsigned cap = (unsigned)std::min<int64_t>((B == 1 ? 2 * n : n) + 1024, 0x7fffffffLL);
     LevelArrays b{};
     double *M = nullptr, *S = nullptr;
     AllocSet lv;

@@ -1,0 +1,283 @@
+"""Continuous-batching force server over device-resident trees.
+
+A request asks for the forces on a subset of one system's particles.  The
+server keeps the trees of recently used systems resident on the GPU under the
+context's HBM budget and serves requests in rounds: all requests that have
+arrived while the previous round was on the GPU are admitted (as long as the
+plan's slots last and their trees fit in memory), their missing trees are
+built on a second stream -- overlapping the walk still in flight -- and the
+whole round runs as one batched walk launch (``tpm_compute_forces_batch``).
+When memory runs short, resident systems that no request in flight needs are
+evicted, least recently used first.
+
+The first request for a system uses the geometric criterion; later requests
+use the relative criterion (paper Sec. 3.1) when every requested particle has
+an |a| from an earlier evaluation, unless the server runs with a fixed
+criterion.  ``serve_per_request`` is the plain baseline: one build (if
+needed), one ``tpm_compute_forces`` call and one synchronisation per request,
+in arrival order.
+"""
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import CRIT_BH, CRIT_RELATIVE, BuildParams, Context, ForceParams, TreePMError
+
+_EBUDGET = -2
+
+
+@dataclass
+class ServeRequest:
+    """Forces on particles ``ids`` of system ``sid`` (arrival in seconds)."""
+
+    rid: int
+    sid: int
+    ids: np.ndarray
+    arrival: float = 0.0
+    acc: np.ndarray = None
+    pot: np.ndarray = None
+    n_int: np.ndarray = None
+    criterion: int = -1
+    t_done: float = float("nan")
+
+    @property
+    def latency(self) -> float:
+        return self.t_done - self.arrival
+
+
+@dataclass
+class _Resident:
+    system: object
+    aold: object          # torch float32 (n,), on the device
+    aold_valid: object    # numpy bool (n,), on the host: which particles have an |a|
+    inflight: int = 0
+
+
+@dataclass
+class _Round:
+    reqs: list
+    acc: object
+    pot: object
+    nint: object
+    offsets: np.ndarray
+    event: object
+    sids: list = field(default_factory=list)
+
+
+class ForceServer:
+    """Serves ``ServeRequest``s for systems described by ``source(sid)``, which
+    returns ``(pos float64 (n,3), mass float32 (n,), BuildParams)`` as host
+    arrays (pinned memory keeps the uploads asynchronous)."""
+
+    def __init__(self, ctx: Context, source, max_round_ids: int = 1 << 21, max_round_requests: int = 512,
+                 theta: float = 0.5, alpha: float = 0.0025, policy: str = "adaptive", group_size: int = None):
+        import torch
+
+        self.torch = torch
+        self.ctx = ctx
+        self.source = source
+        self.plan = ctx.create_plan(max_round_ids, max_round_requests)
+        if group_size:
+            self.plan.group_size = group_size
+        self.max_ids, self.max_req = int(max_round_ids), int(max_round_requests)
+        self.theta, self.alpha, self.policy = theta, alpha, policy
+        self.dev = torch.device("cuda", ctx.device)
+        self.walk_stream = torch.cuda.Stream(self.dev)
+        self.build_stream = torch.cuda.Stream(self.dev)
+        self.resident: "collections.OrderedDict[int, _Resident]" = collections.OrderedDict()
+        self.builds = 0
+        self.evictions = 0
+
+    def close(self):
+        for r in self.resident.values():
+            r.system.release()
+        self.resident.clear()
+        self.plan.close()
+
+    # -------------------------------------------------------------- residency
+    def _evict_one(self) -> bool:
+        for sid, r in self.resident.items():  # least recently used first
+            if r.inflight == 0:
+                r.system.release()
+                del self.resident[sid]
+                self.evictions += 1
+                return True
+        return False
+
+    def ensure_resident(self, sid: int) -> bool:
+        """Builds the tree of ``sid`` on the build stream if it is not resident;
+        False if the budget cannot hold it while the systems in flight stay."""
+        torch = self.torch
+        if sid in self.resident:
+            self.resident.move_to_end(sid)
+            return True
+        pos, mass, bp = self.source(sid)
+        while True:
+            try:
+                system = self.ctx.build_tree(pos, mass, bp, stream=self.build_stream.cuda_stream)
+                break
+            except TreePMError as e:
+                if e.status != _EBUDGET or not self._evict_one():
+                    if e.status == _EBUDGET:
+                        return False
+                    raise
+        n = system.n
+        with torch.cuda.stream(self.build_stream):
+            aold = torch.zeros(n, dtype=torch.float32, device=self.dev)
+        self.resident[sid] = _Resident(system, aold, np.zeros(n, dtype=bool))
+        self.builds += 1
+        return True
+
+    # -------------------------------------------------------------- rounds
+    def _params_for(self, res: _Resident, ids) -> ForceParams:
+        if self.policy == "bh":
+            return ForceParams(crit=CRIT_BH, theta=self.theta)
+        if self.policy == "relative" or (self.policy == "adaptive" and bool(res.aold_valid[ids].all())):
+            return ForceParams(crit=CRIT_RELATIVE, alpha=self.alpha)
+        return ForceParams(crit=CRIT_BH, theta=self.theta)
+
+    def _launch(self, reqs) -> _Round:
+        torch = self.torch
+        self.walk_stream.wait_stream(self.build_stream)
+        with torch.cuda.stream(self.walk_stream):
+            sizes = [len(r.ids) for r in reqs]
+            off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+            ids_h = torch.from_numpy(np.concatenate([r.ids for r in reqs]).astype(np.int32)).pin_memory()
+            ids_d = ids_h.to(self.dev, non_blocking=True)
+            systems, params, aolds = [], [], []
+            for k, r in enumerate(reqs):
+                res = self.resident[r.sid]
+                res.inflight += 1
+                part = ids_d[off[k]:off[k + 1]].long()
+                fp = self._params_for(res, r.ids)
+                r.criterion = fp.crit
+                systems.append(res.system)
+                params.append(fp)
+                aolds.append(res.aold[part])
+            a_old = torch.cat(aolds).contiguous()
+            n = int(off[-1])
+            acc = torch.empty((n, 3), dtype=torch.float32, device=self.dev)
+            pot = torch.empty(n, dtype=torch.float32, device=self.dev)
+            nint = torch.empty(n, dtype=torch.int32, device=self.dev)
+            self.plan.compute_forces_batch(systems, off, params, ids_d, acc, a_old=a_old, pot=pot, n_int=nint,
+                                           stream=self.walk_stream.cuda_stream)
+            # |a| of this evaluation becomes a_old of later ones
+            amag = torch.linalg.vector_norm(acc, dim=1)
+            for k, r in enumerate(reqs):
+                res = self.resident[r.sid]
+                part = ids_d[off[k]:off[k + 1]].long()
+                res.aold[part] = amag[off[k]:off[k + 1]]
+                res.aold_valid[r.ids] = True
+            acc_h = acc.to("cpu", non_blocking=True)
+            pot_h = pot.to("cpu", non_blocking=True)
+            nint_h = nint.to("cpu", non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(self.walk_stream)
+        return _Round(reqs, acc_h, pot_h, nint_h, off, ev, [r.sid for r in reqs])
+
+    def _complete(self, rnd: _Round, t0: float):
+        rnd.event.synchronize()
+        now = time.perf_counter() - t0
+        acc, pot, nint = rnd.acc.numpy(), rnd.pot.numpy(), rnd.nint.numpy()
+        for k, r in enumerate(rnd.reqs):
+            lo, hi = rnd.offsets[k], rnd.offsets[k + 1]
+            r.acc, r.pot, r.n_int = acc[lo:hi], pot[lo:hi], nint[lo:hi]
+            r.t_done = now
+            res = self.resident.get(r.sid)
+            if res is not None:
+                res.inflight -= 1
+
+    def serve(self, requests, realtime: bool = True):
+        """Serves ``requests`` (sorted by arrival).  With ``realtime`` a request
+        becomes visible at its arrival time; otherwise all are visible at once.
+        Returns the requests with results and completion times."""
+        reqs = sorted(requests, key=lambda r: r.arrival)
+        queue = collections.deque()
+        inflight = None
+        i = 0
+        t0 = time.perf_counter()
+        while i < len(reqs) or queue or inflight is not None:
+            now = time.perf_counter() - t0
+            while i < len(reqs) and (not realtime or reqs[i].arrival <= now):
+                queue.append(reqs[i])
+                i += 1
+            if inflight is not None and inflight.event.query():
+                self._complete(inflight, t0)
+                inflight = None
+            if queue and inflight is None:
+                batch, nids = [], 0
+                while queue and len(batch) < self.max_req and nids + len(queue[0].ids) <= self.max_ids:
+                    if not self.ensure_resident(queue[0].sid):
+                        break  # waits for memory held by the round in flight
+                    r = queue.popleft()
+                    batch.append(r)
+                    nids += len(r.ids)
+                if not batch:
+                    if len(queue[0].ids) > self.max_ids:
+                        raise ValueError("request %d larger than the server's round size" % queue[0].rid)
+                    raise MemoryError("the tree of system %d does not fit in the HBM budget" % queue[0].sid)
+                inflight = self._launch(batch)
+            elif queue and inflight is not None:
+                # admit while the GPU walks: build the trees the waiting requests need
+                for r in list(queue)[:self.max_req]:
+                    if r.sid not in self.resident and not self.ensure_resident(r.sid):
+                        break
+                if not inflight.event.query():
+                    time.sleep(0)
+            elif inflight is not None:
+                time.sleep(0)
+            elif i < len(reqs):
+                time.sleep(max(0.0, min(1e-3, reqs[i].arrival - now)))
+        return reqs
+
+
+def serve_per_request(ctx: Context, source, requests, theta: float = 0.5, alpha: float = 0.0025,
+                      policy: str = "adaptive", realtime: bool = True):
+    """Baseline: requests in arrival order, each with its own build (if the
+    system is not resident), ``tpm_compute_forces`` call and synchronisation;
+    LRU eviction under the same budget."""
+    import torch
+
+    dev = torch.device("cuda", ctx.device)
+    resident = collections.OrderedDict()
+    reqs = sorted(requests, key=lambda r: r.arrival)
+    t0 = time.perf_counter()
+    for r in reqs:
+        if realtime:
+            wait = r.arrival - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+        if r.sid in resident:
+            resident.move_to_end(r.sid)
+        else:
+            pos, mass, bp = source(r.sid)
+            while True:
+                try:
+                    system = ctx.build_tree(pos, mass, bp)
+                    break
+                except TreePMError as e:
+                    if e.status != _EBUDGET or not resident:
+                        raise
+                    _, (old, _, _) = resident.popitem(last=False)
+                    old.release()
+            resident[r.sid] = (system, torch.zeros(system.n, device=dev), np.zeros(system.n, dtype=bool))
+        system, aold, valid = resident[r.sid]
+        ids_d = torch.from_numpy(r.ids.astype(np.int32)).to(dev)
+        part = ids_d.long()
+        if policy == "bh" or (policy == "adaptive" and not bool(valid[r.ids].all())):
+            fp = ForceParams(crit=CRIT_BH, theta=theta)
+        else:
+            fp = ForceParams(crit=CRIT_RELATIVE, alpha=alpha)
+        r.criterion = fp.crit
+        acc, pot, nint = system.compute_forces(active_ids=ids_d, a_old=aold[part].contiguous(), fp=fp)
+        aold[part] = torch.linalg.vector_norm(acc, dim=1)
+        valid[r.ids] = True
+        r.acc, r.pot, r.n_int = acc.cpu().numpy(), pot.cpu().numpy(), nint.cpu().numpy()
+        r.t_done = time.perf_counter() - t0
+    for system, _, _ in resident.values():
+        system.release()
+    return reqs

@@ -185,12 +185,10 @@ def timebins(pos: np.ndarray, seed: int, nbins: int = 8, a: float = 1.0, M: floa
     order = np.argsort(dt, kind="stable")
     n = len(pos)
     bins = np.zeros(n, dtype=np.int32)
-    # cumulative fraction of particles in bins >= b is 2^{b-(nbins-1)} for b >= 1
+    # the fraction of particles in bins >= b is 2^-b (b >= 1); bin 0 takes the rest
     start = 0
     for b in range(nbins - 1, 0, -1):
-        frac_ge = 2.0 ** (b - (nbins - 1))
-        end = int(round(frac_ge * n)) if b > 1 else n // 2
-        end = max(end, start)
+        end = max(int(round(2.0 ** -b * n)), start)
         bins[order[start:end]] = b
         start = end
     bins[order[start:]] = 0
