@@ -35,7 +35,24 @@ if ROOT not in sys.path:
 import workloads as W  # noqa: E402
 
 METRIC = "active-particle forces/s and interactions/s at p99 rel. force err <=5e-3; p50/p99 latency"
-FLOPS_PER_INTERACTION = 20  # monopole pair term, FP32 (offset 3, r^2 5 flops... see the design doc)
+FLOPS_PER_INTERACTION = 20  # monopole pair term with potential, FP32
+
+# DRAM bytes (read + write) of one k_walk_group launch of the headline step,
+# from the ncu capture summarised in profiles/k_walk_group_hernquist_2p20_relative.md,
+# valid only for the walk source it was taken from
+WALK_TRAFFIC = {"bytes": 105.766144e6 + 13.333760e6,
+                "walk_cu_sha256": "15552c904a81ffd998e73b12d0d5f4c051b9588825d9ab0af4750493e4a8b567"}
+
+
+def walk_traffic():
+    import hashlib
+
+    path = os.path.join(ROOT, "paper_1909_04667_gb300", "csrc", "walk.cu")
+    try:
+        digest = hashlib.sha256(open(path, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return WALK_TRAFFIC["bytes"] if digest == WALK_TRAFFIC["walk_cu_sha256"] else None
 
 # ------------------------------------------------------------------ configs
 HERNQUIST = dict(n=1 << 20, seed=W.CONFIG_SEEDS[2], h=0.005, G=1.0, bucket=8, theta=0.5, alpha=0.0025)
@@ -242,8 +259,8 @@ def run_ours(args, rank, world):
         build_ms=build_ms, walk_ms=walk_ms,
         e2e={"value": n / (e2e_ms * 1e-3), "unit": "forces/s", "ms_per_step": e2e_ms,
              "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-        roofline={"bound": "alu", "kernel": "k_walk (relative criterion)", "achieved": achieved,
-                  "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+        roofline={"bound": "alu", "kernel": "k_walk_group (relative criterion)", "achieved": achieved,
+                  "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": walk_traffic(),
                   "peak_kind": "FP32 CUDA-core peak = SMs x 128 x 2 x %.0f MHz (%s sm_max)" % (sm_max, pk_kind),
                   "algorithmic": "%d flops x %d useful interactions per launch" % (FLOPS_PER_INTERACTION,
                                                                                     interactions)},
