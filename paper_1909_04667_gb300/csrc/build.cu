@@ -228,7 +228,7 @@ __device__ __forceinline__ uint32_t lower_bound_key(const uint64_t *__restrict__
 }
 
 struct LevelArrays {
-    uint32_t *first, *count, *child, *nchild;
+    uint32_t *first, *count, *child, *nchild, *parent, *arrive;
     uint8_t *level;
     uint64_t *prefix;
 };
@@ -240,19 +240,25 @@ __global__ void k_level0(LevelArrays b, BuildState *__restrict__ st, int64_t n) 
     b.count[0] = (uint32_t)n;
     b.level[0] = 0;
     b.prefix[0] = 0;
-    st->total = 1;
+    b.parent[0] = 0;
     st->lstart[0] = 0;
     st->lcount[0] = 1;
-    st->maxlevel = 0;
 }
 
 // K3: splits every cell of one level that holds more than B particles (and is
 // above the depth cap) into its non-empty octants.  Eight consecutive threads
 // serve one cell: thread o finds where octant o starts in the cell's key
-// range; the cell's first thread reserves the children with one atomic.
+// range; the cell's first thread reserves the children with one atomic on
+// the next level's counter.  Level l + 1 starts right after level l, whose
+// size is final once the previous launch has finished.
 __global__ void k_split_level(const uint64_t *__restrict__ key, LevelArrays b, BuildState *__restrict__ st, int level,
                               int bucket, unsigned cap) {
-    const unsigned ls = st->lstart[level], lc = st->lcount[level];
+    // nodes past the node space (reserved after an overflow) were never written
+    const unsigned ls = st->lstart[level], lc_all = st->lcount[level];
+    const unsigned lc = ls >= cap ? 0u : min(lc_all, cap - ls);
+    const unsigned next_start = ls + lc_all;
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        st->lstart[level + 1] = next_start;
     const int lane = threadIdx.x & 31;
     const unsigned gmask = 0xffu << (lane & 24);
     const int o = lane & 7;
@@ -279,75 +285,77 @@ __global__ void k_split_level(const uint64_t *__restrict__ key, LevelArrays b, B
         const unsigned nch = __popc(bm);
         unsigned first_child = 0;
         if (o == 0)
-            first_child = atomicAdd(&st->total, nch);
+            first_child = next_start + atomicAdd(&st->lcount[level + 1], nch);
         first_child = __shfl_sync(gmask, first_child, 0, 8);
-        if (first_child + nch > cap) {  // out of node space: the host rebuilds with more
-            if (o == 0) {
-                st->overflow = 1;
-                b.child[node] = 0;
-                b.nchild[node] = 0;
-            }
-            continue;
-        }
+        // out of node space: the host rebuilds with more.  The children that
+        // still fit are written all the same, so that every slot below the
+        // cap that the next level visits holds a valid key range.
+        const bool fits = (uint64_t)first_child + nch <= cap;
         if (nonempty) {
             const unsigned ch = first_child + __popc(bm & ((1u << o) - 1u));
-            b.first[ch] = lo;
-            b.count[ch] = hi - lo;
-            b.level[ch] = (uint8_t)(level + 1);
-            b.prefix[ch] = base | (uint64_t)o;
+            if (ch < cap) {
+                b.first[ch] = lo;
+                b.count[ch] = hi - lo;
+                b.level[ch] = (uint8_t)(level + 1);
+                b.prefix[ch] = base | (uint64_t)o;
+                b.parent[ch] = node;
+            }
         }
         if (o == 0) {
-            b.child[node] = first_child;
-            b.nchild[node] = nch;
+            if (!fits)
+                st->overflow = 1;
+            b.child[node] = fits ? first_child : 0u;
+            b.nchild[node] = fits ? nch : 0u;
         }
     }
 }
 
-// The children reserved while splitting level l form level l + 1.
-__global__ void k_level_bounds(BuildState *__restrict__ st, int level, unsigned cap) {
-    if (threadIdx.x != 0)
+// K4: FP64 monopoles in one pass, bottom-up.  Each leaf sums its particles in
+// sorted order; then the last child of a node to finish (counted with an
+// atomic on the parent) sums the node's children in ascending octant order,
+// and so on up to the root.  Explicit round-to-nearest adds / muls, so every
+// sum has the same fixed order and value whichever thread computes it.
+__global__ void k_multipole(LevelArrays b, int64_t total, const uint32_t *__restrict__ perm,
+                            const double *__restrict__ pos, const float *__restrict__ mass, double *__restrict__ M,
+                            double *__restrict__ S) {
+    const int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (node >= total || b.nchild[node] != 0)
         return;
-    const unsigned start = st->lstart[level] + st->lcount[level];
-    const unsigned total = min(st->total, cap);
-    st->lstart[level + 1] = start;
-    st->lcount[level + 1] = total > start ? total - start : 0u;
-    if (total > start)
-        st->maxlevel = level + 1;
-}
-
-// K4: FP64 monopoles of one level, children first (ascending octant), a
-// leaf's particles in sorted order; explicit round-to-nearest adds / muls.
-__global__ void k_multipole(LevelArrays b, const BuildState *__restrict__ st, int level,
-                            const uint32_t *__restrict__ perm, const double *__restrict__ pos,
-                            const float *__restrict__ mass, double *__restrict__ M, double *__restrict__ S) {
-    const unsigned ls = st->lstart[level], lc = st->lcount[level];
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < lc; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t node = ls + i;
     double m = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
-    uint32_t nc = b.nchild[node];
-    if (nc == 0) {
-        uint32_t f = b.first[node], e = f + b.count[node];
-        for (uint32_t s = f; s < e; s++) {
-            uint32_t j = perm[s];
-            double mj = (double)mass[j];
-            m = __dadd_rn(m, mj);
-            sx = __dadd_rn(sx, __dmul_rn(mj, pos[3 * j]));
-            sy = __dadd_rn(sy, __dmul_rn(mj, pos[3 * j + 1]));
-            sz = __dadd_rn(sz, __dmul_rn(mj, pos[3 * j + 2]));
-        }
-    } else {
-        uint32_t c0 = b.child[node];
-        for (uint32_t c = c0; c < c0 + nc; c++) {
-            m = __dadd_rn(m, M[c]);
-            sx = __dadd_rn(sx, S[3 * c]);
-            sy = __dadd_rn(sy, S[3 * c + 1]);
-            sz = __dadd_rn(sz, S[3 * c + 2]);
-        }
+    const uint32_t f = b.first[node], e = f + b.count[node];
+    for (uint32_t s = f; s < e; s++) {
+        const uint32_t j = perm[s];
+        const double mj = (double)mass[j];
+        m = __dadd_rn(m, mj);
+        sx = __dadd_rn(sx, __dmul_rn(mj, pos[3 * j]));
+        sy = __dadd_rn(sy, __dmul_rn(mj, pos[3 * j + 1]));
+        sz = __dadd_rn(sz, __dmul_rn(mj, pos[3 * j + 2]));
     }
     M[node] = m;
     S[3 * node] = sx;
     S[3 * node + 1] = sy;
     S[3 * node + 2] = sz;
+    uint32_t cur = (uint32_t)node;
+    while (cur != 0) {
+        const uint32_t p = b.parent[cur];
+        __threadfence();  // this node's sums are visible before the parent learns it is done
+        const uint32_t nc = b.nchild[p];
+        if (atomicAdd(&b.arrive[p], 1u) != nc - 1)
+            return;  // a sibling still works; it will carry on upwards
+        __threadfence();
+        m = sx = sy = sz = 0.0;
+        const uint32_t c0 = b.child[p];
+        for (uint32_t c = c0; c < c0 + nc; c++) {
+            m = __dadd_rn(m, __ldcg(&M[c]));
+            sx = __dadd_rn(sx, __ldcg(&S[3 * c]));
+            sy = __dadd_rn(sy, __ldcg(&S[3 * c + 1]));
+            sz = __dadd_rn(sz, __ldcg(&S[3 * c + 2]));
+        }
+        M[p] = m;
+        S[3 * p] = sx;
+        S[3 * p + 1] = sy;
+        S[3 * p + 2] = sz;
+        cur = p;
     }
 }
 
@@ -474,12 +482,11 @@ int build_tree_device(Ctx *c, System *s, const double *pos_in, const float *mass
 
     BuildState *dst;
     TPM_CHECK(tmp.get(&dst, 1, st));
-    BuildState *hst;
-    TPM_CUDA(cudaMallocHost(&hst, sizeof(BuildState)));
-    struct HostGuard {
-        void *p;
-        ~HostGuard() { cudaFreeHost(p); }
-    } hg{hst};
+    // the context's pinned page holds the host copy of the build state; one
+    // build at a time per context uses it
+    static_assert(sizeof(BuildState) <= kPinnedStateBytes, "build state exceeds the pinned page");
+    std::lock_guard<std::mutex> build_lock(c->build_mu);
+    BuildState *hst = static_cast<BuildState *>(c->pinned_state);
     memset(hst, 0, sizeof(BuildState));
     for (int a = 0; a < 3; a++) {
         hst->bbox[a] = LLONG_MAX;
@@ -537,22 +544,17 @@ int build_tree_device(Ctx *c, System *s, const double *pos_in, const float *mass
         TPM_CHECK(lv.get(&b.nchild, cap, st));
         TPM_CHECK(lv.get(&b.level, cap, st));
         TPM_CHECK(lv.get(&b.prefix, cap, st));
+        TPM_CHECK(lv.get(&b.parent, cap, st));
+        TPM_CHECK(lv.get(&b.arrive, cap, st));
         TPM_CHECK(lv.get(&M, cap, st));
         TPM_CHECK(lv.get(&S, 3 * (size_t)cap, st));
         TPM_CUDA(cudaMemsetAsync(&dst->overflow, 0, sizeof(int), st));
+        TPM_CUDA(cudaMemsetAsync(dst->lcount, 0, sizeof(dst->lcount), st));
+        TPM_CUDA(cudaMemsetAsync(b.arrive, 0, (size_t)cap * sizeof(uint32_t), st));
         k_level0<<<1, 32, 0, st>>>(b, dst, n);
         count_launch();
         for (int level = 0; level <= kMaxLevel; level++) {
             k_split_level<<<grid, kThreads, 0, st>>>(s->key, b, dst, level, B, cap);
-            count_launch();
-            if (level < kMaxLevel) {
-                k_level_bounds<<<1, 32, 0, st>>>(dst, level, cap);
-                count_launch();
-            }
-        }
-        TPM_CUDA(cudaGetLastError());
-        for (int level = kMaxLevel; level >= 0; level--) {
-            k_multipole<<<grid, kThreads, 0, st>>>(b, dst, level, s->perm, s->pos, s->mass, M, S);
             count_launch();
         }
         TPM_CUDA(cudaGetLastError());
@@ -570,13 +572,29 @@ int build_tree_device(Ctx *c, System *s, const double *pos_in, const float *mass
             set_error("periodic positions must lie in [0, box)");
             return TPM_EINVAL;
         }
-        if (!hst->overflow)
+        uint64_t total = 0;
+        int maxlevel = 0;
+        for (int l = 0; l <= kMaxLevel; l++) {
+            total += hst->lcount[l];
+            if (hst->lcount[l])
+                maxlevel = l;
+        }
+        if (!hst->overflow) {
+            hst->total = (unsigned)total;
+            hst->maxlevel = maxlevel;
             break;
-        if (attempt >= 2 || hst->total >= 0x7fffffffu) {
-            set_error("tree node space overflow (%u nodes needed)", hst->total);
+        }
+        // the count seen is a lower bound (subtrees below the cap's edge were
+        // not explored); no level holds more than min(8^l, n) nodes
+        uint64_t bound = 0;
+        for (int l = 0; l <= kMaxLevel; l++)
+            bound += std::min<uint64_t>(l < 21 ? uint64_t(1) << (3 * l) : UINT64_MAX, (uint64_t)n);
+        bound = std::min<uint64_t>(bound, 0x7fffffffULL);
+        if (attempt >= 5 || cap >= bound) {
+            set_error("tree node space overflow (at least %llu nodes needed)", (unsigned long long)total);
             return TPM_ECUDA;
         }
-        cap = (unsigned)std::min<uint64_t>((uint64_t)hst->total * 2 + 1024, 0x7fffffffULL);
+        cap = (unsigned)std::min<uint64_t>(std::max<uint64_t>(4 * total, 2 * (uint64_t)cap) + 1024, bound);
     }
     for (int a = 0; a < 3; a++)
         s->x0[a] = hst->x0[a];
@@ -584,6 +602,11 @@ int build_tree_device(Ctx *c, System *s, const double *pos_in, const float *mass
     const int64_t nn = hst->total;
     s->nnodes = nn;
     s->maxlevel = hst->maxlevel;
+
+    // ---- monopoles, bottom-up in one pass
+    k_multipole<<<blocks_for(nn), kThreads, 0, st>>>(b, nn, s->perm, s->pos, s->mass, M, S);
+    count_launch();
+    TPM_CUDA(cudaGetLastError());
 
     // ---- pre-order
     uint64_t *okey, *pkey;

@@ -206,6 +206,13 @@ int tpm_create(tpm_ctx **out, int device, size_t budget) {
     }
     uint64_t thr = UINT64_MAX;
     cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    e = cudaMallocHost(&c->pinned_state, kPinnedStateBytes);
+    if (e != cudaSuccess) {
+        cudaMemPoolDestroy(c->pool);
+        delete c;
+        set_error("cudaMallocHost: %s", cudaGetErrorString(e));
+        return TPM_ECUDA;
+    }
     *out = reinterpret_cast<tpm_ctx *>(c);
     return TPM_OK;
 }
@@ -229,6 +236,7 @@ int tpm_destroy(tpm_ctx *h) {
     }
     cudaStreamSynchronize(0);
     cudaMemPoolDestroy(c->pool);
+    cudaFreeHost(c->pinned_state);
     delete c;
     return TPM_OK;
 }

@@ -130,8 +130,12 @@ struct System {
     double pm_G = 0.0;
 };
 
+constexpr size_t kPinnedStateBytes = 4096;
+
 struct Ctx {
     int device = 0;
+    void *pinned_state = nullptr;  // host page for a build's device-side bookkeeping
+    std::mutex build_mu;
     int num_sms = 0;
     size_t budget = 0;
     size_t used = 0;

@@ -76,6 +76,16 @@ def clustered(n, seed, dup=0):
     return pos, np.full(n, 1.0 / n, np.float32)
 
 
+def triplets(n_trip, seed):
+    """Tight triplets: each needs a chain of cells down to the depth cap, so the
+    tree has several times more nodes than particles and the build's first
+    guess of the node space overflows."""
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(-1, 1, (n_trip, 3))
+    pos = np.repeat(c, 3, axis=0) + 1e-9 * rng.standard_normal((3 * n_trip, 3))
+    return pos, np.full(3 * n_trip, 1.0 / (3 * n_trip), np.float32)
+
+
 TREE_CASES = [
     ("plummer8192_B1", lambda: W.plummer(8192, 1001), 1, False),
     ("plummer8192_B8", lambda: W.plummer(8192, 1001), 8, False),
@@ -85,6 +95,7 @@ TREE_CASES = [
     ("single", lambda: W.plummer(1, 9), 1, False),
     ("pair", lambda: W.plummer(2, 9), 1, False),
     ("zeldovich32_B4", lambda: W.zeldovich(32, 3), 4, True),
+    ("triplets_node_overflow_B2", lambda: triplets(1500, 11), 2, False),
 ]
 
 
