@@ -7,17 +7,22 @@
 //
 //   1. root cube and 21-bit integer cell coordinates -> 63-bit Morton keys
 //   2. stable radix sort of (key, particle index)
-//   3. level by level, every cell holding more than B particles is split into
-//      its non-empty octants: eight threads per cell find the eight octant
-//      boundaries in the sorted keys at once, and one atomic per cell
-//      reserves its children (contiguous, in ascending octant order); the
-//      level ranges stay on the device, so no host round trip is needed
-//      between levels
+//   3. the nodes straight from the sorted keys, in depth-first pre-order:
+//      with w(j) the deepest level shared by keys j and j + B, the cell
+//      around particle i holds more than B particles down to level
+//      max w(j) over j in [i - B, i], so i's leaf level D(i) is one below
+//      (capped at 21); the nodes whose first particle is i are its cells at
+//      the levels below the level it shares with particle i - 1, down to
+//      D(i).  Nodes ordered by (first particle, level) are the pre-order,
+//      so a scan of the per-particle node counts places every node; particle
+//      ranges, skip indices and parents follow from searches in the sorted
+//      keys.  No level-by-level passes and no host round trip but one (the
+//      node count, to size the node tables)
 //   4. FP64 masses and mass-weighted positions summed bottom-up, children in
 //      ascending octant order and a leaf's particles in sorted order, with
 //      explicit round-to-nearest operations (no contraction), so the result
 //      is the same bit for bit on any correct implementation of that order
-//   5. depth-first pre-order tables for the walk: per node the FP32 geometric
+//   5. pre-order and breadth-first tables for the walks: per node the FP32 geometric
 //      centre (exact: it lies on the 2^-22 L0 grid), side, centre of mass
 //      relative to the centre, mass, skip index, particle range and leaf flag
 //      -- three 16-byte records loaded with one vector load each -- and per
@@ -134,15 +139,12 @@ __device__ __forceinline__ uint32_t compact3(uint64_t v) {
     return (uint32_t)v;
 }
 
-// Device-side bookkeeping of one build.
+// Device-side bookkeeping of one build (its host copy also receives the node
+// count).
 struct BuildState {
     long long bbox[6];
     int bad;
-    int overflow;
-    unsigned total;  // nodes reserved so far
-    int maxlevel;
-    unsigned lstart[kMaxLevel + 2];
-    unsigned lcount[kMaxLevel + 2];
+    unsigned total;  // nodes of the tree
     double x0[3];
     double L0;
     double scale;  // 2^21 / L0
@@ -208,163 +210,225 @@ __global__ void k_keys(const double *__restrict__ pos, int64_t n, const BuildSta
     idx[i] = (uint32_t)i;
 }
 
-__global__ void k_rank(const uint32_t *__restrict__ perm, int64_t n, uint32_t *__restrict__ rank) {
+// Inverse permutation, and positions and masses gathered into key order for
+// the passes over leaves.
+__global__ void k_rank(const uint32_t *__restrict__ perm, int64_t n, const double *__restrict__ pos,
+                       const float *__restrict__ mass, uint32_t *__restrict__ rank, double *__restrict__ spos,
+                       float *__restrict__ smass) {
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (s < n)
-        rank[perm[s]] = (uint32_t)s;
+    if (s >= n)
+        return;
+    const uint32_t j = perm[s];
+    rank[j] = (uint32_t)s;
+    spos[3 * s] = pos[3 * j];
+    spos[3 * s + 1] = pos[3 * j + 1];
+    spos[3 * s + 2] = pos[3 * j + 2];
+    smass[s] = mass[j];
 }
 
-// first index in [lo, hi) whose key is >= bound (keys ascending)
-__device__ __forceinline__ uint32_t lower_bound_key(const uint64_t *__restrict__ key, uint32_t lo, uint32_t hi,
-                                                    uint64_t bound) {
-    while (lo < hi) {
-        uint32_t mid = lo + ((hi - lo) >> 1);
-        if (key[mid] < bound)
-            lo = mid + 1;
-        else
-            hi = mid;
+// Deepest level whose cell holds both keys (kMaxLevel when they are equal).
+__device__ __forceinline__ int common_level(uint64_t a, uint64_t b) {
+    const uint64_t x = a ^ b;
+    return x ? (kMaxLevel - 1) - (63 - __clzll((long long)x)) / 3 : kMaxLevel;
+}
+
+// Smallest e in [lo, hi] with e == hi or key[e] >= bound (keys ascending,
+// key[lo - 1] < bound): exponential search from lo, then bisection.
+__device__ __forceinline__ uint32_t search_up(const uint64_t *__restrict__ key, uint32_t lo, uint32_t hi,
+                                              uint64_t bound) {
+    uint32_t a = lo, b = lo;
+    uint64_t step = 1;
+    while (b < hi && key[b] < bound) {
+        a = b + 1;
+        b = (uint64_t)(hi - b) > step ? b + (uint32_t)step : hi;
+        step <<= 1;
     }
-    return lo;
+    while (a < b) {
+        const uint32_t mid = a + ((b - a) >> 1);
+        if (key[mid] < bound)
+            a = mid + 1;
+        else
+            b = mid;
+    }
+    return a;
 }
 
-struct LevelArrays {
-    uint32_t *first, *count, *child, *nchild, *parent, *arrive;
+// Smallest f <= i with key[f] >= bound, given key[i] >= bound: exponential
+// search downwards from i, then bisection.
+__device__ __forceinline__ uint32_t search_down(const uint64_t *__restrict__ key, uint32_t i, uint64_t bound) {
+    int64_t hi = i, lo = (int64_t)i - 1, step = 1;
+    while (lo >= 0 && key[lo] >= bound) {
+        hi = lo;
+        lo -= step;
+        step <<= 1;
+    }
+    int64_t a = lo + 1 > 0 ? lo + 1 : 0, b = hi;
+    while (a < b) {
+        const int64_t mid = a + ((b - a) >> 1);
+        if (key[mid] < bound)
+            a = mid + 1;
+        else
+            b = mid;
+    }
+    return (uint32_t)a;
+}
+
+// K3a. Which cells hold more than B particles.  The level-m cell around sorted
+// particle i holds more than B particles iff some run of B + 1 consecutive
+// particles inside it contains i, i.e. iff w(j) >= m for some j in [i - B, i],
+// where w(j) = common_level(key[j], key[j + B]).  The window maximum over
+// [i - B, i] comes from prefix and suffix maxima inside blocks of B + 1
+// entries (one thread per block); this kernel writes them.
+__global__ void k_window_max(const uint64_t *__restrict__ key, int64_t n, int B, int8_t *__restrict__ pre_max,
+                             int8_t *__restrict__ suf_max) {
+    const int64_t W = (int64_t)B + 1;
+    const int64_t j0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * W;
+    if (j0 >= n)
+        return;
+    const int64_t j1 = min(j0 + W, n);
+    int m = -1;
+    for (int64_t j = j0; j < j1; j++) {
+        const int w = j + B < n ? common_level(key[j], key[j + B]) : -1;
+        suf_max[j] = (int8_t)w;
+        m = max(m, w);
+        pre_max[j] = (int8_t)m;
+    }
+    m = -1;
+    for (int64_t j = j1 - 1; j >= j0; j--) {
+        m = max(m, (int)suf_max[j]);
+        suf_max[j] = (int8_t)m;
+    }
+}
+
+// K3b. Per sorted particle i: the level of its leaf, D(i) = min(1 + deepest
+// level whose cell around i holds more than B particles, 21), and the levels
+// at which i is the first particle of its cell, (common_level(key[i-1],
+// key[i]), D(i)].  Those cells are exactly the nodes whose first particle is
+// i, and ordering all nodes by (first particle, level) is the depth-first
+// pre-order: an exclusive scan of the per-particle counts gives every node
+// its pre-order index directly.
+__global__ void k_node_counts(const uint64_t *__restrict__ key, int64_t n, int B, const int8_t *__restrict__ pre_max,
+                              const int8_t *__restrict__ suf_max, uint8_t *__restrict__ top_level,
+                              uint8_t *__restrict__ leaf_level, uint32_t *__restrict__ cnt) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    const int lp = i ? common_level(key[i - 1], key[i]) : -1;
+    int split = pre_max[i];  // deepest level whose cell around i holds > B particles
+    if (i - B >= 0)
+        split = max(split, (int)suf_max[i - B]);
+    const int D = min(split + 1, kMaxLevel);
+    top_level[i] = (uint8_t)(lp + 1);
+    leaf_level[i] = (uint8_t)D;
+    cnt[i] = (uint32_t)max(D - lp, 0);
+}
+
+// Pre-order node arrays of the build.
+struct NodeArrays {
+    uint32_t *first, *count, *skip, *parent, *nchild, *arrive, *order;
     uint8_t *level;
     uint64_t *prefix;
 };
 
-__global__ void k_level0(LevelArrays b, BuildState *__restrict__ st, int64_t n) {
-    if (threadIdx.x != 0)
+// K3c. The nodes whose first particle is sorted particle i, from the top
+// down: particle range (the cell's end found by searching the sorted keys),
+// skip index (the first node of the particle just past the cell), key prefix,
+// parent (the node above with the same first particle, else the cell found by
+// searching downwards) and, by one atomic per node, the parent's child count.
+__global__ void k_nodes(const uint64_t *__restrict__ key, int64_t n, const uint32_t *__restrict__ base,
+                        const uint8_t *__restrict__ top_level, const uint8_t *__restrict__ leaf_level, NodeArrays t) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n)
         return;
-    b.first[0] = 0;
-    b.count[0] = (uint32_t)n;
-    b.level[0] = 0;
-    b.prefix[0] = 0;
-    b.parent[0] = 0;
-    st->lstart[0] = 0;
-    st->lcount[0] = 1;
-}
-
-// K3: splits every cell of one level that holds more than B particles (and is
-// above the depth cap) into its non-empty octants.  Eight consecutive threads
-// serve one cell: thread o finds where octant o starts in the cell's key
-// range; the cell's first thread reserves the children with one atomic on
-// the next level's counter.  Level l + 1 starts right after level l, whose
-// size is final once the previous launch has finished.
-__global__ void k_split_level(const uint64_t *__restrict__ key, LevelArrays b, BuildState *__restrict__ st, int level,
-                              int bucket, unsigned cap) {
-    // nodes past the node space (reserved after an overflow) were never written
-    const unsigned ls = st->lstart[level], lc_all = st->lcount[level];
-    const unsigned lc = ls >= cap ? 0u : min(lc_all, cap - ls);
-    const unsigned next_start = ls + lc_all;
-    if (blockIdx.x == 0 && threadIdx.x == 0)
-        st->lstart[level + 1] = next_start;
-    const int lane = threadIdx.x & 31;
-    const unsigned gmask = 0xffu << (lane & 24);
-    const int o = lane & 7;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < (int64_t)lc * 8; t += stride) {
-        const unsigned node = ls + (unsigned)(t >> 3);
-        const uint32_t f = b.first[node], c = b.count[node];
-        const bool split = (int)c > bucket && level < kMaxLevel;
-        if (!split) {
-            if (o == 0) {
-                b.child[node] = 0;
-                b.nchild[node] = 0;
+    const uint32_t p0 = base[i], nc = base[i + 1] - p0;
+    if (nc == 0)
+        return;
+    const uint32_t total = base[n];
+    const int l0 = top_level[i];
+    const uint64_t ki = key[i];
+    uint32_t end = (uint32_t)n;
+    for (uint32_t k = 0; k < nc; k++) {
+        const int l = l0 + (int)k;
+        const uint32_t p = p0 + k;
+        const int sh = 3 * (kMaxLevel - l);
+        const uint64_t pre = ki >> sh;
+        end = search_up(key, (uint32_t)i + 1, end, (pre + 1) << sh);  // cells nest: the end only shrinks
+        t.first[p] = (uint32_t)i;
+        t.count[p] = end - (uint32_t)i;
+        t.skip[p] = end < n ? base[end] : total;
+        t.level[p] = (uint8_t)l;
+        t.prefix[p] = pre;
+        t.order[p] = p;
+        uint32_t par = 0;
+        if (l > 0) {
+            if (k > 0) {
+                par = p - 1;
+            } else {
+                const uint32_t f = search_down(key, (uint32_t)i, (pre >> 3) << (sh + 3));
+                par = base[f] + (uint32_t)(l - 1 - top_level[f]);
             }
-            continue;
+            atomicAdd(&t.nchild[par], 1u);
         }
-        const int shift = 3 * (kMaxLevel - level - 1);
-        const uint64_t base = b.prefix[node] << 3;
-        const uint32_t lo = (o == 0) ? f : lower_bound_key(key, f, f + c, (base | (uint64_t)o) << shift);
-        uint32_t hi = __shfl_down_sync(gmask, lo, 1, 8);
-        if (o == 7)
-            hi = f + c;
-        const bool nonempty = hi > lo;
-        const unsigned bm = (__ballot_sync(gmask, nonempty) >> (lane & 24)) & 0xffu;
-        const unsigned nch = __popc(bm);
-        unsigned first_child = 0;
-        if (o == 0)
-            first_child = next_start + atomicAdd(&st->lcount[level + 1], nch);
-        first_child = __shfl_sync(gmask, first_child, 0, 8);
-        // out of node space: the host rebuilds with more.  The children that
-        // still fit are written all the same, so that every slot below the
-        // cap that the next level visits holds a valid key range.
-        const bool fits = (uint64_t)first_child + nch <= cap;
-        if (nonempty) {
-            const unsigned ch = first_child + __popc(bm & ((1u << o) - 1u));
-            if (ch < cap) {
-                b.first[ch] = lo;
-                b.count[ch] = hi - lo;
-                b.level[ch] = (uint8_t)(level + 1);
-                b.prefix[ch] = base | (uint64_t)o;
-                b.parent[ch] = node;
-            }
-        }
-        if (o == 0) {
-            if (!fits)
-                st->overflow = 1;
-            b.child[node] = fits ? first_child : 0u;
-            b.nchild[node] = fits ? nch : 0u;
-        }
+        t.parent[p] = par;
     }
 }
 
 // K4: FP64 monopoles in one pass, bottom-up.  Each leaf sums its particles in
 // sorted order; then the last child of a node to finish (counted with an
 // atomic on the parent) sums the node's children in ascending octant order,
-// and so on up to the root.  Explicit round-to-nearest adds / muls, so every
-// sum has the same fixed order and value whichever thread computes it.
-__global__ void k_multipole(LevelArrays b, int64_t total, const uint32_t *__restrict__ perm,
-                            const double *__restrict__ pos, const float *__restrict__ mass, double *__restrict__ M,
+// and so on up to the root.  Sums are stored by breadth-first index, where a
+// node's children are contiguous, so the children's sums load independently.
+// Explicit round-to-nearest adds / muls, so every sum has the same fixed
+// order and value whichever thread computes it.
+__global__ void k_multipole(NodeArrays t, int64_t total, const uint32_t *__restrict__ pre2bfs,
+                            const double *__restrict__ spos, const float *__restrict__ smass, double *__restrict__ M,
                             double *__restrict__ S) {
     const int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (node >= total || b.nchild[node] != 0)
+    if (node >= total || t.nchild[node] != 0)
         return;
     double m = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
-    const uint32_t f = b.first[node], e = f + b.count[node];
+    const uint32_t f = t.first[node], e = f + t.count[node];
     for (uint32_t s = f; s < e; s++) {
-        const uint32_t j = perm[s];
-        const double mj = (double)mass[j];
-        m = __dadd_rn(m, mj);
-        sx = __dadd_rn(sx, __dmul_rn(mj, pos[3 * j]));
-        sy = __dadd_rn(sy, __dmul_rn(mj, pos[3 * j + 1]));
-        sz = __dadd_rn(sz, __dmul_rn(mj, pos[3 * j + 2]));
+        const double ms = (double)smass[s];
+        m = __dadd_rn(m, ms);
+        sx = __dadd_rn(sx, __dmul_rn(ms, spos[3 * s]));
+        sy = __dadd_rn(sy, __dmul_rn(ms, spos[3 * s + 1]));
+        sz = __dadd_rn(sz, __dmul_rn(ms, spos[3 * s + 2]));
     }
-    M[node] = m;
-    S[3 * node] = sx;
-    S[3 * node + 1] = sy;
-    S[3 * node + 2] = sz;
+    uint32_t q = pre2bfs[node];
+    M[q] = m;
+    S[3 * q] = sx;
+    S[3 * q + 1] = sy;
+    S[3 * q + 2] = sz;
     uint32_t cur = (uint32_t)node;
     while (cur != 0) {
-        const uint32_t p = b.parent[cur];
+        const uint32_t p = t.parent[cur];
         __threadfence();  // this node's sums are visible before the parent learns it is done
-        const uint32_t nc = b.nchild[p];
-        if (atomicAdd(&b.arrive[p], 1u) != nc - 1)
+        const uint32_t nc = t.nchild[p];
+        if (atomicAdd(&t.arrive[p], 1u) != nc - 1)
             return;  // a sibling still works; it will carry on upwards
         __threadfence();
         m = sx = sy = sz = 0.0;
-        const uint32_t c0 = b.child[p];
+        const uint32_t c0 = pre2bfs[p + 1];  // first child; the others follow it
         for (uint32_t c = c0; c < c0 + nc; c++) {
             m = __dadd_rn(m, __ldcg(&M[c]));
             sx = __dadd_rn(sx, __ldcg(&S[3 * c]));
             sy = __dadd_rn(sy, __ldcg(&S[3 * c + 1]));
             sz = __dadd_rn(sz, __ldcg(&S[3 * c + 2]));
         }
-        M[p] = m;
-        S[3 * p] = sx;
-        S[3 * p + 1] = sy;
-        S[3 * p + 2] = sz;
+        q = pre2bfs[p];
+        M[q] = m;
+        S[3 * q] = sx;
+        S[3 * q + 1] = sy;
+        S[3 * q + 2] = sz;
         cur = p;
     }
 }
 
-__global__ void k_preorder_keys(LevelArrays b, int64_t total, uint64_t *__restrict__ okey, uint32_t *__restrict__ oval) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= total)
-        return;
-    okey[i] = ((uint64_t)b.first[i] << 5) | (uint64_t)b.level[i];
-    oval[i] = (uint32_t)i;
+__global__ void k_invert(const uint32_t *__restrict__ bfs2pre, int64_t total, uint32_t *__restrict__ pre2bfs) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q < total)
+        pre2bfs[bfs2pre[q]] = (uint32_t)q;
 }
 
 struct NodeOut {
@@ -373,88 +437,55 @@ struct NodeOut {
     uint8_t *level;
     uint64_t *prefix;
     double *mass, *comd;
+    float4 *bcen, *bcom;
+    int4 *blink;
+    float4 *spart;
 };
 
-// K5: pre-order node tables.  skip(p) = number of nodes whose (first, level)
-// key precedes (first + count, 0): the first node after p's subtree.
-__global__ void k_finalize(LevelArrays b, const uint64_t *__restrict__ pkey, const uint32_t *__restrict__ pre2bfs,
-                           int64_t total, const double *__restrict__ M, const double *__restrict__ S, double x0,
-                           double y0, double z0, double L0, NodeOut o) {
-    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+// K5: walk tables.  Pre-order: FP32 geometric centre (exact, on the 2^-22 L0
+// grid) and side, centre of mass relative to the centre and mass, (skip,
+// first particle, count, leaf flag), plus the FP64 values for export.
+// Breadth-first (level by level, each level in key order, so that a node's
+// children are contiguous): the same records with (first child, child count,
+// first particle, count).  A leaf also writes its particles relative to its
+// centre (FP64 difference -> FP32) with their masses.
+__global__ void k_finalize(NodeArrays t, const uint32_t *__restrict__ pre2bfs, int64_t total,
+                           const double *__restrict__ M, const double *__restrict__ S, const double *__restrict__ spos,
+                           const float *__restrict__ smass, double x0, double y0, double z0, double L0, NodeOut o) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= total)
         return;
-    uint32_t bi = pre2bfs[p];
-    uint32_t f = b.first[bi], c = b.count[bi];
-    int lvl = b.level[bi];
-    uint64_t pre = b.prefix[bi];
-    // skip: lower bound of (f + c) << 5 in the sorted pre-order keys after p
-    uint64_t bound = (uint64_t)(f + c) << 5;
-    int64_t lo = p + 1, hi = total;
-    while (lo < hi) {
-        int64_t mid = lo + ((hi - lo) >> 1);
-        if (pkey[mid] < bound)
-            lo = mid + 1;
-        else
-            hi = mid;
-    }
-    int leaf = b.nchild[bi] == 0;
-    double m = M[bi];
-    double cx = __ddiv_rn(S[3 * bi], m), cy = __ddiv_rn(S[3 * bi + 1], m), cz = __ddiv_rn(S[3 * bi + 2], m);
-    uint32_t ix = compact3(pre), iy = compact3(pre >> 1), iz = compact3(pre >> 2);
-    double half = ldexp(L0, -(lvl + 1));  // half side
-    double rx = (double)(2 * (uint64_t)ix + 1) * half, ry = (double)(2 * (uint64_t)iy + 1) * half,
-           rz = (double)(2 * (uint64_t)iz + 1) * half;  // centre relative to x0 (exact)
-    o.cen[p] = make_float4((float)rx, (float)ry, (float)rz, (float)(2.0 * half));
-    o.com[p] = make_float4((float)__dsub_rn(cx, __dadd_rn(x0, rx)), (float)__dsub_rn(cy, __dadd_rn(y0, ry)),
-                           (float)__dsub_rn(cz, __dadd_rn(z0, rz)), (float)m);
-    o.link[p] = make_int4((int)lo, (int)f, (int)c, leaf);
+    const uint32_t f = t.first[p], c = t.count[p], nch = t.nchild[p];
+    const int lvl = t.level[p];
+    const uint64_t pre = t.prefix[p];
+    const uint32_t q = pre2bfs[p];
+    const double m = M[q];
+    const double cx = __ddiv_rn(S[3 * q], m), cy = __ddiv_rn(S[3 * q + 1], m), cz = __ddiv_rn(S[3 * q + 2], m);
+    const double half = ldexp(L0, -(lvl + 1));
+    const double rx = (double)(2 * (uint64_t)compact3(pre) + 1) * half;
+    const double ry = (double)(2 * (uint64_t)compact3(pre >> 1) + 1) * half;
+    const double rz = (double)(2 * (uint64_t)compact3(pre >> 2) + 1) * half;  // centre relative to x0 (exact)
+    const float4 cen = make_float4((float)rx, (float)ry, (float)rz, (float)(2.0 * half));
+    const float4 com = make_float4((float)__dsub_rn(cx, __dadd_rn(x0, rx)), (float)__dsub_rn(cy, __dadd_rn(y0, ry)),
+                                   (float)__dsub_rn(cz, __dadd_rn(z0, rz)), (float)m);
+    o.cen[p] = cen;
+    o.com[p] = com;
+    o.link[p] = make_int4((int)t.skip[p], (int)f, (int)c, nch == 0);
     o.level[p] = (uint8_t)lvl;
     o.prefix[p] = pre;
     o.mass[p] = m;
     o.comd[3 * p] = cx;
     o.comd[3 * p + 1] = cy;
     o.comd[3 * p + 2] = cz;
-}
-
-// Breadth-first node records for the group walk (same values as the pre-order
-// tables; children of a node are contiguous in this order).
-__global__ void k_finalize_bfs(LevelArrays b, int64_t total, const double *__restrict__ M,
-                               const double *__restrict__ S, double x0, double y0, double z0, double L0,
-                               float4 *__restrict__ bcen, float4 *__restrict__ bcom, int4 *__restrict__ blink) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= total)
-        return;
-    const int lvl = b.level[i];
-    const uint64_t pre = b.prefix[i];
-    const double m = M[i];
-    const double cx = __ddiv_rn(S[3 * i], m), cy = __ddiv_rn(S[3 * i + 1], m), cz = __ddiv_rn(S[3 * i + 2], m);
-    const double half = ldexp(L0, -(lvl + 1));
-    const double rx = (double)(2 * (uint64_t)compact3(pre) + 1) * half;
-    const double ry = (double)(2 * (uint64_t)compact3(pre >> 1) + 1) * half;
-    const double rz = (double)(2 * (uint64_t)compact3(pre >> 2) + 1) * half;
-    bcen[i] = make_float4((float)rx, (float)ry, (float)rz, (float)(2.0 * half));
-    bcom[i] = make_float4((float)__dsub_rn(cx, __dadd_rn(x0, rx)), (float)__dsub_rn(cy, __dadd_rn(y0, ry)),
-                          (float)__dsub_rn(cz, __dadd_rn(z0, rz)), (float)m);
-    blink[i] = make_int4((int)b.child[i], (int)b.nchild[i], (int)b.first[i], (int)b.count[i]);
-}
-
-// Leaf particles relative to their leaf centre (FP64 difference -> FP32).
-__global__ void k_leaf_particles(const float4 *__restrict__ cen, const int4 *__restrict__ link, int64_t total,
-                                 const uint32_t *__restrict__ perm, const double *__restrict__ pos,
-                                 const float *__restrict__ mass, double x0, double y0, double z0,
-                                 float4 *__restrict__ spart) {
-    int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (p >= total)
-        return;
-    int4 l = link[p];
-    if (!l.w)
-        return;
-    float4 c = cen[p];
-    double ax = __dadd_rn(x0, (double)c.x), ay = __dadd_rn(y0, (double)c.y), az = __dadd_rn(z0, (double)c.z);
-    for (int s = l.y; s < l.y + l.z; s++) {
-        uint32_t j = perm[s];
-        spart[s] = make_float4((float)__dsub_rn(pos[3 * j], ax), (float)__dsub_rn(pos[3 * j + 1], ay),
-                               (float)__dsub_rn(pos[3 * j + 2], az), mass[j]);
+    o.bcen[q] = cen;
+    o.bcom[q] = com;
+    o.blink[q] = make_int4(nch ? (int)pre2bfs[p + 1] : 0, (int)nch, (int)f, (int)c);
+    if (nch == 0) {  // leaf particles relative to the leaf centre (FP64 difference -> FP32)
+        const double ax = __dadd_rn(x0, (double)cen.x), ay = __dadd_rn(y0, (double)cen.y),
+                     az = __dadd_rn(z0, (double)cen.z);
+        for (uint32_t s = f; s < f + c; s++)
+            o.spart[s] = make_float4((float)__dsub_rn(spos[3 * s], ax), (float)__dsub_rn(spos[3 * s + 1], ay),
+                                     (float)__dsub_rn(spos[3 * s + 2], az), smass[s]);
     }
 }
 
@@ -493,7 +524,6 @@ int build_tree_device(Ctx *c, System *s, const double *pos_in, const float *mass
         hst->bbox[3 + a] = LLONG_MIN;
     }
     TPM_CUDA(cudaMemcpyAsync(dst, hst, sizeof(BuildState), cudaMemcpyHostToDevice, st));
-    const unsigned grid = (unsigned)(c->num_sms * 8);
 
     // ---- prepare, bounding box, root, keys, sort
     k_prepare<<<blocks_for(n), kThreads, 0, st>>>(pos_in, mass_in, n, s->bp.periodic, s->bp.box, s->bp.shift[0],
@@ -519,113 +549,104 @@ int build_tree_device(Ctx *c, System *s, const double *pos_in, const float *mass
     TPM_CUDA(cub::DeviceRadixSort::SortPairs(cub_tmp, sort_bytes, key_raw, s->key, idx_raw, s->perm, (int)n, 0,
                                              3 * kMaxLevel, st));
     count_cub_call();
-    k_rank<<<blocks_for(n), kThreads, 0, st>>>(s->perm, n, s->rank);
+    double *spos;
+    float *smass;
+    TPM_CHECK(tmp.get(&spos, 3 * n, st));
+    TPM_CHECK(tmp.get(&smass, n, st));
+    k_rank<<<blocks_for(n), kThreads, 0, st>>>(s->perm, n, s->pos, s->mass, s->rank, spos, smass);
     count_launch();
     TPM_CUDA(cudaGetLastError());
 
-    // ---- levels and monopoles, all on the device; retried with more node
-    // space in the rare case the first guess is too small
-    // node space: ~0.4 n nodes for B = 8, ~1.5 n for B = 1; an overflow retries
-    unsigned cap = (unsigned)std::min<int64_t>((B == 1 ? 2 * n : n) + 1024, 0x7fffffffLL);
-    LevelArrays b{};
-    double *M = nullptr, *S = nullptr;
-    AllocSet lv;
-    lv.ctx = c;
-    struct LvGuard {
-        AllocSet &t;
-        cudaStream_t st;
-        ~LvGuard() { t.release(st); }
-    } lguard{lv, st};
-    for (int attempt = 0;; attempt++) {
-        lv.release(st);
-        TPM_CHECK(lv.get(&b.first, cap, st));
-        TPM_CHECK(lv.get(&b.count, cap, st));
-        TPM_CHECK(lv.get(&b.child, cap, st));
-        TPM_CHECK(lv.get(&b.nchild, cap, st));
-        TPM_CHECK(lv.get(&b.level, cap, st));
-        TPM_CHECK(lv.get(&b.prefix, cap, st));
-        TPM_CHECK(lv.get(&b.parent, cap, st));
-        TPM_CHECK(lv.get(&b.arrive, cap, st));
-        TPM_CHECK(lv.get(&M, cap, st));
-        TPM_CHECK(lv.get(&S, 3 * (size_t)cap, st));
-        TPM_CUDA(cudaMemsetAsync(&dst->overflow, 0, sizeof(int), st));
-        TPM_CUDA(cudaMemsetAsync(dst->lcount, 0, sizeof(dst->lcount), st));
-        TPM_CUDA(cudaMemsetAsync(b.arrive, 0, (size_t)cap * sizeof(uint32_t), st));
-        k_level0<<<1, 32, 0, st>>>(b, dst, n);
-        count_launch();
-        for (int level = 0; level <= kMaxLevel; level++) {
-            k_split_level<<<grid, kThreads, 0, st>>>(s->key, b, dst, level, B, cap);
-            count_launch();
-        }
-        TPM_CUDA(cudaGetLastError());
-        TPM_CUDA(cudaMemcpyAsync(hst, dst, sizeof(BuildState), cudaMemcpyDeviceToHost, st));
-        TPM_CUDA(cudaStreamSynchronize(st));
-        if (hst->bad & 1) {
-            set_error("non-finite position");
-            return TPM_ENAN;
-        }
-        if (hst->bad & 4) {
-            set_error("masses must be finite and > 0");
-            return TPM_ENAN;
-        }
-        if (hst->bad & 2) {
-            set_error("periodic positions must lie in [0, box)");
-            return TPM_EINVAL;
-        }
-        uint64_t total = 0;
-        int maxlevel = 0;
-        for (int l = 0; l <= kMaxLevel; l++) {
-            total += hst->lcount[l];
-            if (hst->lcount[l])
-                maxlevel = l;
-        }
-        if (!hst->overflow) {
-            hst->total = (unsigned)total;
-            hst->maxlevel = maxlevel;
-            break;
-        }
-        // the count seen is a lower bound (subtrees below the cap's edge were
-        // not explored); no level holds more than min(8^l, n) nodes
-        uint64_t bound = 0;
-        for (int l = 0; l <= kMaxLevel; l++)
-            bound += std::min<uint64_t>(l < 21 ? uint64_t(1) << (3 * l) : UINT64_MAX, (uint64_t)n);
-        bound = std::min<uint64_t>(bound, 0x7fffffffULL);
-        if (attempt >= 5 || cap >= bound) {
-            set_error("tree node space overflow (at least %llu nodes needed)", (unsigned long long)total);
-            return TPM_ECUDA;
-        }
-        cap = (unsigned)std::min<uint64_t>(std::max<uint64_t>(4 * total, 2 * (uint64_t)cap) + 1024, bound);
+    // ---- node counts per particle and their scan: the pre-order indices
+    int8_t *pre_max, *suf_max;
+    uint8_t *top_level, *leaf_level;
+    uint32_t *cnt, *base;
+    TPM_CHECK(tmp.get(&pre_max, n, st));
+    TPM_CHECK(tmp.get(&suf_max, n, st));
+    TPM_CHECK(tmp.get(&top_level, n, st));
+    TPM_CHECK(tmp.get(&leaf_level, n, st));
+    TPM_CHECK(tmp.get(&cnt, n + 1, st));
+    TPM_CHECK(tmp.get(&base, n + 1, st));
+    k_window_max<<<blocks_for((n + B) / ((int64_t)B + 1)), kThreads, 0, st>>>(s->key, n, B, pre_max, suf_max);
+    count_launch();
+    TPM_CUDA(cudaGetLastError());
+    TPM_CUDA(cudaMemsetAsync(cnt + n, 0, sizeof(uint32_t), st));
+    k_node_counts<<<blocks_for(n), kThreads, 0, st>>>(s->key, n, B, pre_max, suf_max, top_level, leaf_level, cnt);
+    count_launch();
+    TPM_CUDA(cudaGetLastError());
+    size_t scan_bytes = 0;
+    TPM_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, scan_bytes, cnt, base, (int)(n + 1), st));
+    void *scan_tmp = cub_tmp;
+    if (scan_bytes > sort_bytes)
+        TPM_CHECK(tmp.get((char **)&scan_tmp, scan_bytes, st));
+    TPM_CUDA(cub::DeviceScan::ExclusiveSum(scan_tmp, scan_bytes, cnt, base, (int)(n + 1), st));
+    count_cub_call();
+    TPM_CUDA(cudaMemcpyAsync(hst, dst, sizeof(BuildState), cudaMemcpyDeviceToHost, st));
+    TPM_CUDA(cudaMemcpyAsync(&hst->total, base + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    TPM_CUDA(cudaStreamSynchronize(st));
+    if (hst->bad & 1) {
+        set_error("non-finite position");
+        return TPM_ENAN;
+    }
+    if (hst->bad & 4) {
+        set_error("masses must be finite and > 0");
+        return TPM_ENAN;
+    }
+    if (hst->bad & 2) {
+        set_error("periodic positions must lie in [0, box)");
+        return TPM_EINVAL;
     }
     for (int a = 0; a < 3; a++)
         s->x0[a] = hst->x0[a];
     s->L0 = hst->L0;
     const int64_t nn = hst->total;
     s->nnodes = nn;
-    s->maxlevel = hst->maxlevel;
+
+    // ---- nodes in pre-order
+    NodeArrays t{};
+    double *M, *S;
+    TPM_CHECK(tmp.get(&t.first, nn, st));
+    TPM_CHECK(tmp.get(&t.count, nn, st));
+    TPM_CHECK(tmp.get(&t.skip, nn, st));
+    TPM_CHECK(tmp.get(&t.parent, nn, st));
+    TPM_CHECK(tmp.get(&t.nchild, nn, st));
+    TPM_CHECK(tmp.get(&t.arrive, nn, st));
+    TPM_CHECK(tmp.get(&t.order, nn, st));
+    TPM_CHECK(tmp.get(&t.level, nn, st));
+    TPM_CHECK(tmp.get(&t.prefix, nn, st));
+    TPM_CHECK(tmp.get(&M, nn, st));
+    TPM_CHECK(tmp.get(&S, 3 * nn, st));
+    TPM_CUDA(cudaMemsetAsync(t.nchild, 0, nn * sizeof(uint32_t), st));
+    TPM_CUDA(cudaMemsetAsync(t.arrive, 0, nn * sizeof(uint32_t), st));
+    k_nodes<<<blocks_for(n), kThreads, 0, st>>>(s->key, n, base, top_level, leaf_level, t);
+    count_launch();
+    TPM_CUDA(cudaGetLastError());
+
+    // ---- breadth-first order: a stable sort of the pre-order by level
+    uint8_t *level_sorted;
+    uint32_t *bfs2pre, *pre2bfs;
+    TPM_CHECK(tmp.get(&level_sorted, nn, st));
+    TPM_CHECK(tmp.get(&bfs2pre, nn, st));
+    TPM_CHECK(tmp.get(&pre2bfs, nn, st));
+    size_t lsort_bytes = 0;
+    TPM_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, lsort_bytes, t.level, level_sorted, t.order, bfs2pre, (int)nn,
+                                             0, 5, st));
+    void *lsort_tmp = cub_tmp;
+    if (lsort_bytes > sort_bytes)
+        TPM_CHECK(tmp.get((char **)&lsort_tmp, lsort_bytes, st));
+    TPM_CUDA(cub::DeviceRadixSort::SortPairs(lsort_tmp, lsort_bytes, t.level, level_sorted, t.order, bfs2pre,
+                                             (int)nn, 0, 5, st));
+    count_cub_call();
+    k_invert<<<blocks_for(nn), kThreads, 0, st>>>(bfs2pre, nn, pre2bfs);
+    count_launch();
+    TPM_CUDA(cudaGetLastError());
 
     // ---- monopoles, bottom-up in one pass
-    k_multipole<<<blocks_for(nn), kThreads, 0, st>>>(b, nn, s->perm, s->pos, s->mass, M, S);
+    k_multipole<<<blocks_for(nn), kThreads, 0, st>>>(t, nn, pre2bfs, spos, smass, M, S);
     count_launch();
     TPM_CUDA(cudaGetLastError());
 
-    // ---- pre-order
-    uint64_t *okey, *pkey;
-    uint32_t *oval, *pre2bfs;
-    TPM_CHECK(tmp.get(&okey, nn, st));
-    TPM_CHECK(tmp.get(&pkey, nn, st));
-    TPM_CHECK(tmp.get(&oval, nn, st));
-    TPM_CHECK(tmp.get(&pre2bfs, nn, st));
-    k_preorder_keys<<<blocks_for(nn), kThreads, 0, st>>>(b, nn, okey, oval);
-    count_launch();
-    TPM_CUDA(cudaGetLastError());
-    size_t sb2 = 0;
-    TPM_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, sb2, okey, pkey, oval, pre2bfs, (int)nn, 0, 37, st));
-    void *cub_tmp2 = cub_tmp;
-    if (sb2 > sort_bytes)
-        TPM_CHECK(tmp.get((char **)&cub_tmp2, sb2, st));
-    TPM_CUDA(cub::DeviceRadixSort::SortPairs(cub_tmp2, sb2, okey, pkey, oval, pre2bfs, (int)nn, 0, 37, st));
-    count_cub_call();
-
+    // ---- walk tables
     TPM_CHECK(s->mem.get(&s->ncen, nn, st));
     TPM_CHECK(s->mem.get(&s->ncom, nn, st));
     TPM_CHECK(s->mem.get(&s->nlink, nn, st));
@@ -633,19 +654,13 @@ int build_tree_device(Ctx *c, System *s, const double *pos_in, const float *mass
     TPM_CHECK(s->mem.get(&s->nprefix, nn, st));
     TPM_CHECK(s->mem.get(&s->nmass, nn, st));
     TPM_CHECK(s->mem.get(&s->ncomd, 3 * nn, st));
-    NodeOut o{s->ncen, s->ncom, s->nlink, s->nlevel, s->nprefix, s->nmass, s->ncomd};
-    k_finalize<<<blocks_for(nn), kThreads, 0, st>>>(b, pkey, pre2bfs, nn, M, S, s->x0[0], s->x0[1], s->x0[2], s->L0, o);
-    count_launch();
-    TPM_CUDA(cudaGetLastError());
     TPM_CHECK(s->mem.get(&s->bcen, nn, st));
     TPM_CHECK(s->mem.get(&s->bcom, nn, st));
     TPM_CHECK(s->mem.get(&s->blink, nn, st));
-    k_finalize_bfs<<<blocks_for(nn), kThreads, 0, st>>>(b, nn, M, S, s->x0[0], s->x0[1], s->x0[2], s->L0, s->bcen,
-                                                        s->bcom, s->blink);
-    count_launch();
-    TPM_CUDA(cudaGetLastError());
-    k_leaf_particles<<<blocks_for(nn), kThreads, 0, st>>>(s->ncen, s->nlink, nn, s->perm, s->pos, s->mass, s->x0[0],
-                                                          s->x0[1], s->x0[2], s->spart);
+    NodeOut o{s->ncen,  s->ncom, s->nlink, s->nlevel, s->nprefix, s->nmass,
+              s->ncomd, s->bcen, s->bcom,  s->blink,  s->spart};
+    k_finalize<<<blocks_for(nn), kThreads, 0, st>>>(t, pre2bfs, nn, M, S, spos, smass, s->x0[0], s->x0[1], s->x0[2],
+                                                    s->L0, o);
     count_launch();
     TPM_CUDA(cudaGetLastError());
     return TPM_OK;

@@ -92,7 +92,6 @@ struct System {
     int64_t n = 0, nnodes = 0;
     tpm_build_params bp{};
     double x0[3] = {0, 0, 0}, L0 = 1.0;
-    int maxlevel = 0;
     AllocSet mem;
 
     // particles

@@ -239,7 +239,8 @@ def serve_per_request(ctx: Context, source, requests, theta: float = 0.5, alpha:
                       policy: str = "adaptive", realtime: bool = True):
     """Baseline: requests in arrival order, each with its own build (if the
     system is not resident), ``tpm_compute_forces`` call and synchronisation;
-    LRU eviction under the same budget."""
+    LRU eviction under the same budget, for a build or for the scratch memory
+    of a force call."""
     import torch
 
     dev = torch.device("cuda", ctx.device)
@@ -273,7 +274,16 @@ def serve_per_request(ctx: Context, source, requests, theta: float = 0.5, alpha:
         else:
             fp = ForceParams(crit=CRIT_RELATIVE, alpha=alpha)
         r.criterion = fp.crit
-        acc, pot, nint = system.compute_forces(active_ids=ids_d, a_old=aold[part].contiguous(), fp=fp)
+        while True:
+            try:
+                acc, pot, nint = system.compute_forces(active_ids=ids_d, a_old=aold[part].contiguous(), fp=fp)
+                break
+            except TreePMError as e:
+                # the call's scratch does not fit: evict another system
+                victim = next((sid for sid in resident if sid != r.sid), None)
+                if e.status != _EBUDGET or victim is None:
+                    raise
+                resident.pop(victim)[0].release()
         aold[part] = torch.linalg.vector_norm(acc, dim=1)
         valid[r.ids] = True
         r.acc, r.pot, r.n_int = acc.cpu().numpy(), pot.cpu().numpy(), nint.cpu().numpy()
