@@ -267,7 +267,8 @@ __global__ void __launch_bounds__(kWalkThreads)
 // bounds (a node is "accepted by all" only if the criterion accepts it even
 // for the box point closest to its centre of mass, and so on), and keeps the
 // per-particle decision only for the nodes where the bounds leave doubt:
-// those are resolved lane by lane exactly as in the lane walk.  The decisions
+// those are resolved lane by lane exactly as in the lane walk, and a lane that
+// accepts such a node adds its monopole right away.  The decisions
 // -- hence every particle's interaction set -- are the per-particle walk's.
 // Accepted nodes and opened leaves go to a per-warp list in shared memory,
 // tagged with the lanes they apply to, and the lanes then sweep the list in a
@@ -685,8 +686,14 @@ __device__ __forceinline__ void group_walk(const TreeView &T, const WalkConsts &
         }
         sn = min(sn + __popc(bp), kStackCap);
 
-        // ---- nodes the bounds could not decide: per-particle decisions; the
-        // node's record comes from the lane that classified it
+        // ---- nodes the bounds could not decide: per-particle decisions, as in
+        // the lane walk.  A lane that accepts the node adds its monopole at
+        // once, with the r^2 its criterion used; only opened nodes go on.  The
+        // node's record comes from the lane that classified it; its links are
+        // packed as (first child, child count) for an internal node and
+        // (first particle, particle count | leaf bit) for a leaf.
+        const int lk0 = is_leaf ? Lk.z : Lk.x;
+        const int lk1 = is_leaf ? (int)((uint32_t)Lk.w | 0x80000000u) : Lk.y;
         unsigned mixed = __ballot_sync(FULL, cls == kMixed);
         while (mixed) {
             const int t = __ffs(mixed) - 1;
@@ -696,8 +703,7 @@ __device__ __forceinline__ void group_walk(const TreeView &T, const WalkConsts &
                         MCz = __shfl_sync(FULL, C.z, t), L = __shfl_sync(FULL, C.w, t);
             const float MOx = __shfl_sync(FULL, O.x, t), MOy = __shfl_sync(FULL, O.y, t),
                         MOz = __shfl_sync(FULL, O.z, t), MOm = __shfl_sync(FULL, O.w, t);
-            const int Lx = __shfl_sync(FULL, Lk.x, t), Ly = __shfl_sync(FULL, Lk.y, t),
-                      Lz = __shfl_sync(FULL, Lk.z, t), Lw = __shfl_sync(FULL, Lk.w, t);
+            const int l0 = __shfl_sync(FULL, lk0, t), l1 = __shfl_sync(FULL, lk1, t);
             const bool act = (mm & lanebit) != 0u;
             const float dx = MCx - gcx, dy = MCy - gcy, dz = MCz - gcz;  // exact
             float px = xox - dx, py = xoy - dy, pz = xoz - dz;
@@ -723,41 +729,33 @@ __device__ __forceinline__ void group_walk(const TreeView &T, const WalkConsts &
             const bool guard = k.box_guard && fabsf(px) <= gl && fabsf(py) <= gl && fabsf(pz) <= gl;
             const bool crit = RELATIVE ? (MOm * L * L > thr * r2 * r2) : (L * L > thr * r2);
             const bool open = act && !far && (guard || crit);
-            const unsigned am = __ballot_sync(FULL, act && !far && !open);
+            if (act && !far && !open) {
+                pair_term<TREEPM>(rx, ry, rz, r2, MOm, k, ax, ay, az, ph);
+                cnt++;
+            }
             const unsigned om = __ballot_sync(FULL, open);
-            float wx = dx, wy = dy, wz = dz;  // node centre, group-centred nearest image
-            if (PERIODIC) {
-                wx = wrap_min_image(wx, k);
-                wy = wrap_min_image(wy, k);
-                wz = wrap_min_image(wz, k);
-            }
-            const bool wflag = PERIODIC && (wide || L > k.bigL);
-            if (am) {
-                const bool full = am == valid_mask;
-                const int at = full ? nf : kNodeCap - 1 - np;
-                if (lane == 0) {
-                    sh.nsrc[at] = make_float4(wx + MOx, wy + MOy, wz + MOz, MOm);
-                    sh.nmask[at] = am;
-                    sh.nwrap[at] = wflag ? 1 : 0;
-                }
-                nf += full ? 1 : 0;
-                np += full ? 0 : 1;
-            }
             if (om) {
-                if (Ly > 0) {
+                if (l1 >= 0) {
                     if (lane == 0) {
                         if (sn < kStackCap) {
-                            sh.stack[sn] = make_uint2((uint32_t)Lx, om);
-                            sh.scount[sn] = (uint8_t)Ly;
+                            sh.stack[sn] = make_uint2((uint32_t)l0, om);
+                            sh.scount[sn] = (uint8_t)l1;
                         } else {
                             atomicOr(err, 2);
                         }
                     }
                     sn = min(sn + 1, kStackCap);
                 } else {
+                    float wx = dx, wy = dy, wz = dz;  // node centre, group-centred nearest image
+                    if (PERIODIC) {
+                        wx = wrap_min_image(wx, k);
+                        wy = wrap_min_image(wy, k);
+                        wz = wrap_min_image(wz, k);
+                    }
+                    const bool wflag = PERIODIC && (wide || L > k.bigL);
                     if (lane == 0) {
-                        sh.lsrc[nl] = make_float4(wx, wy, wz, __int_as_float(Lz));
-                        sh.lmeta[nl] = make_uint2(om, (wflag ? kLeafWrap : 0u) | (uint32_t)Lw);
+                        sh.lsrc[nl] = make_float4(wx, wy, wz, __int_as_float(l0));
+                        sh.lmeta[nl] = make_uint2(om, (wflag ? kLeafWrap : 0u) | ((uint32_t)l1 & kLeafCount));
                     }
                     nl++;
                 }
