@@ -144,6 +144,7 @@ def run_ours(args, rank, world):
     import torch
 
     import paper_1909_04667_gb300 as tpm
+    from paper_1909_04667_gb300 import shard
 
     dev = torch.device("cuda", 0 if world == 1 else int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
@@ -202,11 +203,7 @@ def run_ours(args, rank, world):
         t_step.append(e[0].elapsed_time(e[2]))
     if world > 1:
         torch.distributed.barrier()
-    ms = sum(t_step) / len(t_step)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = shard.max_over_ranks(sum(t_step) / len(t_step), device=dev)
     interactions = int(nint_buf.to(torch.int64).sum().item())
     walk_ms = statistics.mean(t_walk)
     build_ms = statistics.mean(t_build)
@@ -227,7 +224,7 @@ def run_ours(args, rank, world):
         sy.compute_forces(a_old=aold_h, fp=fp_rel, acc=acc_h, pot=pot_h, want_nint=False)
         sy.release()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_ms = statistics.median(e2e_ms)
+    e2e_ms = shard.max_over_ranks(statistics.median(e2e_ms), device=dev)
     h2d = pos.nbytes + mass.nbytes + aold_h.numel() * 4
     d2h = acc_h.numel() * 4 + pot_h.numel() * 4
 
@@ -257,10 +254,12 @@ def run_ours(args, rank, world):
         interactions_per_s=world * interactions / (walk_ms * 1e-3),
         interactions_per_particle=interactions / n,
         build_ms=build_ms, walk_ms=walk_ms,
-        e2e={"value": n / (e2e_ms * 1e-3), "unit": "forces/s", "ms_per_step": e2e_ms,
+        e2e={"value": world * n / (e2e_ms * 1e-3), "unit": "forces/s", "ms_per_step": e2e_ms,
              "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         roofline={"bound": "alu", "kernel": "k_walk_group (relative criterion)", "achieved": achieved,
                   "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": walk_traffic(),
+                  "frac_at_run_clock": (achieved / (fp32_peak * clocks["sm_mhz"] / sm_max)
+                                        if clocks.get("sm_mhz") else None),
                   "peak_kind": "FP32 CUDA-core peak = SMs x 128 x 2 x %.0f MHz (%s sm_max)" % (sm_max, pk_kind),
                   "algorithmic": "%d flops x %d useful interactions per launch" % (FLOPS_PER_INTERACTION,
                                                                                     interactions)},
@@ -569,9 +568,12 @@ def main():
 
             oracle.build()
             r = run_oracle_sample(65536)
+            r1 = run_oracle_sample(4096, nthreads=1)
             out["cpu_baseline"] = {"value": r["value"], "unit": "forces/s", "cores": cores(), "kind": "oracle",
                                    "sample": "whole tree build + relative walk of %d random active particles, "
-                                             "extrapolated to all 2^20" % r["sample"]}
+                                             "extrapolated to all 2^20" % r["sample"],
+                                   "single_core": {"value": r1["value"], "unit": "forces/s", "cores": 1,
+                                                   "sample": "the same with %d particles" % r1["sample"]}}
         print(json.dumps(out))
     if world > 1:
         import torch
