@@ -59,6 +59,7 @@ HERNQUIST = dict(n=1 << 20, seed=W.CONFIG_SEEDS[2], h=0.005, G=1.0, bucket=8, th
 SERVING = dict(seed=W.CONFIG_SEEDS[5], n_systems=48, n_requests=600, rate=200.0, nmin=1 << 12, nmax=1 << 20,
                overcommit=1.5, bytes_per_particle=118, round_ids=1 << 21)
 TIMEBINS = dict(nbins=8, seed=W.CONFIG_SEEDS[4], req_lo=64, req_hi=65536)
+HIERARCHY = dict(nbins=8, dt_tick=0.005, c_grav=0.025)
 ZELDOVICH = dict(ngrid=128, seed=W.CONFIG_SEEDS[3], pm_n=256, asmth=1.25, rcut=4.5, G=1.0, bucket=8, theta=0.5,
                  alpha=0.005)
 
@@ -232,6 +233,7 @@ def run_ours(args, rank, world):
     periodic = None if args.no_periodic else run_periodic(ctx, tpm, torch, dev, stream, flush,
                                                           max(2, min(args.steps, 5)))
     batching = None if args.no_batching else run_batching(ctx, tpm, torch, dev, stream, pos_d, mass_d)
+    hierarchy = None if args.no_hierarchy else run_hierarchy(ctx, tpm, torch, dev, stream)
 
     ctx.close()
     serving = None if args.no_serving else run_serving(tpm, torch, dev)
@@ -268,6 +270,7 @@ def run_ours(args, rank, world):
         clocks=clocks,
         periodic_treepm=periodic,
         batching=batching,
+        hierarchy=hierarchy,
         serving=serving,
     )
 
@@ -288,6 +291,39 @@ def timebin_requests(perm, bins, seed):
     ids = np.concatenate(ids).astype(np.int32)
     off = np.concatenate([[0], np.cumsum(np.concatenate(sizes))])
     return ids, off, np.asarray(subs)
+
+
+def run_hierarchy(ctx, tpm, torch, dev, stream):
+    """Hierarchical KDK time stepping of the Hernquist 2^20 set (cold start):
+    bins from the step criterion sqrt(2 C_grav eps / |a|), one tree build per
+    tick for the particles due, one whole cycle of 2^(nbins-1) ticks timed
+    after one warm-up cycle."""
+    from paper_1909_04667_gb300.integrate import Integrator
+
+    cfg, hc = HERNQUIST, HIERARCHY
+    pos, mass = hernquist_inputs()
+    sp = tpm.StepParams(dt_tick=hc["dt_tick"], nbins=hc["nbins"], c_grav=hc["c_grav"], eps=cfg["h"] / 2.8)
+    bp = tpm.BuildParams(G=cfg["G"], h=cfg["h"], shift=root_shift(0, 5), leaf_bucket=cfg["bucket"])
+    integ = Integrator(ctx, pos, np.zeros_like(pos), mass, bp, sp, tpm.ForceParams(crit=tpm.CRIT_BH, theta=cfg["theta"]),
+                       tpm.ForceParams(crit=tpm.CRIT_RELATIVE, alpha=cfg["alpha"]),
+                       shift=lambda t: root_shift(t, 5))
+    integ.run_cycle()
+    hist = np.bincount(integ.bins.cpu().numpy().astype(np.int64), minlength=hc["nbins"])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k0, _ = tpm.launch_counts()
+    e0.record(stream)
+    forces = integ.run_cycle()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    k1, _ = tpm.launch_counts()
+    ms = e0.elapsed_time(e1)
+    ticks = 1 << (hc["nbins"] - 1)
+    return {"workload": "hernquist_n2^20_kdk_%dbins_dt%g_Cgrav%g" % (hc["nbins"], hc["dt_tick"], hc["c_grav"]),
+            "ms_per_cycle": ms, "ticks_per_cycle": ticks, "forces_per_cycle": int(forces),
+            "forces_per_s": forces / (ms * 1e-3), "builds_per_cycle": ticks, "bin_occupancy": hist.tolist(),
+            "gpu_launches_per_cycle": int(k1 - k0),
+            "note": "all particles drift and the tree is rebuilt at every tick; forces for the particles due"}
 
 
 def run_batching(ctx, tpm, torch, dev, stream, pos_d, mass_d, reps=3):
@@ -547,6 +583,7 @@ def main():
     ap.add_argument("--bucket", type=int, default=None, help="leaf bucket B of the headline workload")
     ap.add_argument("--no-batching", action="store_true", help="skip the time-bin batching measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-hierarchy", action="store_true", help="skip the KDK time-bin hierarchy measurement")
     args = ap.parse_args()
     if args.bucket:
         HERNQUIST["bucket"] = args.bucket

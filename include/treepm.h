@@ -291,6 +291,66 @@ int tpm_tree_export(tpm_ctx *ctx, tpm_sys s, uint64_t *key, uint32_t *perm, uint
  * of the last tpm_pm_long_range on s.  Synchronous. */
 int tpm_pm_export(tpm_ctx *ctx, tpm_sys s, float *phi, int64_t count);
 
+/* ---------------------------------------------------------------------------
+ * Time stepping around the force path (Sec. 7.1-7.3).
+ *
+ * A cycle of length T is cut into 2^N ticks of dt_tick = T / 2^N
+ * (N = nbins - 1).  Bin b (0 <= b <= N) has the step dt_tick 2^(N - b): bin 0
+ * is the longest step, bin N the shortest.  Bin b is due at tick t (taken
+ * modulo 2^N) when t is a multiple of 2^(N - b).  A particle's step may not
+ * exceed sqrt(2 C_grav eps / |a|) (Sec. 7.1; the paper prints the inequality
+ * reversed, an upper bound is meant); it takes the bin of the largest step
+ * not above that.  Moving to a shorter step is always allowed, to a longer
+ * one only onto a bin that is due at the current tick (Sec. 7.2): a particle
+ * asking for a longer step that is not due takes the longest due step
+ * between the one it asks for and its current one.  Kick-drift-kick leapfrog
+ * (Sec. 7.3): each step opens and closes with a half kick v += a dt / 2, all
+ * particles drift every tick, and the tree is rebuilt at every tick for the
+ * forces on the particles due.  FP64 positions and velocities; every FP64
+ * update uses round-to-nearest multiplies and adds in a fixed order.
+ * --------------------------------------------------------------------------- */
+typedef struct {
+    double dt_tick; /* the shortest step, T / 2^(nbins - 1) (> 0) */
+    int32_t nbins;  /* number of bins, 1..31 */
+    double c_grav;  /* ErrTolIntAccuracy C_grav (> 0) */
+    double eps;     /* softening length of the criterion (> 0; eps = h / 2.8) */
+} tpm_step_params;
+
+/*
+ * Drift: x += v dt for n particles (pos, vel: n x 3 FP64, device memory).
+ * With periodic = 1 every coordinate is wrapped back into [0, box).
+ * Errors: TPM_EINVAL (null pointers, host memory, n < 0, non-finite dt,
+ * box <= 0 when periodic), TPM_ECUDA.
+ */
+int tpm_drift(tpm_ctx *ctx, double *pos, const double *vel, int64_t n, double dt, int32_t periodic, double box,
+              void *stream);
+
+/*
+ * The particles due at `tick`: their indices, ascending, into ids (device,
+ * room for n), and their number into *n_active (host; the call waits for the
+ * stream).  With a_old non-NULL, a_old[k] = amag[ids[k]] (device arrays) --
+ * the |a| of the previous force evaluation that the relative criterion needs.
+ *   bins  n time bins (int8, device), as written by tpm_kick.
+ * Errors: TPM_EINVAL (null pointers, host memory, n outside [1, 2^31 - 1],
+ * nbins outside [1, 31], tick < 0), TPM_EBUDGET (scratch), TPM_ECUDA.
+ */
+int tpm_active_set(tpm_ctx *ctx, const int8_t *bins, const float *amag, int64_t n, int64_t tick, int32_t nbins,
+                   uint32_t *ids, float *a_old, int64_t *n_active, void *stream);
+
+/*
+ * Kicks for the n_active particles ids[k] (< n; others are skipped) whose
+ * accelerations acc[k] (n_active x 3 FP32, in ids order) were just computed
+ * at `tick`: the closing half kick with the step of the particle's current
+ * bin (skipped when first = 1, the start of the integration), the new bin
+ * from the step criterion and the nesting rule (with first = 1 any bin may
+ * be taken), the opening half kick with the new step, and amag[i] = |a|
+ * (FP32) for the next relative criterion.  vel (n x 3 FP64), bins (n int8),
+ * amag (n FP32): device memory, updated in place.
+ * Errors: TPM_EINVAL (null pointers, host memory, bad params), TPM_ECUDA.
+ */
+int tpm_kick(tpm_ctx *ctx, const uint32_t *ids, int64_t n_active, int64_t n, const float *acc, double *vel,
+             int8_t *bins, float *amag, int64_t tick, const tpm_step_params *p, int32_t first, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

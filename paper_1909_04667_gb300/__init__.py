@@ -21,8 +21,8 @@ import numpy as np
 
 from . import _build
 
-__all__ = ["Context", "System", "Plan", "BuildParams", "ForceParams", "TreePMError", "lib_path", "CRIT_BH",
-           "CRIT_RELATIVE", "BATCH_PRESORTED"]
+__all__ = ["Context", "System", "Plan", "BuildParams", "ForceParams", "StepParams", "TreePMError", "lib_path",
+           "CRIT_BH", "CRIT_RELATIVE", "BATCH_PRESORTED"]
 
 CRIT_BH = 0
 CRIT_RELATIVE = 1
@@ -46,6 +46,10 @@ class _BuildParams(C.Structure):
 class _ForceParams(C.Structure):
     _fields_ = [("crit", C.c_int32), ("theta", C.c_double), ("alpha", C.c_double), ("box_guard", C.c_int32),
                 ("treepm", C.c_int32), ("pm_n", C.c_int32), ("asmth", C.c_double), ("rcut", C.c_double)]
+
+
+class _StepParams(C.Structure):
+    _fields_ = [("dt_tick", C.c_double), ("nbins", C.c_int32), ("c_grav", C.c_double), ("eps", C.c_double)]
 
 
 def lib_path() -> str:
@@ -87,6 +91,9 @@ def _load():
         "tpm_plan_sync_status": (i32, [vp, vp, vp]),
         "tpm_plan_autotune": (i32, [vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, C.c_uint32, i32, vp,
                                     C.POINTER(i32), C.POINTER(C.c_float)]),
+        "tpm_drift": (i32, [vp, vp, vp, i64, C.c_double, C.c_int32, C.c_double, vp]),
+        "tpm_active_set": (i32, [vp, vp, vp, i64, i64, C.c_int32, vp, vp, C.POINTER(i64), vp]),
+        "tpm_kick": (i32, [vp, vp, i64, i64, vp, vp, vp, vp, i64, C.POINTER(_StepParams), C.c_int32, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -154,6 +161,42 @@ class ForceParams:
     def _c(self):
         return _ForceParams(int(self.crit), self.theta, self.alpha, int(self.box_guard), int(self.treepm),
                             int(self.pm_n), self.asmth, self.rcut)
+
+
+@dataclass
+class StepParams:
+    """Time-bin hierarchy and step criterion (``tpm_step_params``)."""
+    dt_tick: float = 1e-3
+    nbins: int = 8
+    c_grav: float = 0.025
+    eps: float = 0.01 / 2.8
+
+    def _c(self):
+        return _StepParams(self.dt_tick, int(self.nbins), self.c_grav, self.eps)
+
+
+def drift(ctx: "Context", pos, vel, dt: float, periodic: bool = False, box: float = 1.0, stream=None):
+    """``tpm_drift``: pos += vel dt in place (n x 3 FP64 device tensors)."""
+    _check(_lib.tpm_drift(ctx._h, _ptr(pos), _ptr(vel), int(pos.shape[0]), float(dt), int(periodic), float(box),
+                          _stream(stream, ctx.device)))
+
+
+def active_set(ctx: "Context", bins, tick: int, nbins: int, ids, amag=None, a_old=None, stream=None) -> int:
+    """``tpm_active_set``: indices of the particles due at ``tick`` into ``ids``
+    (and their previous |a| into ``a_old``); returns how many."""
+    n = C.c_int64(0)
+    _check(_lib.tpm_active_set(ctx._h, _ptr(bins), _ptr(amag), int(bins.shape[0]), int(tick), int(nbins), _ptr(ids),
+                               _ptr(a_old), C.byref(n), _stream(stream, ctx.device)))
+    return n.value
+
+
+def kick(ctx: "Context", ids, n_active: int, acc, vel, bins, amag, tick: int, sp: StepParams, first: bool = False,
+         stream=None):
+    """``tpm_kick``: closing half kick, new bin, opening half kick for the
+    particles ``ids[:n_active]`` with accelerations ``acc`` (ids order)."""
+    cp = sp._c()
+    _check(_lib.tpm_kick(ctx._h, _ptr(ids), int(n_active), int(vel.shape[0]), _ptr(acc), _ptr(vel), _ptr(bins),
+                         _ptr(amag), int(tick), C.byref(cp), int(first), _stream(stream, ctx.device)))
 
 
 BATCH_PRESORTED = 1
