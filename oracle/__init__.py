@@ -311,6 +311,118 @@ def treepm(pos, mass, targets, box: float, ngrid: int, asmth: float, rcut_cells:
     return a_s + a_l, p_s + p_l, nint
 
 
+# ---------------------------------------------------------------- isolated PM
+def pm_region_isolated(pos):
+    """Mesh region of the nonperiodic PM (Sec. 3.3): a cube of side L_pm = the
+    tree root's side (smallest power of two >= 1.25 x the largest extent of
+    the bounding box; extent 1 for a single point) centred on the bounding
+    box, so that at least a tenth of L_pm stays free on every side.  Returns
+    (corner (3,), L_pm)."""
+    pos = np.asarray(pos, dtype=np.float64)
+    lo, hi = pos.min(axis=0), pos.max(axis=0)
+    ext = float(np.max(hi - lo))
+    if not ext > 0.0:
+        ext = 1.0
+    f, e = math.frexp(1.25 * ext)
+    side = math.ldexp(1.0, e - 1) if f == 0.5 else math.ldexp(1.0, e)
+    corner = (lo + hi) * 0.5 - 0.5 * side
+    return corner, side
+
+
+def pm_potential_isolated(pos, mass, corner, side: float, ngrid: int, rs: float, G: float = 1.0) -> np.ndarray:
+    """Long-range potential with nonperiodic boundaries (Sec. 3.3: zero padding
+    and the Green's function of isolated boundaries), FP64.
+
+    CIC masses on ngrid^3 mesh points x = corner + i dx (dx = side / ngrid)
+    inside a zero-padded (2 ngrid)^3 mesh; the potential is the convolution
+    Phi(p) = sum_q m_q g(p - q) with the long-range kernel of the Gaussian
+    split, g(r) = -G erf(r / 2 r_s) / r (g(0) = -G / (sqrt(pi) r_s)), sampled
+    at the mesh separations min(|i|, 2 ngrid - |i|) dx, so the circular
+    convolution of the padded mesh is the open one for every mesh point of
+    the unpadded region.  The CIC windows are divided out in k-space as in
+    the periodic mesh (W(k)^2, W = prod_a sinc^2(k_a dx / 2)).  Returns the
+    (2 ngrid)^3 potential; only [0, ngrid]^3 is physical."""
+    n2 = 2 * ngrid
+    dx = side / ngrid
+    t = (np.asarray(pos, dtype=np.float64) - np.asarray(corner)) * (ngrid / side)
+    i0 = np.floor(t)
+    f = t - i0
+    i0 = i0.astype(np.int64)
+    if i0.min() < 0 or i0.max() + 1 >= ngrid:
+        raise ValueError("particles outside the mesh region")
+    m = np.asarray(mass, dtype=np.float64)
+    rho = np.zeros(n2 ** 3)
+    for cx in (0, 1):
+        wx = f[:, 0] if cx else 1.0 - f[:, 0]
+        for cy in (0, 1):
+            wy = f[:, 1] if cy else 1.0 - f[:, 1]
+            for cz in (0, 1):
+                wz = f[:, 2] if cz else 1.0 - f[:, 2]
+                idx = ((i0[:, 0] + cx) * n2 + i0[:, 1] + cy) * n2 + i0[:, 2] + cz
+                np.add.at(rho, idx, m * wx * wy * wz)
+    rho = rho.reshape(n2, n2, n2)
+    d = np.minimum(np.arange(n2), n2 - np.arange(n2)) * dx
+    r = np.sqrt(d[:, None, None] ** 2 + d[None, :, None] ** 2 + d[None, None, :] ** 2)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        g = np.array([math.erf(v) for v in (r / (2.0 * rs)).ravel()]).reshape(r.shape) / r
+    g[0, 0, 0] = 1.0 / (math.sqrt(math.pi) * rs)
+    g *= -G
+    n = np.fft.fftfreq(n2, d=1.0 / n2)
+    nz = np.fft.rfftfreq(n2, d=1.0 / n2)
+    sx = np.sinc(n / n2)  # sinc(k dx / 2) with k = 2 pi n / (n2 dx)
+    sz = np.sinc(nz / n2)
+    w = (sx[:, None, None] * sx[None, :, None] * sz[None, None, :]) ** 2
+    phik = np.fft.rfftn(rho) * np.fft.rfftn(g) / (w * w)
+    return np.fft.irfftn(phik, s=(n2, n2, n2), axes=(0, 1, 2))
+
+
+def pm_interpolate_isolated(phi: np.ndarray, pos, corner, side: float, ngrid: int):
+    """4-point finite-difference force (a = -grad Phi) and the potential,
+    CIC-interpolated to ``pos`` from the physical part of an isolated mesh."""
+    dx = side / ngrid
+    grads = []
+    for ax in range(3):
+        d1 = np.roll(phi, -1, axis=ax) - np.roll(phi, 1, axis=ax)
+        d2 = np.roll(phi, -2, axis=ax) - np.roll(phi, 2, axis=ax)
+        grads.append(-((4.0 / 3.0) * d1 / 2.0 - (1.0 / 3.0) * d2 / 4.0) / dx)
+    n2 = phi.shape[0]
+    fields = [g.ravel() for g in grads] + [phi.ravel()]
+    t = (np.asarray(pos, dtype=np.float64) - np.asarray(corner)) * (ngrid / side)
+    i0 = np.floor(t)
+    f = t - i0
+    i0 = i0.astype(np.int64)
+    if i0.min() < 2 or i0.max() + 3 > ngrid:
+        raise ValueError("the difference stencil leaves the physical mesh")
+    out = np.zeros((len(i0), 4))
+    for cx in (0, 1):
+        wx = f[:, 0] if cx else 1.0 - f[:, 0]
+        for cy in (0, 1):
+            wy = f[:, 1] if cy else 1.0 - f[:, 1]
+            for cz in (0, 1):
+                wz = f[:, 2] if cz else 1.0 - f[:, 2]
+                idx = ((i0[:, 0] + cx) * n2 + i0[:, 1] + cy) * n2 + i0[:, 2] + cz
+                w = wx * wy * wz
+                for c in range(4):
+                    out[:, c] += w * fields[c][idx]
+    return out[:, :3], out[:, 3]
+
+
+def treepm_isolated(pos, mass, targets, ngrid: int, asmth: float, rcut_cells: float, G: float, h: float,
+                    crit: str = "bh", theta: float = 0.5, alpha: float = 0.0025, a_old=None, bucket: int = 8,
+                    shift=(0.0, 0.0, 0.0), nthreads: int = 0):
+    """TreePM with nonperiodic boundaries (Sec. 3.3, 3.4): short-range walk of
+    the open tree with the erfc split and cutoff, plus the isolated mesh;
+    r_s = asmth x the mesh spacing of ``pm_region_isolated``."""
+    corner, side = pm_region_isolated(pos)
+    rs = asmth * side / ngrid
+    tree = Tree(pos, mass, bucket=bucket, shift=shift)
+    a_s, p_s, nint = tree.walk(targets, G, h, crit=crit, theta=theta, alpha=alpha, a_old=a_old, treepm=True, rs=rs,
+                               rcut=rcut_cells * rs, nthreads=nthreads)
+    phi = pm_potential_isolated(pos, mass, corner, side, ngrid, rs, G)
+    a_l, p_l = pm_interpolate_isolated(phi, np.asarray(pos)[np.asarray(targets, dtype=np.int64)], corner, side, ngrid)
+    return a_s + a_l, p_s + p_l, nint
+
+
 # ---------------------------------------------------------------- insertion tree
 def insertion_tree(pos, x0, L0: float, bucket: int = 1, order=None):
     """The paper's construction (Sec. 3.1), brute force: start from the cubic
