@@ -60,6 +60,7 @@ SERVING = dict(seed=W.CONFIG_SEEDS[5], n_systems=48, n_requests=600, rate=200.0,
                overcommit=1.5, bytes_per_particle=118, round_ids=1 << 21)
 TIMEBINS = dict(nbins=8, seed=W.CONFIG_SEEDS[4], req_lo=64, req_hi=65536)
 HIERARCHY = dict(nbins=8, dt_tick=0.005, c_grav=0.025)
+ISOLATED = dict(pm_n=64, asmth=2.5, rcut=4.5)
 ZELDOVICH = dict(ngrid=128, seed=W.CONFIG_SEEDS[3], pm_n=256, asmth=1.25, rcut=4.5, G=1.0, bucket=8, theta=0.5,
                  alpha=0.005)
 
@@ -234,6 +235,8 @@ def run_ours(args, rank, world):
                                                           max(2, min(args.steps, 5)))
     batching = None if args.no_batching else run_batching(ctx, tpm, torch, dev, stream, pos_d, mass_d)
     hierarchy = None if args.no_hierarchy else run_hierarchy(ctx, tpm, torch, dev, stream)
+    isolated = None if args.no_isolated else run_isolated(ctx, tpm, torch, dev, stream, flush, pos_d, mass_d,
+                                                          max(2, min(args.steps, 5)))
 
     ctx.close()
     serving = None if args.no_serving else run_serving(tpm, torch, dev)
@@ -271,6 +274,7 @@ def run_ours(args, rank, world):
         periodic_treepm=periodic,
         batching=batching,
         hierarchy=hierarchy,
+        isolated_treepm=isolated,
         serving=serving,
     )
 
@@ -507,6 +511,45 @@ def run_periodic(ctx, tpm, torch, dev, stream, flush, steps):
             "interactions_per_particle": inter / n}
 
 
+def run_isolated(ctx, tpm, torch, dev, stream, flush, pos_d, mass_d, steps):
+    """TreePM with open boundaries on the Hernquist 2^20 set: zero-padded
+    (2 pm_n)^3 mesh over the root cube, r_s = a_s mesh cells; one step =
+    build + mesh + short-range relative walk with interpolation."""
+    cfg, ic = HERNQUIST, ISOLATED
+    n = pos_d.shape[0]
+    bp = lambda k: tpm.BuildParams(G=cfg["G"], h=cfg["h"], shift=root_shift(k, 6), leaf_bucket=cfg["bucket"])
+    common = dict(treepm=True, pm_n=ic["pm_n"], asmth=ic["asmth"], rcut=ic["rcut"])
+    fp_bh = tpm.ForceParams(crit=tpm.CRIT_BH, theta=cfg["theta"], **common)
+    fp_rel = tpm.ForceParams(crit=tpm.CRIT_RELATIVE, alpha=cfg["alpha"], **common)
+    s = ctx.build_tree(pos_d, mass_d, bp(0))
+    s.pm_long_range(fp_bh)
+    acc, pot, nint = s.compute_forces(fp=fp_bh)
+    s.release()
+    a_old = torch.linalg.vector_norm(acc, dim=1).contiguous()
+    res = []
+    for k in range(steps + 2):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        l2_flush(flush)
+        ev[0].record(stream)
+        sy = ctx.build_tree(pos_d, mass_d, bp(100 + k))
+        ev[1].record(stream)
+        sy.pm_long_range(fp_rel)
+        ev[2].record(stream)
+        sy.compute_forces(a_old=a_old, fp=fp_rel, acc=acc, pot=pot, n_int=nint)
+        ev[3].record(stream)
+        sy.release()
+        torch.cuda.synchronize()
+        if k >= 2:
+            res.append([ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])])
+    r = np.array(res).mean(0)
+    ms = float(r.sum())
+    inter = int(nint.to(torch.int64).sum().item())
+    return {"workload": "hernquist_n2^20_treepm_open_pm%d_padded%d^3_asmth%g_relative_alpha%g" % (
+                ic["pm_n"], 2 * ic["pm_n"], ic["asmth"], cfg["alpha"]),
+            "value": n / (ms * 1e-3), "unit": "forces/s", "ms_per_step": ms, "build_ms": float(r[0]),
+            "pm_ms": float(r[1]), "walk_interp_ms": float(r[2]), "interactions_per_particle": inter / n}
+
+
 # ------------------------------------------------------------------ CPU oracle
 def run_oracle_sample(sample: int, nthreads: int = 0):
     """The FP64 oracle (as it stands) on a bounded sample of the headline
@@ -584,6 +627,7 @@ def main():
     ap.add_argument("--no-batching", action="store_true", help="skip the time-bin batching measurement")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-hierarchy", action="store_true", help="skip the KDK time-bin hierarchy measurement")
+    ap.add_argument("--no-isolated", action="store_true", help="skip the open-boundary TreePM measurement")
     args = ap.parse_args()
     if args.bucket:
         HERNQUIST["bucket"] = args.bucket

@@ -2,14 +2,17 @@
  * treepm.h -- C ABI of libtreepm, a GB300 (sm_103a) implementation of the
  * TreePM gravitational force on the currently active particles, as described
  * in Weinberger, Springel & Pakmor, "The AREPO public code release"
- * (Sec. 3 gravity, Sec. 7.2 local time steps).
+ * (Sec. 3 gravity, Sec. 7.1-7.3 time stepping).
  *
  * The library builds an oct-tree with monopole moments for a particle set
  * (Sec. 3.1), keeps it resident on the GPU, and evaluates the force and
  * potential on any subset of "active" particles from the full mass
- * distribution (Sec. 7.3: an active particle interacts with all mass).  For a
- * periodic box the force is split into a short-range tree part and a
- * long-range particle-mesh part (Sec. 3.3, 3.4).
+ * distribution (Sec. 7.3: an active particle interacts with all mass).  The
+ * force may be split into a short-range tree part and a long-range
+ * particle-mesh part (Sec. 3.3, 3.4): always for a periodic box, optionally
+ * for open boundaries (zero-padded mesh).  Around the force path, drift,
+ * due-set and kick calls step a system through a power-of-two time-bin
+ * hierarchy (Sec. 7.1-7.3).
  *
  * Conventions shared by every call
  * --------------------------------
@@ -22,7 +25,7 @@
  *   out and synchronises the stream before returning; with device pointers a
  *   call is stream-ordered on `stream` (a cudaStream_t, NULL = legacy default
  *   stream) and returns once the work is enqueued (the tree build itself
- *   synchronises `stream` between tree levels).
+ *   synchronises `stream` once, to read the node count).
  * - The caller owns every buffer it passes.  Inputs are read during the call
  *   (host) or before the stream reaches the end of the call's work (device)
  *   and may be reused afterwards.  The library owns the resident trees and
@@ -79,7 +82,8 @@ typedef struct {
     double theta;       /* ErrTolTheta, used when crit = TPM_CRIT_BH (> 0) */
     double alpha;       /* ErrTolForceAcc, used when crit = TPM_CRIT_RELATIVE (>= 0) */
     int32_t box_guard;  /* 1: always open a node whose 1.2 L cube around its centre holds the particle */
-    int32_t treepm;     /* 1: short-range tree force + long-range PM (periodic systems only) */
+    int32_t treepm;     /* 1: short-range tree force + long-range PM (required for periodic systems; open
+                           systems use the zero-padded isolated mesh) */
     int32_t pm_n;       /* PMGRID: mesh points per side (power of two, 8..1024) */
     double asmth;       /* ASMTH a_s: split scale r_s = a_s box / pm_n */
     double rcut;        /* RCUT a_cut: tree cutoff radius a_cut r_s */
@@ -132,14 +136,21 @@ int tpm_build_tree(tpm_ctx *ctx, const double *pos, const float *mass, int64_t n
                    void *stream, tpm_sys *out);
 
 /*
- * Long-range particle-mesh potential of a periodic system (Sec. 3.3, 3.4):
- * CIC assignment of all mass onto pm_n^3 mesh points at x = i box / pm_n,
- * FFT, multiplication by -4 pi G / k^2 exp(-k^2 r_s^2) / W(k)^2 with the CIC
- * window W = prod_a sinc^2(k_a dx / 2) and the k = 0 mode removed (mean
- * density subtracted), inverse FFT.  The mesh stays with the system until the
+ * Long-range particle-mesh potential (Sec. 3.3, 3.4), r_s = asmth dx.
+ * Periodic systems: CIC assignment of all mass onto pm_n^3 mesh points at
+ * x = i dx, dx = box / pm_n, FFT, multiplication by -4 pi G / k^2
+ * exp(-k^2 r_s^2) / W(k)^2 with the CIC window W = prod_a sinc^2(k_a dx / 2)
+ * and the k = 0 mode removed (mean density subtracted), inverse FFT.
+ * Open boundaries (zero padding and the isolated Green's function): pm_n^3
+ * mesh points over a cube of the tree root's side L0 centred on the particles'
+ * bounding box (dx = L0 / pm_n), inside a zero-padded (2 pm_n)^3 mesh; the
+ * potential is the convolution of the CIC masses with the long-range kernel
+ * -G erf(r / 2 r_s) / r sampled at the padded mesh's circular separations,
+ * divided by W(k)^2 in k-space, k = 0 kept (pm_n <= 512).  Both: 4-point
+ * finite-difference force meshes.  The meshes stay with the system until the
  * next call or release; tpm_compute_forces with treepm = 1 interpolates from
- * it.  Errors: TPM_EINVAL (open system, bad pm_n / asmth), TPM_ENOSYS_HANDLE,
- * TPM_EBUDGET, TPM_ECUDA.
+ * them.  Errors: TPM_EINVAL (treepm = 0, bad pm_n / asmth / rcut),
+ * TPM_ENOSYS_HANDLE, TPM_EBUDGET, TPM_ECUDA.
  */
 int tpm_pm_long_range(tpm_ctx *ctx, tpm_sys s, const tpm_force_params *p, void *stream);
 
@@ -287,8 +298,10 @@ int tpm_tree_info(tpm_ctx *ctx, tpm_sys s, int64_t *n, int64_t *n_nodes, double 
 int tpm_tree_export(tpm_ctx *ctx, tpm_sys s, uint64_t *key, uint32_t *perm, uint8_t *level, uint64_t *prefix,
                     uint32_t *first, uint32_t *count, uint32_t *skip, double *mass, double *com, double *xtree);
 
-/* Host copy of the long-range mesh potential (pm_n^3 floats, C order x, y, z)
- * of the last tpm_pm_long_range on s.  Synchronous. */
+/* Host copy of the long-range mesh potential of the last tpm_pm_long_range on
+ * s: m^3 floats, C order x, y, z, with m = pm_n (periodic) or 2 pm_n (open
+ * boundaries: the zero-padded mesh, physical for indices <= pm_n).
+ * count must be m^3.  Synchronous. */
 int tpm_pm_export(tpm_ctx *ctx, tpm_sys s, float *phi, int64_t count);
 
 /* ---------------------------------------------------------------------------

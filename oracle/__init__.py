@@ -312,6 +312,16 @@ def treepm(pos, mass, targets, box: float, ngrid: int, asmth: float, rcut_cells:
 
 
 # ---------------------------------------------------------------- isolated PM
+def _erf(x: np.ndarray) -> np.ndarray:
+    """Elementwise FP64 erf (scipy's when installed, else the math module's)."""
+    try:
+        from scipy.special import erf
+
+        return erf(x)
+    except ImportError:
+        return np.vectorize(math.erf)(x)
+
+
 def pm_region_isolated(pos):
     """Mesh region of the nonperiodic PM (Sec. 3.3): a cube of side L_pm = the
     tree root's side (smallest power of two >= 1.25 x the largest extent of
@@ -364,7 +374,7 @@ def pm_potential_isolated(pos, mass, corner, side: float, ngrid: int, rs: float,
     d = np.minimum(np.arange(n2), n2 - np.arange(n2)) * dx
     r = np.sqrt(d[:, None, None] ** 2 + d[None, :, None] ** 2 + d[None, None, :] ** 2)
     with np.errstate(invalid="ignore", divide="ignore"):
-        g = np.array([math.erf(v) for v in (r / (2.0 * rs)).ravel()]).reshape(r.shape) / r
+        g = _erf(r / (2.0 * rs)) / r
     g[0, 0, 0] = 1.0 / (math.sqrt(math.pi) * rs)
     g *= -G
     n = np.fft.fftfreq(n2, d=1.0 / n2)

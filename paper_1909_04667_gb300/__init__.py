@@ -403,10 +403,12 @@ class System:
         out.update(info)
         return out
 
-    def pm_export(self, pm_n: int) -> np.ndarray:
-        phi = np.zeros(pm_n ** 3, np.float32)
+    def pm_export(self, mesh: int) -> np.ndarray:
+        """``tpm_pm_export``: the potential mesh, ``mesh`` points per side (pm_n
+        for a periodic system, 2 pm_n for the zero-padded mesh of an open one)."""
+        phi = np.zeros(mesh ** 3, np.float32)
         _check(_lib.tpm_pm_export(self.ctx._h, self.handle, phi.ctypes.data, phi.size))
-        return phi.reshape(pm_n, pm_n, pm_n)
+        return phi.reshape(mesh, mesh, mesh)
 
 
 def launch_counts():

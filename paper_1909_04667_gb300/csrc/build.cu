@@ -596,8 +596,11 @@ int build_tree_device(Ctx *c, System *s, const double *pos_in, const float *mass
         set_error("periodic positions must lie in [0, box)");
         return TPM_EINVAL;
     }
-    for (int a = 0; a < 3; a++)
+    for (int a = 0; a < 3; a++) {
         s->x0[a] = hst->x0[a];
+        s->bb_lo[a] = from_ordered_bits(hst->bbox[a]);
+        s->bb_hi[a] = from_ordered_bits(hst->bbox[3 + a]);
+    }
     s->L0 = hst->L0;
     const int64_t nn = hst->total;
     s->nnodes = nn;

@@ -122,8 +122,8 @@ extern "C" int tpm_compute_forces_noalloc(tpm_ctx *h, tpm_sys sid, const uint32_
         set_error("the relative criterion needs a_old");
         return TPM_EINVAL;
     }
-    if ((p->treepm != 0) != (s->bp.periodic != 0)) {
-        set_error("treepm forces need a periodic system and periodic systems need treepm");
+    if (s->bp.periodic && !p->treepm) {
+        set_error("periodic systems need treepm = 1");
         return TPM_EINVAL;
     }
     if (p->treepm && (!s->phi || s->pm_n != p->pm_n)) {

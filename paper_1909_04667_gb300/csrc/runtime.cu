@@ -104,21 +104,22 @@ int check_force_params(const System *s, const tpm_force_params *p) {
         set_error("alpha must be finite and >= 0");
         return TPM_EINVAL;
     }
-    if (s && (p->treepm != 0) != (s->bp.periodic != 0)) {
-        set_error("treepm forces need a periodic system and periodic systems need treepm");
+    if (s && s->bp.periodic && !p->treepm) {
+        set_error("periodic systems need treepm = 1");
         return TPM_EINVAL;
     }
     if (p->treepm) {
         int n = p->pm_n;
-        if (n < 8 || n > 1024 || (n & (n - 1))) {
-            set_error("pm_n must be a power of two in [8, 1024]");
+        const int nmax = (s && !s->bp.periodic) ? 512 : 1024;  // open boundaries: a (2 n)^3 padded mesh
+        if (n < 8 || n > nmax || (n & (n - 1))) {
+            set_error("pm_n must be a power of two in [8, %d]", nmax);
             return TPM_EINVAL;
         }
         if (!(p->asmth > 0.0) || !(p->rcut > 0.0) || !std::isfinite(p->asmth) || !std::isfinite(p->rcut)) {
             set_error("asmth and rcut must be finite and > 0");
             return TPM_EINVAL;
         }
-        if (s && p->rcut * p->asmth * s->bp.box / n >= 0.25 * s->bp.box) {
+        if (s && s->bp.periodic && p->rcut * p->asmth * s->bp.box / n >= 0.25 * s->bp.box) {
             set_error("cutoff radius must stay below a quarter of the box");
             return TPM_EINVAL;
         }
@@ -234,6 +235,9 @@ int tpm_destroy(tpm_ctx *h) {
         cufftDestroy(kv.second.first);
         cufftDestroy(kv.second.second);
     }
+    for (auto &kv : c->iso_green)
+        ctx_free(c, kv.second.p, kv.second.bytes, 0);
+    c->iso_green.clear();
     cudaStreamSynchronize(0);
     cudaMemPoolDestroy(c->pool);
     cudaFreeHost(c->pinned_state);
@@ -340,7 +344,7 @@ int tpm_pm_long_range(tpm_ctx *h, tpm_sys sid, const tpm_force_params *p, void *
     }
     TPM_CHECK(check_force_params(s, p));
     if (!p->treepm) {
-        set_error("tpm_pm_long_range needs treepm = 1 (periodic system)");
+        set_error("tpm_pm_long_range needs treepm = 1");
         return TPM_EINVAL;
     }
     TPM_CUDA(cudaSetDevice(c->device));
@@ -374,7 +378,7 @@ int tpm_compute_forces(tpm_ctx *h, tpm_sys sid, const uint32_t *active_ids, int6
         return TPM_EINVAL;
     }
     if (p->treepm) {
-        const double rs = p->asmth * s->bp.box / p->pm_n;
+        const double rs = p->asmth * pm_side(s) / p->pm_n;
         if (!s->phi || s->pm_n != p->pm_n || std::fabs(s->pm_rs - rs) > 1e-12 * rs || s->pm_G != s->bp.G) {
             set_error("no long-range mesh for these parameters: call tpm_pm_long_range first");
             return TPM_EINVAL;
@@ -625,9 +629,9 @@ int tpm_pm_export(tpm_ctx *h, tpm_sys sid, float *phi, int64_t count) {
         set_error("no long-range mesh: call tpm_pm_long_range first");
         return TPM_EINVAL;
     }
-    const int64_t ncell = (int64_t)s->pm_n * s->pm_n * s->pm_n;
+    const int64_t ncell = (int64_t)s->pm_mesh * s->pm_mesh * s->pm_mesh;
     if (count != ncell) {
-        set_error("count must be pm_n^3 = %lld", (long long)ncell);
+        set_error("count must be the mesh size^3 = %lld", (long long)ncell);
         return TPM_EINVAL;
     }
     TPM_CUDA(cudaSetDevice(c->device));

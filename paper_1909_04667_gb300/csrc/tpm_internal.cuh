@@ -6,6 +6,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <map>
 #include <mutex>
 #include <string>
 #include <unordered_map>
@@ -121,10 +122,16 @@ struct System {
     // walk's candidate stack overflowed (read and cleared by tpm_sync_status)
     int *err = nullptr;
 
-    // long-range mesh
+    double bb_lo[3] = {0, 0, 0}, bb_hi[3] = {0, 0, 0};  // bounding box of the tree positions
+
+    // long-range mesh: potential and x, y, z force meshes of pm_mesh^3 points
+    // (pm_mesh = pm_n, or 2 pm_n zero-padded for open boundaries) at
+    // pm_corner + i pm_side / pm_n
     AllocSet pm_mem;
     float *phi = nullptr;
     int pm_n = 0;
+    int pm_mesh = 0;
+    double pm_corner[3] = {0, 0, 0};
     double pm_rs = 0.0;
     double pm_G = 0.0;
 };
@@ -145,7 +152,14 @@ struct Ctx {
     // cached cuFFT plans (one pair per mesh size)
     std::unordered_map<int, std::pair<cufftHandle, cufftHandle>> fft_plans;
     std::unordered_map<int, size_t> fft_work_bytes;
+    // transforms of the isolated long-range kernel in mesh units, keyed by
+    // (padded mesh size, split scale in cells)
+    std::map<std::pair<int, double>, DevAlloc> iso_green;
 };
+
+// Side of the mesh region: the box (periodic) or the tree root's side, a
+// cube centred on the particles (open boundaries, zero-padded mesh).
+inline double pm_side(const System *s) { return s->bp.periodic ? s->bp.box : s->L0; }
 
 // ------------------------------------------------------------------ stages
 // Tree build (keys, sort, levels, multipoles, pre-order tables): fills s.

@@ -873,11 +873,11 @@ void launch(const System *s, const WalkRequest &r, const WalkConsts &k, bool lan
     }
 }
 
-// Kernel choice: the group walk for open boundaries, the lane walk for the
-// short-range TreePM walk (there the cutoff sphere cuts through most groups,
-// so the group bounds rarely decide and the lane walk is faster).  TPM_WALK=
-// lanes or group forces one for comparison; both make the same per-particle
-// decisions.
+// Kernel choice: the group walk for open boundaries (with or without the
+// TreePM split), the lane walk for the periodic short-range walk (there the
+// cutoff sphere, a few mean spacings wide, cuts through most groups, so the
+// group bounds rarely decide and the lane walk is faster).  TPM_WALK=lanes or
+// group forces one for comparison; both make the same per-particle decisions.
 int walk_override() {
     static int v = -1;
     if (v < 0) {
@@ -901,7 +901,7 @@ WalkConsts make_consts(const System *s, const tpm_force_params *p) {
     k.boxinv = (float)(1.0 / s->bp.box);
     k.bigL = (float)(0.25 * s->bp.box);
     if (p->treepm) {
-        const double rs = p->asmth * s->bp.box / p->pm_n;
+        const double rs = p->asmth * pm_side(s) / p->pm_n;
         const double rc = p->rcut * rs;
         k.rcut2 = (float)(rc * rc);
         k.inv2rs = (float)(1.0 / (2.0 * rs));
@@ -945,18 +945,22 @@ int walk_device(Ctx *, const System *s, const tpm_force_params *p, const WalkReq
     const WalkConsts k = make_consts(s, p);
     const bool per = s->bp.periodic != 0, rel = p->crit == TPM_CRIT_RELATIVE, tpm = p->treepm != 0;
     const int ov = walk_override();
-    const bool lanes = ov == 1 || (ov == 0 && tpm);
+    const bool lanes = ov == 1 || (ov == 0 && per);
     int *err = s->err;
     if (!per && !rel && !tpm)
         launch<false, false, false>(s, r, k, lanes, err, st);
     else if (!per && rel && !tpm)
         launch<false, true, false>(s, r, k, lanes, err, st);
+    else if (!per && !rel && tpm)
+        launch<false, false, true>(s, r, k, lanes, err, st);
+    else if (!per && rel && tpm)
+        launch<false, true, true>(s, r, k, lanes, err, st);
     else if (per && !rel && tpm)
         launch<true, false, true>(s, r, k, lanes, err, st);
     else if (per && rel && tpm)
         launch<true, true, true>(s, r, k, lanes, err, st);
     else {
-        set_error("unsupported walk mode (periodic systems need treepm = 1, open systems treepm = 0)");
+        set_error("unsupported walk mode (periodic systems need treepm = 1)");
         return TPM_EINVAL;
     }
     TPM_CUDA(cudaGetLastError());
