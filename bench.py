@@ -40,8 +40,8 @@ FLOPS_PER_INTERACTION = 20  # monopole pair term with potential, FP32 (the design doc
 # DRAM bytes (read + write) of one k_walk_group launch of the headline step,
 # from the ncu capture summarised in profiles/k_walk_group_hernquist_2p20_relative.md,
 # valid only for the walk source it was taken from
-WALK_TRAFFIC = {"bytes": 105.766144e6 + 13.333760e6,
-                "walk_cu_sha256": "15552c904a81ffd998e73b12d0d5f4c051b9588825d9ab0af4750493e4a8b567"}
+WALK_TRAFFIC = {"bytes": 98.628352e6 + 12.795648e6,
+                "walk_cu_sha256": "41a448d2611dc070086950d46b9094c2d0f7bfc79987d141e8f9ab4b9f357f70"}
 
 
 def walk_traffic():
