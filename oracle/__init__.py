@@ -54,7 +54,7 @@ def build(force: bool = False) -> str:
 class WalkParams(C.Structure):
     _fields_ = [("G", C.c_double), ("h", C.c_double), ("crit", C.c_int), ("theta", C.c_double),
                 ("alpha", C.c_double), ("box_guard", C.c_int), ("treepm", C.c_int), ("rs", C.c_double),
-                ("rcut", C.c_double)]
+                ("rcut", C.c_double), ("ewald", C.c_int), ("etab", C.c_void_p), ("ent", C.c_int)]
 
 
 def _load():
@@ -87,6 +87,10 @@ def _load():
             lib.orc_tree_walk.argtypes = [vp, i64, vp, vp, C.POINTER(WalkParams), vp, vp, vp, C.c_int]
             lib.orc_ewald.restype = None
             lib.orc_ewald.argtypes = [i64, vp, vp, i64, vp, d, d, d, d, C.c_int, vp, vp, C.c_int]
+            lib.orc_ewald_correction.restype = None
+            lib.orc_ewald_correction.argtypes = [d, d, d, d, vp]
+            lib.orc_ewald_table.restype = None
+            lib.orc_ewald_table.argtypes = [d, C.c_int, vp, C.c_int]
             lib.orc_num_threads.restype = C.c_int
             lib.orc_num_threads.argtypes = []
             _lib = lib
@@ -173,12 +177,16 @@ class Tree:
 
     def walk(self, targets, G: float, h: float, crit: str = "bh", theta: float = 0.7, alpha: float = 0.0025,
              a_old=None, box_guard: bool = True, treepm: bool = False, rs: float = 0.0, rcut: float = 0.0,
-             nthreads: int = 0):
+             ewald: bool = False, ewald_nt: int = 64, nthreads: int = 0):
         """Per-particle walk for ``targets`` (original indices).  Returns
-        (acc (k,3), pot (k,), n_int (k,)) in FP64 / uint32."""
+        (acc (k,3), pot (k,), n_int (k,)) in FP64 / uint32.  With ``ewald`` (a
+        periodic tree without ``treepm``) every term gets the Ewald correction
+        interpolated from ``ewald_table(box, ewald_nt)``."""
         targets = np.ascontiguousarray(targets, dtype=np.uint32)
         k = len(targets)
-        prm = WalkParams(G, h, 0 if crit == "bh" else 1, theta, alpha, int(box_guard), int(treepm), rs, rcut)
+        tab = ewald_table(self.box, ewald_nt) if ewald else None
+        prm = WalkParams(G, h, 0 if crit == "bh" else 1, theta, alpha, int(box_guard), int(treepm), rs, rcut,
+                         int(ewald), tab.ctypes.data if ewald else None, int(ewald_nt))
         ao = None
         if a_old is not None:
             ao = np.ascontiguousarray(a_old, dtype=np.float32)
@@ -192,6 +200,28 @@ class Tree:
 
 
 # ---------------------------------------------------------------- Ewald
+def ewald_correction(box: float, d) -> np.ndarray:
+    """(fx, fy, fz, phi): what the nearest image of a unit mass at separation
+    d (source - target) misses of the periodic field (G = 1, Sec. 3.1)."""
+    out = np.zeros(4)
+    _load().orc_ewald_correction(float(box), float(d[0]), float(d[1]), float(d[2]), _p(out))
+    return out
+
+
+_EWALD_TABLES = {}
+
+
+def ewald_table(box: float, nt: int = 64) -> np.ndarray:
+    """The correction on the grid (i, j, k) box / (2 nt), 0 <= i, j, k <= nt,
+    shape (nt+1, nt+1, nt+1, 4); computed once per (box, nt)."""
+    key = (float(box), int(nt))
+    if key not in _EWALD_TABLES:
+        tab = np.zeros((nt + 1, nt + 1, nt + 1, 4))
+        _load().orc_ewald_table(float(box), int(nt), _p(tab), 0)
+        _EWALD_TABLES[key] = tab
+    return _EWALD_TABLES[key]
+
+
 def ewald_params(box: float, tol_erfc: float = 4.1, rreal_frac: float = 0.3):
     """Splitting with alpha r_E = tol_erfc and the k cutoff set so that
     exp(-k^2 / 4 alpha^2) matches erfc(alpha r_E) (k_max = 2 alpha tol_erfc)."""

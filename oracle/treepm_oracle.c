@@ -19,6 +19,7 @@
  *   per-particle tree walk: geometric / relative opening criterion,
  *     1.2 L box guard, short-range cutoff                            [Sec. 3.1, 3.4]
  *   Ewald summation with neutralising background (periodic target)   [Sec. 2.2, 3.1]
+ *   Ewald correction of the periodic tree walk (table, trilinear)    [Sec. 3.1]
  *
  * Readings where the paper is silent or garbled are stated at each function.
  * The parity of every function is pinned by the CPU tests (closed forms,
@@ -424,7 +425,13 @@ typedef struct {
     int box_guard;     /* 1: apply the 1.2 L box rule */
     int treepm;        /* 1: short-range force only, with cutoff */
     double rs, rcut;   /* split scale r_s and cutoff radius a_cut r_s */
+    int ewald;         /* 1 (periodic tree, treepm = 0): add the Ewald correction */
+    const double *etab; /* correction table of orc_ewald_table, (ent+1)^3 x 4 */
+    int ent;           /* table intervals per axis over [0, box/2] */
 } orc_walk_params;
+
+static void orc_ewald_lookup(const orc_walk_params *p, double box, double dx, double dy, double dz, double f[3],
+                             double *phi);
 
 static inline double orc_wrap(double d, int periodic, double box)
 {
@@ -451,6 +458,20 @@ static inline void orc_pair(const orc_walk_params *p, double dx, double dy, doub
     acc[1] += m * dy * kf;
     acc[2] += m * dz * kf;
     *pot += m * kp;
+}
+
+/* Monopole / pair term of the periodic tree without the mesh: the nearest
+ * image (spline-softened) plus the Ewald correction at the same separation. */
+static inline void orc_pair_ewald(const orc_walk_params *p, double box, double dx, double dy, double dz, double m,
+                                  double acc[3], double *pot)
+{
+    orc_pair(p, dx, dy, dz, m, acc, pot);
+    double f[3], ph;
+    orc_ewald_lookup(p, box, dx, dy, dz, f, &ph);
+    acc[0] += m * f[0];
+    acc[1] += m * f[1];
+    acc[2] += m * f[2];
+    *pot += m * ph;
 }
 
 static void orc_walk_one(const orc_tree *t, int64_t i, double aold, const orc_walk_params *p, double acc[3],
@@ -496,8 +517,12 @@ static void orc_walk_one(const orc_tree *t, int64_t i, double aold, const orc_wa
                 open = p->G * t->mass[id] * L * L > p->alpha * aold * d2 * d2;
         }
         int leaf = (t->skip[id] == id + 1);
+        int ew = per && p->ewald && !p->treepm;
         if (!open) {
-            orc_pair(p, dx, dy, dz, t->mass[id], acc, pot);
+            if (ew)
+                orc_pair_ewald(p, box, dx, dy, dz, t->mass[id], acc, pot);
+            else
+                orc_pair(p, dx, dy, dz, t->mass[id], acc, pot);
             cnt++;
             id = t->skip[id];
         } else if (!leaf) {
@@ -511,11 +536,19 @@ static void orc_walk_one(const orc_tree *t, int64_t i, double aold, const orc_wa
                        qz = orc_wrap(t->x[3 * j + 2] - xi[2], per, box);
                 if (p->treepm && qx * qx + qy * qy + qz * qz > rcut2)
                     continue;
-                orc_pair(p, qx, qy, qz, (double)t->m[j], acc, pot);
+                if (ew)
+                    orc_pair_ewald(p, box, qx, qy, qz, (double)t->m[j], acc, pot);
+                else
+                    orc_pair(p, qx, qy, qz, (double)t->m[j], acc, pot);
                 cnt++;
             }
             id = t->skip[id];
         }
+    }
+    if (per && p->ewald && !p->treepm) { /* the particle's own images and background */
+        double f[3], ph;
+        orc_ewald_lookup(p, box, 0.0, 0.0, 0.0, f, &ph);
+        *pot += (double)t->m[i] * ph;
     }
     acc[0] *= p->G;
     acc[1] *= p->G;
@@ -788,6 +821,127 @@ void orc_ewald(int64_t n, const double *pos, const float *mass, int64_t nt, cons
     free(czlo);
     free(czhi);
     free(coff);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Ewald correction of the periodic tree (Sec. 3.1: the contributions of the */
+/* mirrored images, by the Ewald technique).  For a unit mass (G = 1) at     */
+/* separation d = x_source - x_target (nearest image), in a cube of side L  */
+/* with the mean density subtracted, the periodic acceleration of the target */
+/* is, with the split a = 2 / L,                                             */
+/*   a_E(d) = sum_n (d + nL)/s^3 [erfc(a s) + 2 a s/sqrt(pi) e^{-a^2 s^2}]   */
+/*            + (4 pi / V) sum_{k != 0} k/k^2 e^{-k^2/4a^2} sin(k.d),        */
+/*   s = |d + nL|, k = 2 pi m / L,                                           */
+/* and its potential                                                         */
+/*   phi_E(d) = -sum_n erfc(a s)/s - (4 pi / V) sum_k e^{-k^2/4a^2}/k^2     */
+/*              cos(k.d) + pi / (a^2 V).                                     */
+/* The correction is what the nearest image misses: a_E - d/|d|^3 and       */
+/* phi_E + 1/|d|; at d = 0 the force correction vanishes and the potential  */
+/* correction is the particle's own lattice term (the limit of the n = 0     */
+/* real-space term is -2a/sqrt(pi)).  Images |n| <= 4 and |m| <= 5 (both    */
+/* sums converged far below FP64 rounding at a = 2 / L).                     */
+/* ------------------------------------------------------------------------ */
+void orc_ewald_correction(double box, double dx, double dy, double dz, double out[4])
+{
+    double a = 2.0 / box, a2 = a * a, V = box * box * box, sqpi = sqrt(ORC_PI);
+    double f[3] = {0, 0, 0}, ph = 0.0;
+    double d2 = dx * dx + dy * dy + dz * dz;
+    for (int nx = -4; nx <= 4; nx++)
+        for (int ny = -4; ny <= 4; ny++)
+            for (int nz = -4; nz <= 4; nz++) {
+                double sx = dx + nx * box, sy = dy + ny * box, sz = dz + nz * box;
+                double s2 = sx * sx + sy * sy + sz * sz;
+                if (nx == 0 && ny == 0 && nz == 0) {
+                    if (d2 == 0.0) {
+                        ph += 2.0 * a / sqpi; /* lim_{s->0} erf(a s) / s */
+                        continue;
+                    }
+                    double s = sqrt(s2);
+                    /* n = 0: only the erfc part differs from the nearest image */
+                    double g = erfc(a * s) + 2.0 * a * s / sqpi * exp(-a2 * s2);
+                    f[0] += sx / (s2 * s) * (g - 1.0);
+                    f[1] += sy / (s2 * s) * (g - 1.0);
+                    f[2] += sz / (s2 * s) * (g - 1.0);
+                    ph += -erfc(a * s) / s + 1.0 / s;
+                    continue;
+                }
+                double s = sqrt(s2);
+                double g = erfc(a * s) + 2.0 * a * s / sqpi * exp(-a2 * s2);
+                f[0] += sx / (s2 * s) * g;
+                f[1] += sy / (s2 * s) * g;
+                f[2] += sz / (s2 * s) * g;
+                ph += -erfc(a * s) / s;
+            }
+    double tw = 2.0 * ORC_PI / box;
+    for (int mx = -5; mx <= 5; mx++)
+        for (int my = -5; my <= 5; my++)
+            for (int mz = -5; mz <= 5; mz++) {
+                int m2 = mx * mx + my * my + mz * mz;
+                if (m2 == 0 || m2 > 30)
+                    continue;
+                double kx = tw * mx, ky = tw * my, kz = tw * mz, k2 = tw * tw * m2;
+                double w = exp(-k2 / (4.0 * a2)) / k2;
+                double kd = kx * dx + ky * dy + kz * dz;
+                f[0] += 4.0 * ORC_PI / V * w * kx * sin(kd);
+                f[1] += 4.0 * ORC_PI / V * w * ky * sin(kd);
+                f[2] += 4.0 * ORC_PI / V * w * kz * sin(kd);
+                ph -= 4.0 * ORC_PI / V * w * cos(kd);
+            }
+    ph += ORC_PI / (a2 * V);
+    out[0] = f[0];
+    out[1] = f[1];
+    out[2] = f[2];
+    out[3] = ph;
+}
+
+/* The correction on the grid d = (i, j, k) box / (2 nt), 0 <= i, j, k <= nt,
+ * as (fx, fy, fz, phi) per point, x slowest. */
+void orc_ewald_table(double box, int nt, double *tab, int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0)
+        omp_set_num_threads(nthreads);
+#endif
+    int64_t m = nt + 1;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t e = 0; e < m * m * m; e++) {
+        int64_t i = e / (m * m), j = (e / m) % m, k = e % m;
+        double step = 0.5 * box / nt;
+        orc_ewald_correction(box, i * step, j * step, k * step, &tab[4 * e]);
+    }
+}
+
+/* Trilinear interpolation of the table at d, folded into [0, box/2]^3: the
+ * force correction is odd in its own component and even in the others, the
+ * potential correction even in all. */
+static void orc_ewald_lookup(const orc_walk_params *p, double box, double dx, double dy, double dz, double f[3],
+                             double *phi)
+{
+    double d[3] = {dx, dy, dz}, sg[3], u[3];
+    int i0[3];
+    int nt = p->ent;
+    for (int a = 0; a < 3; a++) {
+        sg[a] = d[a] < 0.0 ? -1.0 : 1.0;
+        double t = fabs(d[a]) * (2.0 * nt / box);
+        int q = (int)floor(t);
+        if (q >= nt)
+            q = nt - 1;
+        i0[a] = q;
+        u[a] = t - q;
+    }
+    int64_t m = nt + 1;
+    double v[4] = {0, 0, 0, 0};
+    for (int c = 0; c < 8; c++) {
+        int bx = c & 1, by = (c >> 1) & 1, bz = (c >> 2) & 1;
+        double w = (bx ? u[0] : 1.0 - u[0]) * (by ? u[1] : 1.0 - u[1]) * (bz ? u[2] : 1.0 - u[2]);
+        const double *e = &p->etab[4 * (((i0[0] + bx) * m + (i0[1] + by)) * m + (i0[2] + bz))];
+        for (int q = 0; q < 4; q++)
+            v[q] += w * e[q];
+    }
+    f[0] = sg[0] * v[0];
+    f[1] = sg[1] * v[1];
+    f[2] = sg[2] * v[2];
+    *phi = v[3];
 }
 
 int orc_num_threads(void)
