@@ -69,7 +69,7 @@ typedef enum {
 typedef struct {
     double G;            /* gravitational constant, > 0 */
     double h;            /* spline softening support, > 0: Newtonian beyond h; h = 2.8 eps (Sec. 3.2) */
-    int32_t periodic;    /* 0: open boundaries; 1: periodic cube [0, box)^3 (needs TreePM forces) */
+    int32_t periodic;    /* 0: open boundaries; 1: periodic cube [0, box)^3 */
     double box;          /* periodic box side (> 0; ignored when periodic = 0) */
     double shift[3];     /* random root placement in [0, 1)^3 drawn by the caller per build
                             (Sec. 3.1: randomised tree domain / random box shift) */
@@ -82,8 +82,8 @@ typedef struct {
     double theta;       /* ErrTolTheta, used when crit = TPM_CRIT_BH (> 0) */
     double alpha;       /* ErrTolForceAcc, used when crit = TPM_CRIT_RELATIVE (>= 0) */
     int32_t box_guard;  /* 1: always open a node whose 1.2 L cube around its centre holds the particle */
-    int32_t treepm;     /* 1: short-range tree force + long-range PM (required for periodic systems; open
-                           systems use the zero-padded isolated mesh) */
+    int32_t treepm;     /* 1: short-range tree force + long-range PM (open systems: the zero-padded isolated
+                           mesh); 0 on a periodic system: the tree with the Ewald correction */
     int32_t pm_n;       /* PMGRID: mesh points per side (power of two, 8..1024) */
     double asmth;       /* ASMTH a_s: split scale r_s = a_s box / pm_n */
     double rcut;        /* RCUT a_cut: tree cutoff radius a_cut r_s */
@@ -165,8 +165,14 @@ int tpm_pm_long_range(tpm_ctx *ctx, tpm_sys s, const tpm_force_params *p, void *
  * the spline-softened Newtonian force (Sec. 3.2), times the short-range
  * factor erfc(r/2r_s) + r/(sqrt(pi) r_s) exp(-r^2/4r_s^2) under TreePM, to
  * which the mesh force (4-point finite differences, CIC interpolation) is then
- * added.  Pair arithmetic is FP32 on positions taken relative to node and
- * group centres in FP64.
+ * added.  A periodic system with treepm = 0 is a pure tree with the Ewald
+ * correction (Sec. 3.1): every term is taken at the nearest image and gets
+ * the correction for all other images and the neutralising background,
+ * interpolated trilinearly from a table of the Ewald sums over [0, box/2]^3
+ * (65^3 points, built on the device once per context -- the first such call
+ * allocates it), and each potential gets the particle's own lattice term.
+ * Pair arithmetic is FP32 on positions taken relative to node and group
+ * centres in FP64.
  *   active_ids  n_active indices into the particle order given at build time,
  *               or NULL for all particles in that order (n_active must be n).
  *   a_old       n_active |a| from the previous evaluation (relative criterion),
@@ -197,7 +203,10 @@ int tpm_compute_forces(tpm_ctx *ctx, tpm_sys s, const uint32_t *active_ids, int6
  *     larger sets are rejected with TPM_EINVAL;
  *   - every array (active_ids, a_old, acc, pot, n_int) must be device memory
  *     (host arrays would need staging buffers): TPM_EINVAL otherwise;
- *   - the call is stream-ordered and never synchronises.
+ *   - the call is stream-ordered and never synchronises;
+ *   - on a periodic system without treepm the context's Ewald table must
+ *     exist already (any tpm_compute_forces call of that kind builds it):
+ *     TPM_EINVAL otherwise.
  * The first call on a device looks up the array's device address (it loads
  * the library's device code on that device), so make that first call before
  * any stream capture.  All calls share the one array, which keeps the last

@@ -122,10 +122,6 @@ extern "C" int tpm_compute_forces_noalloc(tpm_ctx *h, tpm_sys sid, const uint32_
         set_error("the relative criterion needs a_old");
         return TPM_EINVAL;
     }
-    if (s->bp.periodic && !p->treepm) {
-        set_error("periodic systems need treepm = 1");
-        return TPM_EINVAL;
-    }
     if (p->treepm && (!s->phi || s->pm_n != p->pm_n)) {
         set_error("no long-range mesh for these parameters: call tpm_pm_long_range first");
         return TPM_EINVAL;
@@ -172,6 +168,7 @@ extern "C" int tpm_compute_forces_noalloc(tpm_ctx *h, tpm_sys sid, const uint32_
     r.acc = acc;
     r.pot = pot;
     r.nint = n_int;
+    r.no_alloc = 1;
     if (p->treepm) {
         TPM_CHECK(pm_interp_device(c, s, r, st));
         r.accumulate = 1;

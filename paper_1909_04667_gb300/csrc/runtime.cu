@@ -104,10 +104,6 @@ int check_force_params(const System *s, const tpm_force_params *p) {
         set_error("alpha must be finite and >= 0");
         return TPM_EINVAL;
     }
-    if (s && s->bp.periodic && !p->treepm) {
-        set_error("periodic systems need treepm = 1");
-        return TPM_EINVAL;
-    }
     if (p->treepm) {
         int n = p->pm_n;
         const int nmax = (s && !s->bp.periodic) ? 512 : 1024;  // open boundaries: a (2 n)^3 padded mesh
@@ -238,6 +234,7 @@ int tpm_destroy(tpm_ctx *h) {
     for (auto &kv : c->iso_green)
         ctx_free(c, kv.second.p, kv.second.bytes, 0);
     c->iso_green.clear();
+    ctx_free(c, c->ewald_tab.p, c->ewald_tab.bytes, 0);
     cudaStreamSynchronize(0);
     cudaMemPoolDestroy(c->pool);
     cudaFreeHost(c->pinned_state);

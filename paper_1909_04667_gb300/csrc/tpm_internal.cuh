@@ -17,6 +17,7 @@
 namespace tpm {
 
 constexpr int kMaxLevel = 21;  // 21 bits per axis, 63-bit keys
+constexpr int kEwaldN = 64;    // Ewald correction table: kEwaldN intervals per axis over [0, L/2]
 
 // ------------------------------------------------------------------ errors
 void set_error(const char *fmt, ...);
@@ -155,7 +156,14 @@ struct Ctx {
     // transforms of the isolated long-range kernel in mesh units, keyed by
     // (padded mesh size, split scale in cells)
     std::map<std::pair<int, double>, DevAlloc> iso_green;
+    // Ewald correction of the periodic tree (unit box), and its value at d = 0
+    DevAlloc ewald_tab;
+    float ewald_phi0 = 0.0f;
 };
+
+// The context's Ewald correction table ((kEwaldN+1)^3 float4, unit box),
+// built on first use unless may_alloc is false.
+int ewald_table_for(Ctx *c, bool may_alloc, cudaStream_t st, const float4 **tab, float *phi0);
 
 // Side of the mesh region: the box (periodic) or the tree root's side, a
 // cube centred on the particles (open boundaries, zero-padded mesh).
@@ -177,6 +185,7 @@ struct WalkRequest {
     float *pot;                  // nullable
     uint32_t *nint;              // nullable
     int accumulate;              // 1: add to acc / pot instead of overwriting
+    int no_alloc = 0;            // 1: the call must not allocate device memory
 };
 
 int walk_device(Ctx *c, const System *s, const tpm_force_params *p, const WalkRequest &r, cudaStream_t st);

@@ -40,6 +40,12 @@ struct WalkConsts {
     float box, boxinv, bigL;
     float G;
     int box_guard;
+    // Ewald correction (periodic tree without the mesh): unit-box table of
+    // (ent + 1)^3 float4, index scale 2 ent / box, force and potential scales
+    // 1 / box^2 and 1 / box, and the own-lattice potential at d = 0
+    const float4 *etab;
+    float escale, efs, eps, ephi0;
+    int ent;
 };
 
 __device__ __forceinline__ uint32_t compact3w(uint64_t v) {
@@ -122,6 +128,38 @@ __device__ __forceinline__ float wrap_min_image(float d, const WalkConsts &k) {
     return fmaf(-k.box, rintf(d * k.boxinv), d);
 }
 
+// Ewald correction (Sec. 3.1) of mass m at nearest-image offset (rx, ry, rz)
+// (source minus target): trilinear interpolation of the table at |r| per
+// axis; the force correction is odd in its own component and even in the
+// others, the potential correction even in all.
+__device__ __forceinline__ void ewald_term(float rx, float ry, float rz, float m, const WalkConsts &k, float &ax,
+                                           float &ay, float &az, float &ph) {
+    const int top = k.ent - 1, m1 = k.ent + 1;
+    const float ux = fabsf(rx) * k.escale, uy = fabsf(ry) * k.escale, uz = fabsf(rz) * k.escale;
+    const int ix = min((int)ux, top), iy = min((int)uy, top), iz = min((int)uz, top);
+    const float fx = ux - (float)ix, fy = uy - (float)iy, fz = uz - (float)iz;
+    const float4 *t = k.etab + ((ix * m1 + iy) * m1 + iz);
+    const int sy = m1, sx = m1 * m1;
+    const float4 c000 = __ldg(t), c001 = __ldg(t + 1), c010 = __ldg(t + sy), c011 = __ldg(t + sy + 1);
+    const float4 c100 = __ldg(t + sx), c101 = __ldg(t + sx + 1), c110 = __ldg(t + sx + sy),
+                 c111 = __ldg(t + sx + sy + 1);
+    float v[4];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const float a00 = (&c000.x)[q] + fz * ((&c001.x)[q] - (&c000.x)[q]);
+        const float a01 = (&c010.x)[q] + fz * ((&c011.x)[q] - (&c010.x)[q]);
+        const float a10 = (&c100.x)[q] + fz * ((&c101.x)[q] - (&c100.x)[q]);
+        const float a11 = (&c110.x)[q] + fz * ((&c111.x)[q] - (&c110.x)[q]);
+        const float b0 = a00 + fy * (a01 - a00), b1 = a10 + fy * (a11 - a10);
+        v[q] = b0 + fx * (b1 - b0);
+    }
+    const float mf = m * k.efs;
+    ax = fmaf(mf, rx < 0.0f ? -v[0] : v[0], ax);
+    ay = fmaf(mf, ry < 0.0f ? -v[1] : v[1], ay);
+    az = fmaf(mf, rz < 0.0f ? -v[2] : v[2], az);
+    ph = fmaf(m * k.eps, v[3], ph);
+}
+
 template <bool PERIODIC, bool RELATIVE, bool TREEPM>
 __global__ void __launch_bounds__(kWalkThreads)
     k_walk(const float4 *__restrict__ ncen, const float4 *__restrict__ ncom, const int4 *__restrict__ nlink,
@@ -130,6 +168,7 @@ __global__ void __launch_bounds__(kWalkThreads)
            const uint32_t *__restrict__ sidx, const uint32_t *__restrict__ slot, const float *__restrict__ a_old,
            int64_t n_act, WalkConsts k, float *__restrict__ acc, float *__restrict__ pot,
            uint32_t *__restrict__ nint, int accumulate) {
+    constexpr bool EWALD = PERIODIC && !TREEPM;  // periodic tree without the mesh
     const int lane = threadIdx.x & 31;
     const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane);
     if (g0 >= n_act)
@@ -179,7 +218,7 @@ __global__ void __launch_bounds__(kWalkThreads)
         }
         const float L = C.w;
         float rx = O.x - px, ry = O.y - py, rz = O.z - pz;  // particle -> centre of mass
-        if (PERIODIC && L > k.bigL) {
+        if (PERIODIC && (EWALD || L > k.bigL)) {  // the Ewald table needs the nearest image
             rx = wrap_min_image(rx, k);
             ry = wrap_min_image(ry, k);
             rz = wrap_min_image(rz, k);
@@ -202,6 +241,8 @@ __global__ void __launch_bounds__(kWalkThreads)
         if (act && !open) {
             if (!far) {
                 pair_term<TREEPM>(rx, ry, rz, r2, O.w, k, ax, ay, az, ph);
+                if (EWALD)
+                    ewald_term(rx, ry, rz, O.w, k, ax, ay, az, ph);
                 cnt++;
             }
             skip_until = Lk.x;
@@ -221,7 +262,7 @@ __global__ void __launch_bounds__(kWalkThreads)
             const float4 P = __ldg(&spart[jj]);
             if (open && (uint32_t)jj != s) {
                 float qx = P.x - px, qy = P.y - py, qz = P.z - pz;
-                if (PERIODIC && L > k.bigL) {
+                if (PERIODIC && (EWALD || L > k.bigL)) {
                     qx = wrap_min_image(qx, k);
                     qy = wrap_min_image(qy, k);
                     qz = wrap_min_image(qz, k);
@@ -229,6 +270,8 @@ __global__ void __launch_bounds__(kWalkThreads)
                 const float q2 = fmaf(qx, qx, fmaf(qy, qy, qz * qz));
                 if (!TREEPM || q2 <= k.rcut2) {
                     pair_term<TREEPM>(qx, qy, qz, q2, P.w, k, ax, ay, az, ph);
+                    if (EWALD)
+                        ewald_term(qx, qy, qz, P.w, k, ax, ay, az, ph);
                     cnt++;
                 }
             }
@@ -237,6 +280,8 @@ __global__ void __launch_bounds__(kWalkThreads)
     }
     if (!valid)
         return;
+    if (EWALD)  // the particle's own images and the background
+        ph = fmaf(__ldg(&spart[s]).w * k.eps, k.ephi0, ph);
     const float G = k.G;
     if (accumulate) {
         acc[3 * (size_t)out] += G * ax;
@@ -339,6 +384,11 @@ __device__ __forceinline__ int classify_group(float4 C, float4 O, float gcx, flo
                 mz = fmaxf(fmaxf(bz0, -bz1), 0.0f);
     const float Mx = fmaxf(fabsf(bx0), fabsf(bx1)), My = fmaxf(fabsf(by0), fabsf(by1)),
                 Mz = fmaxf(fabsf(bz0), fabsf(bz1));
+    // without the cutoff (Ewald tree) nodes near half a box away occur: when a
+    // particle of the group may see another image of the centre or the
+    // centre of mass than the group-centred one, decide per particle
+    if (PERIODIC && !TREEPM && fmaxf(fmaxf(fmaxf(fx, fy), fz), fmaxf(fmaxf(Mx, My), Mz)) >= 0.5f * k.box * dn)
+        return kMixed;
     const float dmin2 = fmaf(mx, mx, fmaf(my, my, mz * mz));
     const float dmax2 = fmaf(Mx, Mx, fmaf(My, My, Mz * Mz));
     bool open_all, acc_all;
@@ -389,6 +439,8 @@ __device__ __forceinline__ void sweep_full(const GroupShared &sh, int nf, float 
                 rz = wrap_min_image(rz, k);
             }
             pair_term<TREEPM>(rx, ry, rz, fmaf(rx, rx, fmaf(ry, ry, rz * rz)), A.w, k, ax, ay, az, ph);
+            if (PERIODIC && !TREEPM)
+                ewald_term(rx, ry, rz, A.w, k, ax, ay, az, ph);
         }
         return;
     }
@@ -449,6 +501,8 @@ __device__ __forceinline__ void sweep_partial(const GroupShared &sh, int np, uns
             const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
             cnt += mine ? 1u : 0u;
             pair_term<TREEPM>(rx, ry, rz, mine ? r2 : 1.0f, mine ? E.w : 0.0f, k, ax, ay, az, ph);
+            if (PERIODIC && !TREEPM)
+                ewald_term(rx, ry, rz, mine ? E.w : 0.0f, k, ax, ay, az, ph);
         }
         return;
     }
@@ -508,6 +562,8 @@ __device__ __forceinline__ void sweep_leaves(const GroupShared &sh, int nl, unsi
             const float q2 = fmaf(qx, qx, fmaf(qy, qy, qz * qz));
             if (mine && (uint32_t)jj != self && (!TREEPM || q2 <= k.rcut2)) {
                 pair_term<TREEPM>(qx, qy, qz, q2, P.w, k, ax, ay, az, ph);
+                if (PERIODIC && !TREEPM)
+                    ewald_term(qx, qy, qz, P.w, k, ax, ay, az, ph);
                 cnt++;
             }
         }
@@ -534,6 +590,7 @@ __device__ __forceinline__ void group_walk(const TreeView &T, const WalkConsts &
                                            int64_t g0, int gcount, const float *__restrict__ a_old,
                                            float *__restrict__ acc, float *__restrict__ pot,
                                            uint32_t *__restrict__ nint, int accumulate, int *__restrict__ err) {
+    constexpr bool EWALD = PERIODIC && !TREEPM;  // periodic tree without the mesh
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const unsigned lanebit = 1u << lane;
@@ -654,7 +711,9 @@ __device__ __forceinline__ void group_walk(const TreeView &T, const WalkConsts &
         }
         __syncwarp();
         const bool is_leaf = Lk.y == 0;
-        const bool wrapf = PERIODIC && (wide || C.w > k.bigL);
+        // pair vectors are wrapped per lane when the group-centred image may
+        // not be the particle's nearest one, and always for the Ewald table
+        const bool wrapf = PERIODIC && (EWALD || wide || C.w > k.bigL);
         const bool e_acc = cls == kAccept, e_leaf = cls == kOpen && is_leaf, e_push = cls == kOpen && !is_leaf;
         const bool e_full = e_acc && nmask == valid_mask;
         const unsigned bf = __ballot_sync(FULL, e_full);
@@ -713,7 +772,7 @@ __device__ __forceinline__ void group_walk(const TreeView &T, const WalkConsts &
                 pz = wrap_min_image(pz, k);
             }
             float rx = MOx - px, ry = MOy - py, rz = MOz - pz;
-            if (PERIODIC && L > k.bigL) {
+            if (PERIODIC && (EWALD || L > k.bigL)) {
                 rx = wrap_min_image(rx, k);
                 ry = wrap_min_image(ry, k);
                 rz = wrap_min_image(rz, k);
@@ -731,6 +790,8 @@ __device__ __forceinline__ void group_walk(const TreeView &T, const WalkConsts &
             const bool open = act && !far && (guard || crit);
             if (act && !far && !open) {
                 pair_term<TREEPM>(rx, ry, rz, r2, MOm, k, ax, ay, az, ph);
+                if (EWALD)
+                    ewald_term(rx, ry, rz, MOm, k, ax, ay, az, ph);
                 cnt++;
             }
             const unsigned om = __ballot_sync(FULL, open);
@@ -752,7 +813,7 @@ __device__ __forceinline__ void group_walk(const TreeView &T, const WalkConsts &
                         wy = wrap_min_image(wy, k);
                         wz = wrap_min_image(wz, k);
                     }
-                    const bool wflag = PERIODIC && (wide || L > k.bigL);
+                    const bool wflag = PERIODIC && (EWALD || wide || L > k.bigL);
                     if (lane == 0) {
                         sh.lsrc[nl] = make_float4(wx, wy, wz, __int_as_float(l0));
                         sh.lmeta[nl] = make_uint2(om, (wflag ? kLeafWrap : 0u) | ((uint32_t)l1 & kLeafCount));
@@ -780,6 +841,8 @@ __device__ __forceinline__ void group_walk(const TreeView &T, const WalkConsts &
     sweep_leaves<PERIODIC, TREEPM>(sh, nl, lanebit, s, xox, xoy, xoz, spart, k, ax, ay, az, ph, cnt);
     if (!valid)
         return;
+    if (EWALD)  // the particle's own images and the background
+        ph = fmaf(__ldg(&spart[s]).w * k.eps, k.ephi0, ph);
     const float G = k.G;
     if (accumulate) {
         acc[3 * (size_t)out] += G * ax;
@@ -909,6 +972,17 @@ WalkConsts make_consts(const System *s, const tpm_force_params *p) {
     return k;
 }
 
+// The Ewald constants of a periodic tree without the mesh (table at unit box).
+void set_ewald(WalkConsts &k, const System *s, const float4 *tab, float phi0) {
+    const double L = s->bp.box;
+    k.etab = tab;
+    k.ent = kEwaldN;
+    k.escale = (float)(2.0 * kEwaldN / L);
+    k.efs = (float)(1.0 / (L * L));
+    k.eps = (float)(1.0 / L);
+    k.ephi0 = phi0;
+}
+
 }  // namespace
 
 size_t batch_req_bytes() { return sizeof(BatchReq); }
@@ -939,11 +1013,17 @@ int launch_walk_batch(Ctx *c, const void *reqs, const uint4 *groups, const unsig
     return TPM_OK;
 }
 
-int walk_device(Ctx *, const System *s, const tpm_force_params *p, const WalkRequest &r, cudaStream_t st) {
+int walk_device(Ctx *c, const System *s, const tpm_force_params *p, const WalkRequest &r, cudaStream_t st) {
     if (r.n_act == 0)
         return TPM_OK;
-    const WalkConsts k = make_consts(s, p);
+    WalkConsts k = make_consts(s, p);
     const bool per = s->bp.periodic != 0, rel = p->crit == TPM_CRIT_RELATIVE, tpm = p->treepm != 0;
+    if (per && !tpm) {
+        const float4 *tab;
+        float phi0;
+        TPM_CHECK(ewald_table_for(c, !r.no_alloc, st, &tab, &phi0));
+        set_ewald(k, s, tab, phi0);
+    }
     const int ov = walk_override();
     const bool lanes = ov == 1 || (ov == 0 && per);
     int *err = s->err;
@@ -959,10 +1039,10 @@ int walk_device(Ctx *, const System *s, const tpm_force_params *p, const WalkReq
         launch<true, false, true>(s, r, k, lanes, err, st);
     else if (per && rel && tpm)
         launch<true, true, true>(s, r, k, lanes, err, st);
-    else {
-        set_error("unsupported walk mode (periodic systems need treepm = 1)");
-        return TPM_EINVAL;
-    }
+    else if (per && !rel)
+        launch<true, false, false>(s, r, k, lanes, err, st);
+    else
+        launch<true, true, false>(s, r, k, lanes, err, st);
     TPM_CUDA(cudaGetLastError());
     return TPM_OK;
 }

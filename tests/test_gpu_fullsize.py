@@ -148,3 +148,49 @@ def test_hernquist_isolated_treepm_full_size(oracle_mod, tpm, pm_n, asmth, bound
     assert gpu_p99 <= 1.05 * floor_p99 + 1e-5, (gpu_p99, floor_p99)
     if bound:
         assert gpu_p99 <= bound, gpu_p99
+
+
+def test_zeldovich_ewald_tree_full_size(oracle_mod, tpm):
+    # the 128^3 box as a pure tree with the Ewald correction (no mesh): the
+    # geometric first pass, then the relative criterion; parity with the
+    # oracle walk on sampled particles and the error against the exact
+    # Ewald sum at the oracle's floor
+    import torch
+
+    dev = torch.device("cuda", 0)
+    cfg = bench.ZELDOVICH
+    pos, mass = bench.zeldovich_inputs()
+    n = len(pos)
+    h = bench.zeldovich_h()
+    shift = bench.root_shift(0, 3)
+    ctx = tpm.Context(0)
+    s = ctx.build_tree(torch.from_numpy(pos).to(dev), torch.from_numpy(mass).to(dev),
+                       tpm.BuildParams(G=cfg["G"], h=h, periodic=True, box=1.0, shift=shift, leaf_bucket=cfg["bucket"]))
+    a_bh, _, _ = s.compute_forces(fp=tpm.ForceParams(crit=tpm.CRIT_BH, theta=cfg["theta"]))
+    a_old = torch.linalg.vector_norm(a_bh, dim=1).contiguous()
+    # the sampled particles take the oracle's |a_old| on both sides: each has
+    # thousands of relative decisions in this box of cancelling forces, so an
+    # inherited |a_old| difference would flip some of them
+    tg = W.random_targets(n, 512, 97)
+    tree = oracle_mod.Tree(pos, mass, bucket=cfg["bucket"], periodic=True, box=1.0, shift=shift)
+    o_bh, _, _ = tree.walk(tg, cfg["G"], h, theta=cfg["theta"], ewald=True)
+    aold_o = np.linalg.norm(o_bh, axis=1).astype(np.float32)
+    a_old[torch.from_numpy(tg.astype(np.int64)).to(dev)] = torch.from_numpy(aold_o).to(dev)
+    a_rel, _, n_rel = s.compute_forces(a_old=a_old, fp=tpm.ForceParams(crit=tpm.CRIT_RELATIVE, alpha=cfg["alpha"]))
+    a_rel, n_rel = a_rel.cpu().numpy().astype(np.float64), n_rel.cpu().numpy()
+    s.release()
+    ctx.close()
+    o_rel, _, on_rel = tree.walk(tg, cfg["G"], h, crit="rel", alpha=cfg["alpha"], a_old=aold_o, ewald=True)
+    same = n_rel[tg] == on_rel
+    assert same.mean() >= 0.98
+    # FP32 accumulation of ~3500 terms that nearly cancel (a linear box): the
+    # running sum reaches ~4 pi G rho L/2 ~ 6 while a force is ~0.03, so the
+    # rounding walk is ~6e-8 x 6 x sqrt(3500) / 0.03 ~ 7e-4 of the rms force
+    scale = np.sqrt(np.mean(np.sum(o_rel * o_rel, axis=1)))
+    e = np.linalg.norm(a_rel[tg] - o_rel, axis=1) / scale
+    assert np.percentile(e[same], 99) < 2e-3 and e[same].max() < 1e-2, (np.percentile(e[same], 99), e.max())
+    ae, _ = oracle_mod.ewald(pos, mass, tg, cfg["G"], 1.0)
+    gpu, floor = rel(a_rel[tg], ae), rel(o_rel, ae)
+    print("periodic Ewald tree vs Ewald: GPU p50 %.3g p99 %.3g; oracle p50 %.3g p99 %.3g" % (
+        np.median(gpu), np.percentile(gpu, 99), np.median(floor), np.percentile(floor, 99)))
+    assert np.percentile(gpu, 99) <= 1.05 * np.percentile(floor, 99) + 1e-4
