@@ -87,6 +87,10 @@ def _load():
             lib.orc_tree_walk.argtypes = [vp, i64, vp, vp, C.POINTER(WalkParams), vp, vp, vp, C.c_int]
             lib.orc_ewald.restype = None
             lib.orc_ewald.argtypes = [i64, vp, vp, i64, vp, d, d, d, d, C.c_int, vp, vp, C.c_int]
+            lib.orc_direct_soft.restype = None
+            lib.orc_direct_soft.argtypes = [i64, vp, vp, vp, i64, vp, d, vp, vp, C.c_int]
+            lib.orc_tree_set_soft.restype = None
+            lib.orc_tree_set_soft.argtypes = [vp, vp]
             lib.orc_ewald_correction.restype = None
             lib.orc_ewald_correction.argtypes = [d, d, d, d, vp]
             lib.orc_ewald_table.restype = None
@@ -125,6 +129,20 @@ def gshort_pot(r: float, rs: float) -> float:
 
 
 # ---------------------------------------------------------------- direct sum
+def direct_soft(pos, mass, hsoft, targets, G: float, nthreads: int = 0):
+    """FP64 direct sum with per-particle spline supports ``hsoft``; a pair
+    interacts with the larger of its two supports (Sec. 3.2)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    mass = np.ascontiguousarray(mass, dtype=np.float32)
+    hsoft = np.ascontiguousarray(hsoft, dtype=np.float32)
+    targets = np.ascontiguousarray(targets, dtype=np.uint32)
+    acc = np.zeros((len(targets), 3))
+    pot = np.zeros(len(targets))
+    _load().orc_direct_soft(len(pos), _p(pos), _p(mass), _p(hsoft), len(targets), _p(targets), G, _p(acc), _p(pot),
+                            nthreads)
+    return acc, pot
+
+
 def direct(pos, mass, targets, G: float, h: float, nthreads: int = 0):
     """Softened FP64 direct sum on ``targets`` (open boundaries)."""
     pos = np.ascontiguousarray(pos, dtype=np.float64)
@@ -140,10 +158,14 @@ def direct(pos, mass, targets, G: float, h: float, nthreads: int = 0):
 class Tree:
     """Key-prefix oct-tree of the oracle (FP64 monopoles), pre-order nodes."""
 
-    def __init__(self, pos, mass, bucket: int = 1, periodic: bool = False, box: float = 1.0, shift=(0.0, 0.0, 0.0)):
+    def __init__(self, pos, mass, bucket: int = 1, periodic: bool = False, box: float = 1.0, shift=(0.0, 0.0, 0.0),
+                 hsoft=None):
+        """``hsoft``: per-particle spline supports (Sec. 3.2), else the walk's
+        uniform ``h``."""
         self._lib = _load()
         self.pos = np.ascontiguousarray(pos, dtype=np.float64)
         self.mass = np.ascontiguousarray(mass, dtype=np.float32)
+        self.hsoft = None if hsoft is None else np.ascontiguousarray(hsoft, dtype=np.float32)
         self.n = len(self.pos)
         self.bucket = int(bucket)
         self.periodic = bool(periodic)
@@ -158,6 +180,8 @@ class Tree:
         L0 = np.zeros(1)
         self._lib.orc_tree_root(self._h, _p(x0), _p(L0))
         self.x0, self.L0 = x0, float(L0[0])
+        if self.hsoft is not None:
+            self._lib.orc_tree_set_soft(self._h, _p(self.hsoft))
 
     def __del__(self):
         h = getattr(self, "_h", None)

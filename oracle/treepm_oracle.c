@@ -128,6 +128,41 @@ void orc_direct(int64_t n, const double *pos, const float *mass, int64_t nt, con
 }
 
 /* ------------------------------------------------------------------------ */
+/* Direct sum with per-particle softening (Sec. 3.2): particles may carry    */
+/* different spline supports; a pair interacts with the larger of the two.  */
+/* ------------------------------------------------------------------------ */
+void orc_direct_soft(int64_t n, const double *pos, const float *mass, const float *hsoft, int64_t nt,
+                     const uint32_t *targets, double G, double *acc, double *pot, int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0)
+        omp_set_num_threads(nthreads);
+#endif
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < nt; t++) {
+        int64_t i = targets[t];
+        double ax = 0, ay = 0, az = 0, ph = 0;
+        for (int64_t j = 0; j < n; j++) {
+            if (j == i)
+                continue;
+            double dx = pos[3 * i] - pos[3 * j], dy = pos[3 * i + 1] - pos[3 * j + 1], dz = pos[3 * i + 2] - pos[3 * j + 2];
+            double r = sqrt(dx * dx + dy * dy + dz * dz);
+            double m = (double)mass[j];
+            double h = hsoft[i] > hsoft[j] ? (double)hsoft[i] : (double)hsoft[j];
+            double kf = orc_kforce(r, h);
+            ax -= m * dx * kf;
+            ay -= m * dy * kf;
+            az -= m * dz * kf;
+            ph += m * orc_kpot(r, h);
+        }
+        acc[3 * t] = G * ax;
+        acc[3 * t + 1] = G * ay;
+        acc[3 * t + 2] = G * az;
+        pot[t] = G * ph;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Oct-tree (Sec. 3.1).                                                      */
 /*                                                                           */
 /* Root.  Open boundaries: a cubical root of power-of-two side L0, the       */
@@ -171,6 +206,8 @@ typedef struct orc_tree {
     uint64_t *prefix;
     uint32_t *first, *count, *skip;
     double *mass, *com; /* com: 3 per node */
+    const float *hsoft; /* per-particle spline support (original order), NULL: uniform */
+    double *hmax, *hmin; /* per node: largest and smallest support of its particles */
 } orc_tree;
 
 static uint64_t orc_spread(uint64_t v)
@@ -278,6 +315,8 @@ void orc_tree_free(orc_tree *t)
     free(t->skip);
     free(t->mass);
     free(t->com);
+    free(t->hmax);
+    free(t->hmin);
     free(t);
 }
 
@@ -365,6 +404,33 @@ orc_tree *orc_tree_build(int64_t n, const double *pos, const float *mass, int pe
 
 int64_t orc_tree_nnodes(const orc_tree *t) { return t->nnodes; }
 
+/* Per-particle softening (Sec. 3.2) for the walk: each node records the      */
+/* largest and smallest support among its particles.  hsoft (original order) */
+/* must outlive the tree; NULL returns to the uniform softening.             */
+void orc_tree_set_soft(orc_tree *t, const float *hsoft)
+{
+    free(t->hmax);
+    free(t->hmin);
+    t->hmax = t->hmin = NULL;
+    t->hsoft = hsoft;
+    if (!hsoft)
+        return;
+    t->hmax = malloc(t->nnodes * sizeof(double));
+    t->hmin = malloc(t->nnodes * sizeof(double));
+    for (int64_t id = 0; id < t->nnodes; id++) {
+        double hi = 0.0, lo = INFINITY;
+        for (uint32_t s = t->first[id]; s < t->first[id] + t->count[id]; s++) {
+            double h = hsoft[t->perm[s]];
+            if (h > hi)
+                hi = h;
+            if (h < lo)
+                lo = h;
+        }
+        t->hmax[id] = hi;
+        t->hmin[id] = lo;
+    }
+}
+
 void orc_tree_root(const orc_tree *t, double x0[3], double *L0)
 {
     x0[0] = t->x0[0];
@@ -444,12 +510,12 @@ static inline double orc_wrap(double d, int periodic, double box)
     return d;
 }
 
-static inline void orc_pair(const orc_walk_params *p, double dx, double dy, double dz, double m, double acc[3],
-                            double *pot)
+static inline void orc_pair(const orc_walk_params *p, double h, double dx, double dy, double dz, double m,
+                            double acc[3], double *pot)
 {
-    /* (dx,dy,dz) = x_source - x_target */
+    /* (dx,dy,dz) = x_source - x_target; h the spline support of the pair */
     double r = sqrt(dx * dx + dy * dy + dz * dz);
-    double kf = orc_kforce(r, p->h), kp = orc_kpot(r, p->h);
+    double kf = orc_kforce(r, h), kp = orc_kpot(r, h);
     if (p->treepm) {
         kf *= orc_gshort_force(r, p->rs);
         kp *= orc_gshort_pot(r, p->rs);
@@ -462,10 +528,10 @@ static inline void orc_pair(const orc_walk_params *p, double dx, double dy, doub
 
 /* Monopole / pair term of the periodic tree without the mesh: the nearest
  * image (spline-softened) plus the Ewald correction at the same separation. */
-static inline void orc_pair_ewald(const orc_walk_params *p, double box, double dx, double dy, double dz, double m,
-                                  double acc[3], double *pot)
+static inline void orc_pair_ewald(const orc_walk_params *p, double h, double box, double dx, double dy, double dz,
+                                  double m, double acc[3], double *pot)
 {
-    orc_pair(p, dx, dy, dz, m, acc, pot);
+    orc_pair(p, h, dx, dy, dz, m, acc, pot);
     double f[3], ph;
     orc_ewald_lookup(p, box, dx, dy, dz, f, &ph);
     acc[0] += m * f[0];
@@ -482,6 +548,7 @@ static void orc_walk_one(const orc_tree *t, int64_t i, double aold, const orc_wa
     int per = t->periodic;
     double rcut2 = p->rcut * p->rcut;
     uint32_t self = t->rank[i];
+    const double hi = t->hsoft ? (double)t->hsoft[i] : p->h; /* the target's support */
     acc[0] = acc[1] = acc[2] = 0.0;
     *pot = 0.0;
     uint32_t cnt = 0;
@@ -510,6 +577,14 @@ static void orc_walk_one(const orc_tree *t, int64_t i, double aold, const orc_wa
         int open = 0;
         if (p->box_guard && fabs(px) <= 0.6 * L && fabs(py) <= 0.6 * L && fabs(pz) <= 0.6 * L)
             open = 1;
+        /* Sec. 3.2: a node of mixed softenings whose largest exceeds the
+         * target's, closer than that largest, is always opened */
+        double hnode = hi;
+        if (t->hsoft) {
+            if (t->hmin[id] < t->hmax[id] && hi < t->hmax[id] && d2 < t->hmax[id] * t->hmax[id])
+                open = 1;
+            hnode = hi > t->hmax[id] ? hi : t->hmax[id];
+        }
         if (!open) {
             if (p->crit == 0)
                 open = L * L > p->theta * p->theta * d2;
@@ -520,9 +595,9 @@ static void orc_walk_one(const orc_tree *t, int64_t i, double aold, const orc_wa
         int ew = per && p->ewald && !p->treepm;
         if (!open) {
             if (ew)
-                orc_pair_ewald(p, box, dx, dy, dz, t->mass[id], acc, pot);
+                orc_pair_ewald(p, hnode, box, dx, dy, dz, t->mass[id], acc, pot);
             else
-                orc_pair(p, dx, dy, dz, t->mass[id], acc, pot);
+                orc_pair(p, hnode, dx, dy, dz, t->mass[id], acc, pot);
             cnt++;
             id = t->skip[id];
         } else if (!leaf) {
@@ -536,10 +611,13 @@ static void orc_walk_one(const orc_tree *t, int64_t i, double aold, const orc_wa
                        qz = orc_wrap(t->x[3 * j + 2] - xi[2], per, box);
                 if (p->treepm && qx * qx + qy * qy + qz * qz > rcut2)
                     continue;
+                double hp = hi;
+                if (t->hsoft && (double)t->hsoft[j] > hp)
+                    hp = (double)t->hsoft[j];
                 if (ew)
-                    orc_pair_ewald(p, box, qx, qy, qz, (double)t->m[j], acc, pot);
+                    orc_pair_ewald(p, hp, box, qx, qy, qz, (double)t->m[j], acc, pot);
                 else
-                    orc_pair(p, qx, qy, qz, (double)t->m[j], acc, pot);
+                    orc_pair(p, hp, qx, qy, qz, (double)t->m[j], acc, pot);
                 cnt++;
             }
             id = t->skip[id];

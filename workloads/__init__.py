@@ -165,6 +165,23 @@ def root_shift(seed: int) -> np.ndarray:
     return _rng(seed ^ 0x5EED).uniform(0.0, 1.0, 3)
 
 
+def two_species(n_dm: int, n_star: int, seed: int, h_dm: float = 0.005, h_star: float = 0.001,
+                star_scale: float = 0.1, star_mass_frac: float = 0.1):
+    """Two collisionless species with their own softening: a Hernquist halo
+    (M = 1 - star_mass_frac, a = 1, spline support h_dm) around a compact
+    Plummer sphere of stars (M = star_mass_frac, scale star_scale, support
+    h_star), shuffled together.  Returns (pos, mass, hsoft, species)."""
+    rng = _rng(seed)
+    p_dm, m_dm = hernquist(n_dm, seed)
+    p_st, m_st = plummer(n_star, seed + 1)
+    pos = np.concatenate([p_dm, p_st * star_scale])
+    mass = np.concatenate([m_dm * (1.0 - star_mass_frac), m_st * star_mass_frac]).astype(np.float32)
+    hsoft = np.concatenate([np.full(n_dm, h_dm), np.full(n_star, h_star)]).astype(np.float32)
+    species = np.concatenate([np.zeros(n_dm, np.int8), np.ones(n_star, np.int8)])
+    order = rng.permutation(n_dm + n_star)
+    return pos[order], mass[order], hsoft[order], species[order]
+
+
 def timebins(pos: np.ndarray, seed: int, nbins: int = 8, a: float = 1.0, M: float = 1.0,
              scatter: float = 0.3) -> np.ndarray:
     """Power-of-two time bins (0 = longest step, nbins-1 = shortest).
