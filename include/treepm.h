@@ -136,6 +136,21 @@ int tpm_build_tree(tpm_ctx *ctx, const double *pos, const float *mass, int64_t n
                    void *stream, tpm_sys *out);
 
 /*
+ * tpm_build_tree with per-particle softening (Sec. 3.2): hsoft holds each
+ * particle's spline support (n FP32 > 0, host or device; p->h is then not
+ * used by the walk).  A pair interacts with the larger of its two supports;
+ * an accepted node with the larger of the target's support and the node's
+ * largest; a node holding particles of different supports is always opened
+ * for a target whose support is smaller than the node's largest and whose
+ * distance to the node's centre of mass is below that largest.  Open
+ * boundaries only (with or without treepm).  The node set and monopoles are
+ * those of tpm_build_tree.  Errors: as tpm_build_tree, TPM_EINVAL (null
+ * hsoft, periodic system), TPM_ENAN (a support not finite or not > 0).
+ */
+int tpm_build_tree_soft(tpm_ctx *ctx, const double *pos, const float *mass, const float *hsoft, int64_t n,
+                        const tpm_build_params *p, void *stream, tpm_sys *out);
+
+/*
  * Long-range particle-mesh potential (Sec. 3.3, 3.4), r_s = asmth dx.
  * Periodic systems: CIC assignment of all mass onto pm_n^3 mesh points at
  * x = i dx, dx = box / pm_n, FFT, multiplication by -4 pi G / k^2

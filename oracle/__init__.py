@@ -473,13 +473,13 @@ def pm_interpolate_isolated(phi: np.ndarray, pos, corner, side: float, ngrid: in
 
 def treepm_isolated(pos, mass, targets, ngrid: int, asmth: float, rcut_cells: float, G: float, h: float,
                     crit: str = "bh", theta: float = 0.5, alpha: float = 0.0025, a_old=None, bucket: int = 8,
-                    shift=(0.0, 0.0, 0.0), nthreads: int = 0):
+                    shift=(0.0, 0.0, 0.0), nthreads: int = 0, hsoft=None):
     """TreePM with nonperiodic boundaries (Sec. 3.3, 3.4): short-range walk of
     the open tree with the erfc split and cutoff, plus the isolated mesh;
     r_s = asmth x the mesh spacing of ``pm_region_isolated``."""
     corner, side = pm_region_isolated(pos)
     rs = asmth * side / ngrid
-    tree = Tree(pos, mass, bucket=bucket, shift=shift)
+    tree = Tree(pos, mass, bucket=bucket, shift=shift, hsoft=hsoft)
     a_s, p_s, nint = tree.walk(targets, G, h, crit=crit, theta=theta, alpha=alpha, a_old=a_old, treepm=True, rs=rs,
                                rcut=rcut_cells * rs, nthreads=nthreads)
     phi = pm_potential_isolated(pos, mass, corner, side, ngrid, rs, G)

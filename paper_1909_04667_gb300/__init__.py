@@ -73,6 +73,7 @@ def _load():
         "tpm_destroy": (i32, [vp]),
         "tpm_memory": (i32, [vp, C.POINTER(sz), C.POINTER(sz)]),
         "tpm_build_tree": (i32, [vp, vp, vp, i64, C.POINTER(_BuildParams), vp, C.POINTER(C.c_uint64)]),
+        "tpm_build_tree_soft": (i32, [vp, vp, vp, vp, i64, C.POINTER(_BuildParams), vp, C.POINTER(C.c_uint64)]),
         "tpm_pm_long_range": (i32, [vp, C.c_uint64, C.POINTER(_ForceParams), vp]),
         "tpm_compute_forces": (i32, [vp, C.c_uint64, vp, i64, vp, C.POINTER(_ForceParams), vp, vp, vp, vp]),
         "tpm_release": (i32, [vp, C.c_uint64]),
@@ -304,8 +305,10 @@ class Context:
     def create_plan(self, max_ids: int, max_requests: int) -> Plan:
         return Plan(self, max_ids, max_requests)
 
-    def build_tree(self, pos, mass, params: BuildParams, stream=None) -> "System":
-        """``tpm_build_tree``: pos (n, 3) float64, mass (n,) float32, on host or device."""
+    def build_tree(self, pos, mass, params: BuildParams, stream=None, hsoft=None) -> "System":
+        """``tpm_build_tree``: pos (n, 3) float64, mass (n,) float32, on host or
+        device; with ``hsoft`` (n,) float32 per-particle spline supports,
+        ``tpm_build_tree_soft``."""
         n = int(pos.shape[0])
         if tuple(pos.shape) != (n, 3) or int(mass.shape[0]) != n:
             raise ValueError("pos must be (n, 3) and mass (n,)")
@@ -313,8 +316,15 @@ class Context:
         _dtype_check(mass, "float32")
         out = C.c_uint64()
         cp = params._c()
-        _check(_lib.tpm_build_tree(self._h, _ptr(pos), _ptr(mass), n, C.byref(cp), _stream(stream, self.device),
-                                   C.byref(out)))
+        if hsoft is None:
+            _check(_lib.tpm_build_tree(self._h, _ptr(pos), _ptr(mass), n, C.byref(cp), _stream(stream, self.device),
+                                       C.byref(out)))
+        else:
+            if int(hsoft.shape[0]) != n:
+                raise ValueError("hsoft must be (n,)")
+            _dtype_check(hsoft, "float32")
+            _check(_lib.tpm_build_tree_soft(self._h, _ptr(pos), _ptr(mass), _ptr(hsoft), n, C.byref(cp),
+                                            _stream(stream, self.device), C.byref(out)))
         return System(self, out.value, n, params)
 
 

@@ -190,8 +190,8 @@ int run_batch(Ctx *c, Plan *pl, int64_t n_req, const tpm_sys *systems, const int
             }
             const System *s = it->second;
             const tpm_force_params *p = &params[r];
-            if (s->bp.periodic || p->treepm) {
-                set_error("batched evaluation supports open boundaries (request %lld)", (long long)r);
+            if (s->bp.periodic || p->treepm || s->psoft) {
+                set_error("batched evaluation supports open boundaries with uniform softening (request %lld)", (long long)r);
                 return TPM_EINVAL;
             }
             if (p->crit != TPM_CRIT_BH && p->crit != TPM_CRIT_RELATIVE) {

@@ -213,8 +213,9 @@ __global__ void k_keys(const double *__restrict__ pos, int64_t n, const BuildSta
 // Inverse permutation, and positions and masses gathered into key order for
 // the passes over leaves.
 __global__ void k_rank(const uint32_t *__restrict__ perm, int64_t n, const double *__restrict__ pos,
-                       const float *__restrict__ mass, uint32_t *__restrict__ rank, double *__restrict__ spos,
-                       float *__restrict__ smass) {
+                       const float *__restrict__ mass, const float *__restrict__ hsoft, uint32_t *__restrict__ rank,
+                       double *__restrict__ spos, float *__restrict__ smass, float *__restrict__ psoft,
+                       int *__restrict__ bad) {
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= n)
         return;
@@ -224,6 +225,12 @@ __global__ void k_rank(const uint32_t *__restrict__ perm, int64_t n, const doubl
     spos[3 * s + 1] = pos[3 * j + 1];
     spos[3 * s + 2] = pos[3 * j + 2];
     smass[s] = mass[j];
+    if (hsoft) {  // per-particle softening, in key order
+        const float h = hsoft[j];
+        if (!(h > 0.0f) || !isfinite(h))
+            atomicOr(bad, 8);
+        psoft[s] = h;
+    }
 }
 
 // Deepest level whose cell holds both keys (kMaxLevel when they are equal).
@@ -382,11 +389,13 @@ __global__ void k_nodes(const uint64_t *__restrict__ key, int64_t n, const uint3
 // order and value whichever thread computes it.
 __global__ void k_multipole(NodeArrays t, int64_t total, const uint32_t *__restrict__ pre2bfs,
                             const double *__restrict__ spos, const float *__restrict__ smass, double *__restrict__ M,
-                            double *__restrict__ S) {
+                            double *__restrict__ S, const float *__restrict__ psoft, float *__restrict__ hmx,
+                            float *__restrict__ hmn) {
     const int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (node >= total || t.nchild[node] != 0)
         return;
     double m = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+    float hi = 0.0f, lo = INFINITY;  // largest / smallest softening (per-particle softening only)
     const uint32_t f = t.first[node], e = f + t.count[node];
     for (uint32_t s = f; s < e; s++) {
         const double ms = (double)smass[s];
@@ -394,12 +403,20 @@ __global__ void k_multipole(NodeArrays t, int64_t total, const uint32_t *__restr
         sx = __dadd_rn(sx, __dmul_rn(ms, spos[3 * s]));
         sy = __dadd_rn(sy, __dmul_rn(ms, spos[3 * s + 1]));
         sz = __dadd_rn(sz, __dmul_rn(ms, spos[3 * s + 2]));
+        if (psoft) {
+            hi = fmaxf(hi, psoft[s]);
+            lo = fminf(lo, psoft[s]);
+        }
     }
     uint32_t q = pre2bfs[node];
     M[q] = m;
     S[3 * q] = sx;
     S[3 * q + 1] = sy;
     S[3 * q + 2] = sz;
+    if (psoft) {
+        hmx[q] = hi;
+        hmn[q] = lo;
+    }
     uint32_t cur = (uint32_t)node;
     while (cur != 0) {
         const uint32_t p = t.parent[cur];
@@ -409,18 +426,28 @@ __global__ void k_multipole(NodeArrays t, int64_t total, const uint32_t *__restr
             return;  // a sibling still works; it will carry on upwards
         __threadfence();
         m = sx = sy = sz = 0.0;
+        hi = 0.0f;
+        lo = INFINITY;
         const uint32_t c0 = pre2bfs[p + 1];  // first child; the others follow it
         for (uint32_t c = c0; c < c0 + nc; c++) {
             m = __dadd_rn(m, __ldcg(&M[c]));
             sx = __dadd_rn(sx, __ldcg(&S[3 * c]));
             sy = __dadd_rn(sy, __ldcg(&S[3 * c + 1]));
             sz = __dadd_rn(sz, __ldcg(&S[3 * c + 2]));
+            if (psoft) {
+                hi = fmaxf(hi, __ldcg(&hmx[c]));
+                lo = fminf(lo, __ldcg(&hmn[c]));
+            }
         }
         q = pre2bfs[p];
         M[q] = m;
         S[3 * q] = sx;
         S[3 * q + 1] = sy;
         S[3 * q + 2] = sz;
+        if (psoft) {
+            hmx[q] = hi;
+            hmn[q] = lo;
+        }
         cur = p;
     }
 }
@@ -440,6 +467,7 @@ struct NodeOut {
     float4 *bcen, *bcom;
     int4 *blink;
     float4 *spart;
+    float *nsoft, *bsoft;  // per-particle softening only
 };
 
 // K5: walk tables.  Pre-order: FP32 geometric centre (exact, on the 2^-22 L0
@@ -451,7 +479,8 @@ struct NodeOut {
 // centre (FP64 difference -> FP32) with their masses.
 __global__ void k_finalize(NodeArrays t, const uint32_t *__restrict__ pre2bfs, int64_t total,
                            const double *__restrict__ M, const double *__restrict__ S, const double *__restrict__ spos,
-                           const float *__restrict__ smass, double x0, double y0, double z0, double L0, NodeOut o) {
+                           const float *__restrict__ smass, const float *__restrict__ hmx,
+                           const float *__restrict__ hmn, double x0, double y0, double z0, double L0, NodeOut o) {
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= total)
         return;
@@ -480,6 +509,11 @@ __global__ void k_finalize(NodeArrays t, const uint32_t *__restrict__ pre2bfs, i
     o.bcen[q] = cen;
     o.bcom[q] = com;
     o.blink[q] = make_int4(nch ? (int)pre2bfs[p + 1] : 0, (int)nch, (int)f, (int)c);
+    if (hmx) {  // largest softening, negative when the node mixes softenings
+        const float v = hmn[q] < hmx[q] ? -hmx[q] : hmx[q];
+        o.nsoft[p] = v;
+        o.bsoft[q] = v;
+    }
     if (nch == 0) {  // leaf particles relative to the leaf centre (FP64 difference -> FP32)
         const double ax = __dadd_rn(x0, (double)cen.x), ay = __dadd_rn(y0, (double)cen.y),
                      az = __dadd_rn(z0, (double)cen.z);
@@ -491,7 +525,8 @@ __global__ void k_finalize(NodeArrays t, const uint32_t *__restrict__ pre2bfs, i
 
 }  // namespace
 
-int build_tree_device(Ctx *c, System *s, const double *pos_in, const float *mass_in, cudaStream_t st) {
+int build_tree_device(Ctx *c, System *s, const double *pos_in, const float *mass_in, const float *hsoft_in,
+                      cudaStream_t st) {
     const int64_t n = s->n;
     const int B = s->bp.leaf_bucket;
     AllocSet tmp;
@@ -553,7 +588,10 @@ int build_tree_device(Ctx *c, System *s, const double *pos_in, const float *mass
     float *smass;
     TPM_CHECK(tmp.get(&spos, 3 * n, st));
     TPM_CHECK(tmp.get(&smass, n, st));
-    k_rank<<<blocks_for(n), kThreads, 0, st>>>(s->perm, n, s->pos, s->mass, s->rank, spos, smass);
+    if (hsoft_in)
+        TPM_CHECK(s->mem.get(&s->psoft, n, st));
+    k_rank<<<blocks_for(n), kThreads, 0, st>>>(s->perm, n, s->pos, s->mass, hsoft_in, s->rank, spos, smass, s->psoft,
+                                               &dst->bad);
     count_launch();
     TPM_CUDA(cudaGetLastError());
 
@@ -595,6 +633,10 @@ int build_tree_device(Ctx *c, System *s, const double *pos_in, const float *mass
     if (hst->bad & 2) {
         set_error("periodic positions must lie in [0, box)");
         return TPM_EINVAL;
+    }
+    if (hst->bad & 8) {
+        set_error("softening lengths must be finite and > 0");
+        return TPM_ENAN;
     }
     for (int a = 0; a < 3; a++) {
         s->x0[a] = hst->x0[a];
@@ -644,8 +686,15 @@ int build_tree_device(Ctx *c, System *s, const double *pos_in, const float *mass
     count_launch();
     TPM_CUDA(cudaGetLastError());
 
-    // ---- monopoles, bottom-up in one pass
-    k_multipole<<<blocks_for(nn), kThreads, 0, st>>>(t, nn, pre2bfs, spos, smass, M, S);
+    // ---- monopoles (and softening extremes), bottom-up in one pass
+    float *hmx = nullptr, *hmn = nullptr;
+    if (s->psoft) {
+        TPM_CHECK(tmp.get(&hmx, nn, st));
+        TPM_CHECK(tmp.get(&hmn, nn, st));
+        TPM_CHECK(s->mem.get(&s->nsoft, nn, st));
+        TPM_CHECK(s->mem.get(&s->bsoft, nn, st));
+    }
+    k_multipole<<<blocks_for(nn), kThreads, 0, st>>>(t, nn, pre2bfs, spos, smass, M, S, s->psoft, hmx, hmn);
     count_launch();
     TPM_CUDA(cudaGetLastError());
 
@@ -661,9 +710,9 @@ int build_tree_device(Ctx *c, System *s, const double *pos_in, const float *mass
     TPM_CHECK(s->mem.get(&s->bcom, nn, st));
     TPM_CHECK(s->mem.get(&s->blink, nn, st));
     NodeOut o{s->ncen,  s->ncom, s->nlink, s->nlevel, s->nprefix, s->nmass,
-              s->ncomd, s->bcen, s->bcom,  s->blink,  s->spart};
-    k_finalize<<<blocks_for(nn), kThreads, 0, st>>>(t, pre2bfs, nn, M, S, spos, smass, s->x0[0], s->x0[1], s->x0[2],
-                                                    s->L0, o);
+              s->ncomd, s->bcen, s->bcom,  s->blink,  s->spart,  s->nsoft, s->bsoft};
+    k_finalize<<<blocks_for(nn), kThreads, 0, st>>>(t, pre2bfs, nn, M, S, spos, smass, hmx, hmn, s->x0[0], s->x0[1],
+                                                    s->x0[2], s->L0, o);
     count_launch();
     TPM_CUDA(cudaGetLastError());
     return TPM_OK;

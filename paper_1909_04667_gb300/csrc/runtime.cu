@@ -257,9 +257,13 @@ int tpm_memory(const tpm_ctx *h, size_t *used, size_t *budget) {
     return TPM_OK;
 }
 
-int tpm_build_tree(tpm_ctx *h, const double *pos, const float *mass, int64_t n, const tpm_build_params *p,
-                   void *stream, tpm_sys *out) {
-    clear_error();
+}  // extern "C"
+
+namespace tpm {
+namespace {
+
+int build_entry(tpm_ctx *h, const double *pos, const float *mass, const float *hsoft, int64_t n,
+                const tpm_build_params *p, void *stream, tpm_sys *out) {
     if (!h || !pos || !mass || !p || !out) {
         set_error("null argument");
         return TPM_EINVAL;
@@ -312,8 +316,18 @@ int tpm_build_tree(tpm_ctx *h, const double *pos, const float *mass, int64_t n, 
         }
         dmass = d;
     }
+    const float *dsoft = hsoft;
+    if (rc == TPM_OK && hsoft && !is_device_ptr(hsoft)) {
+        float *d;
+        rc = stage.get(&d, n, st);
+        if (rc == TPM_OK && cudaMemcpyAsync(d, hsoft, n * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess) {
+            set_error("copy of softening lengths to the device failed");
+            rc = TPM_ECUDA;
+        }
+        dsoft = d;
+    }
     if (rc == TPM_OK)
-        rc = build_tree_device(c, s, dpos, dmass, st);
+        rc = build_tree_device(c, s, dpos, dmass, dsoft, st);
     stage.release(st);
     if (rc != TPM_OK) {
         s->mem.release(st);
@@ -325,6 +339,31 @@ int tpm_build_tree(tpm_ctx *h, const double *pos, const float *mass, int64_t n, 
     c->systems[s->id] = s;
     *out = s->id;
     return TPM_OK;
+}
+
+}  // namespace
+}  // namespace tpm
+
+extern "C" {
+
+int tpm_build_tree(tpm_ctx *h, const double *pos, const float *mass, int64_t n, const tpm_build_params *p,
+                   void *stream, tpm_sys *out) {
+    clear_error();
+    return build_entry(h, pos, mass, nullptr, n, p, stream, out);
+}
+
+int tpm_build_tree_soft(tpm_ctx *h, const double *pos, const float *mass, const float *hsoft, int64_t n,
+                        const tpm_build_params *p, void *stream, tpm_sys *out) {
+    clear_error();
+    if (!hsoft) {
+        set_error("null hsoft");
+        return TPM_EINVAL;
+    }
+    if (p && p->periodic) {
+        set_error("per-particle softening is available with open boundaries");
+        return TPM_EINVAL;
+    }
+    return build_entry(h, pos, mass, hsoft, n, p, stream, out);
 }
 
 int tpm_pm_long_range(tpm_ctx *h, tpm_sys sid, const tpm_force_params *p, void *stream) {

@@ -103,6 +103,12 @@ struct System {
     uint32_t *perm = nullptr;  // sorted position -> original index
     uint32_t *rank = nullptr;  // original index -> sorted position
     float4 *spart = nullptr;   // n, sorted: (x - leaf centre) FP32, mass
+    // per-particle softening (Sec. 3.2), nullptr when uniform: spline support
+    // per sorted particle, and per node its largest support, negative when
+    // the node holds particles of different supports (pre-order and BFS)
+    float *psoft = nullptr;
+    float *nsoft = nullptr;
+    float *bsoft = nullptr;
 
     // nodes, depth-first pre-order
     float4 *ncen = nullptr;  // geometric centre relative to x0 (exact in FP32), side L
@@ -171,7 +177,8 @@ inline double pm_side(const System *s) { return s->bp.periodic ? s->bp.box : s->
 
 // ------------------------------------------------------------------ stages
 // Tree build (keys, sort, levels, multipoles, pre-order tables): fills s.
-int build_tree_device(Ctx *c, System *s, const double *pos_in, const float *mass_in, cudaStream_t st);
+int build_tree_device(Ctx *c, System *s, const double *pos_in, const float *mass_in, const float *hsoft_in,
+                      cudaStream_t st);
 
 // Long-range mesh potential into s->phi.
 int pm_solve_device(Ctx *c, System *s, const tpm_force_params *p, cudaStream_t st);

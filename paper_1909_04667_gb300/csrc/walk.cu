@@ -82,10 +82,11 @@ __device__ __forceinline__ void short_range_factors(float r, float inv2rs, float
 // (source minus target) to the acceleration and potential sums.  With the
 // cubic-spline density of support h the force is Newtonian from r = h on.
 template <bool TREEPM>
-__device__ __forceinline__ void pair_term(float rx, float ry, float rz, float r2, float m, const WalkConsts &k,
-                                          float &ax, float &ay, float &az, float &ph) {
+__device__ __forceinline__ void pair_term_s(float rx, float ry, float rz, float r2, float m, float h2, float hinv,
+                                            float hinv3, const WalkConsts &k, float &ax, float &ay, float &az,
+                                            float &ph) {
     float kf, kp;
-    if (r2 >= k.h2) {
+    if (r2 >= h2) {
         const float ri = rsqrtf(r2);
         const float ri2 = ri * ri;
         kf = ri * ri2;
@@ -98,16 +99,16 @@ __device__ __forceinline__ void pair_term(float rx, float ry, float rz, float r2
         }
     } else {
         const float r = sqrtf(r2);
-        const float u = r * k.hinv;
+        const float u = r * hinv;
         const float u2 = u * u;
         if (u < 0.5f) {
-            kf = k.hinv3 * fmaf(u2, fmaf(32.0f, u, -38.4f), 10.666666667f);
-            kp = k.hinv * fmaf(u2, fmaf(u2, fmaf(6.4f, u, -9.6f), 5.333333333f), -2.8f);
+            kf = hinv3 * fmaf(u2, fmaf(32.0f, u, -38.4f), 10.666666667f);
+            kp = hinv * fmaf(u2, fmaf(u2, fmaf(6.4f, u, -9.6f), 5.333333333f), -2.8f);
         } else {
             const float iu = __fdividef(1.0f, u);
-            kf = k.hinv3 * (fmaf(u, fmaf(u, fmaf(-10.666666667f, u, 38.4f), -48.0f), 21.333333333f) -
+            kf = hinv3 * (fmaf(u, fmaf(u, fmaf(-10.666666667f, u, 38.4f), -48.0f), 21.333333333f) -
                             0.066666666667f * iu * iu * iu);
-            kp = k.hinv * (fmaf(u2, fmaf(u, fmaf(u, fmaf(-2.133333333f, u, 9.6f), -16.0f), 10.666666667f), -3.2f) +
+            kp = hinv * (fmaf(u2, fmaf(u, fmaf(u, fmaf(-2.133333333f, u, 9.6f), -16.0f), 10.666666667f), -3.2f) +
                            0.066666666667f * iu);
         }
         if (TREEPM) {
@@ -123,6 +124,27 @@ __device__ __forceinline__ void pair_term(float rx, float ry, float rz, float r2
     az = fmaf(mk, rz, az);
     ph = fmaf(m, kp, ph);
 }
+
+template <bool TREEPM>
+__device__ __forceinline__ void pair_term(float rx, float ry, float rz, float r2, float m, const WalkConsts &k,
+                                          float &ax, float &ay, float &az, float &ph) {
+    pair_term_s<TREEPM>(rx, ry, rz, r2, m, k.h2, k.hinv, k.hinv3, k, ax, ay, az, ph);
+}
+
+// The same pair term with the pair's own spline support h (per-particle
+// softening, Sec. 3.2); 1 / h only inside the support.
+template <bool TREEPM>
+__device__ __forceinline__ void pair_term_h(float rx, float ry, float rz, float r2, float m, float h,
+                                            const WalkConsts &k, float &ax, float &ay, float &az, float &ph) {
+    const float h2 = h * h;
+    float hinv = 0.0f, hinv3 = 0.0f;
+    if (r2 < h2) {
+        hinv = 1.0f / h;
+        hinv3 = hinv * hinv * hinv;
+    }
+    pair_term_s<TREEPM>(rx, ry, rz, r2, m, h2, hinv, hinv3, k, ax, ay, az, ph);
+}
+
 
 __device__ __forceinline__ float wrap_min_image(float d, const WalkConsts &k) {
     return fmaf(-k.box, rintf(d * k.boxinv), d);
@@ -160,14 +182,14 @@ __device__ __forceinline__ void ewald_term(float rx, float ry, float rz, float m
     ph = fmaf(m * k.eps, v[3], ph);
 }
 
-template <bool PERIODIC, bool RELATIVE, bool TREEPM>
+template <bool PERIODIC, bool RELATIVE, bool TREEPM, bool VARH>
 __global__ void __launch_bounds__(kWalkThreads)
     k_walk(const float4 *__restrict__ ncen, const float4 *__restrict__ ncom, const int4 *__restrict__ nlink,
            const float4 *__restrict__ spart, const uint64_t *__restrict__ key, const uint32_t *__restrict__ perm,
            const double *__restrict__ pos, double x0, double y0, double z0, double L0, int nnodes,
-           const uint32_t *__restrict__ sidx, const uint32_t *__restrict__ slot, const float *__restrict__ a_old,
-           int64_t n_act, WalkConsts k, float *__restrict__ acc, float *__restrict__ pot,
-           uint32_t *__restrict__ nint, int accumulate) {
+           const float *__restrict__ psoft, const float *__restrict__ nsoft, const uint32_t *__restrict__ sidx,
+           const uint32_t *__restrict__ slot, const float *__restrict__ a_old, int64_t n_act, WalkConsts k,
+           float *__restrict__ acc, float *__restrict__ pot, uint32_t *__restrict__ nint, int accumulate) {
     constexpr bool EWALD = PERIODIC && !TREEPM;  // periodic tree without the mesh
     const int lane = threadIdx.x & 31;
     const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane);
@@ -199,6 +221,7 @@ __global__ void __launch_bounds__(kWalkThreads)
     float thr = k.thr_const;
     if (RELATIVE)
         thr = valid ? k.alpha_over_G * fabsf(a_old[out]) : 0.0f;
+    const float hi = VARH ? __ldg(&psoft[s]) : 0.0f;  // this particle's spline support
 
     float ax = 0.f, ay = 0.f, az = 0.f, ph = 0.f;
     uint32_t cnt = 0;
@@ -237,10 +260,19 @@ __global__ void __launch_bounds__(kWalkThreads)
             crit = O.w * L * L > thr * r2 * r2;
         else
             crit = L * L > thr * r2;
+        float hn = 0.0f;
+        if (VARH) {  // Sec. 3.2: a node of mixed softenings is opened inside its largest one
+            const float v = __ldg(&nsoft[n]);
+            hn = fabsf(v);
+            crit = crit || (v < 0.0f && hi < hn && r2 < hn * hn);
+        }
         const bool open = act && !far && (guard || crit);
         if (act && !open) {
             if (!far) {
-                pair_term<TREEPM>(rx, ry, rz, r2, O.w, k, ax, ay, az, ph);
+                if (VARH)
+                    pair_term_h<TREEPM>(rx, ry, rz, r2, O.w, fmaxf(hi, hn), k, ax, ay, az, ph);
+                else
+                    pair_term<TREEPM>(rx, ry, rz, r2, O.w, k, ax, ay, az, ph);
                 if (EWALD)
                     ewald_term(rx, ry, rz, O.w, k, ax, ay, az, ph);
                 cnt++;
@@ -269,7 +301,10 @@ __global__ void __launch_bounds__(kWalkThreads)
                 }
                 const float q2 = fmaf(qx, qx, fmaf(qy, qy, qz * qz));
                 if (!TREEPM || q2 <= k.rcut2) {
-                    pair_term<TREEPM>(qx, qy, qz, q2, P.w, k, ax, ay, az, ph);
+                    if (VARH)
+                        pair_term_h<TREEPM>(qx, qy, qz, q2, P.w, fmaxf(hi, __ldg(&psoft[jj])), k, ax, ay, az, ph);
+                    else
+                        pair_term<TREEPM>(qx, qy, qz, q2, P.w, k, ax, ay, az, ph);
                     if (EWALD)
                         ewald_term(qx, qy, qz, P.w, k, ax, ay, az, ph);
                     cnt++;
@@ -324,7 +359,7 @@ constexpr int kGroupWarps = 4;
 constexpr int kStackCap = 256;
 constexpr int kStackSafe = kStackCap - 64;  // above this, take one candidate at a time
 constexpr int kNodeFlush = 64;              // sweep once this many node entries are queued
-constexpr int kNodeCap = kNodeFlush + 64;   // one batch adds at most 64
+constexpr int kNodeCap = kNodeFlush + 32;   // one batch adds at most 32 (one per candidate)
 constexpr int kLeafFlush = 32;
 constexpr int kLeafCap = kLeafFlush + 64;
 constexpr uint32_t kLeafWrap = 0x80000000u, kLeafCount = 0x7fffffffu;
@@ -334,6 +369,7 @@ struct GroupShared {
     uint2 stack[kStackCap];  // (first child, lane mask)
     uint8_t scount[kStackCap];
     float4 nsrc[kNodeCap];   // accepted node: centre of mass (group frame) + mass
+    float nsoft[kNodeCap];   // its largest spline support (per-particle softening only)
     uint32_t nmask[kNodeCap];
     uint8_t nwrap[kNodeCap];
     float4 lsrc[kLeafCap];   // opened leaf: centre (group frame) + first particle
@@ -342,11 +378,11 @@ struct GroupShared {
 };
 
 // Conservative decision for all particles inside [lo, hi] (group frame).
-template <bool PERIODIC, bool RELATIVE, bool TREEPM>
+template <bool PERIODIC, bool RELATIVE, bool TREEPM, bool VARH>
 __device__ __forceinline__ int classify_group(float4 C, float4 O, float gcx, float gcy, float gcz, float lox,
                                               float loy, float loz, float hix, float hiy, float hiz, float thr_min,
-                                              float thr_max, bool wide, const WalkConsts &k, float &dcx, float &dcy,
-                                              float &dcz) {
+                                              float thr_max, bool wide, float hsig, float hmin_g, const WalkConsts &k,
+                                              float &dcx, float &dcy, float &dcz) {
     dcx = C.x - gcx;
     dcy = C.y - gcy;
     dcz = C.z - gcz;
@@ -401,6 +437,8 @@ __device__ __forceinline__ int classify_group(float4 C, float4 O, float gcx, flo
         open_all = q > k.thr_const * dmax2 * up;
         acc_all = q <= k.thr_const * dmin2 * dn;
     }
+    if (VARH && hsig < 0.0f && hmin_g < -hsig && dmin2 < hsig * hsig)
+        acc_all = false;  // Sec. 3.2: some particle may have to open this node of mixed softenings
     if (guard_all || open_all)
         return kOpen;
     if (guard_none && acc_all)
@@ -425,9 +463,10 @@ __device__ __forceinline__ void newton_term(float rx, float ry, float rz, float 
 // An entry closer than the softening length h contributes nothing in this
 // pass (its mass is zeroed, its distance replaced by h so rsqrt stays finite)
 // and gets its spline term in a second pass, taken only when some lane met
-// such an entry.
-template <bool PERIODIC, bool TREEPM>
-__device__ __forceinline__ void sweep_full(const GroupShared &sh, int nf, float xox, float xoy, float xoz,
+// such an entry.  With per-particle softening (VARH) the support of an entry
+// is the larger of the lane's own (hi) and the node's largest (Sec. 3.2).
+template <bool PERIODIC, bool TREEPM, bool VARH>
+__device__ __forceinline__ void sweep_full(const GroupShared &sh, int nf, float xox, float xoy, float xoz, float hi,
                                            const WalkConsts &k, float &ax, float &ay, float &az, float &ph) {
     if (TREEPM || PERIODIC) {
         for (int e = 0; e < nf; e++) {
@@ -438,7 +477,11 @@ __device__ __forceinline__ void sweep_full(const GroupShared &sh, int nf, float 
                 ry = wrap_min_image(ry, k);
                 rz = wrap_min_image(rz, k);
             }
-            pair_term<TREEPM>(rx, ry, rz, fmaf(rx, rx, fmaf(ry, ry, rz * rz)), A.w, k, ax, ay, az, ph);
+            const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+            if (VARH)
+                pair_term_h<TREEPM>(rx, ry, rz, r2, A.w, fmaxf(hi, sh.nsoft[e]), k, ax, ay, az, ph);
+            else
+                pair_term<TREEPM>(rx, ry, rz, r2, A.w, k, ax, ay, az, ph);
             if (PERIODIC && !TREEPM)
                 ewald_term(rx, ry, rz, A.w, k, ax, ay, az, ph);
         }
@@ -455,26 +498,41 @@ __device__ __forceinline__ void sweep_full(const GroupShared &sh, int nf, float 
         for (int u = 0; u < 4; u++) {
             const float rx = A[u].x - xox, ry = A[u].y - xoy, rz = A[u].z - xoz;
             const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-            const bool sf = r2 < k.h2;
+            float h2 = k.h2;
+            if (VARH) {
+                const float he = fmaxf(hi, sh.nsoft[e + u]);
+                h2 = he * he;
+            }
+            const bool sf = r2 < h2;
             soft |= sf;
-            newton_term(rx, ry, rz, sf ? k.h2 : r2, sf ? 0.0f : A[u].w, ax, ay, az, ph);
+            newton_term(rx, ry, rz, sf ? h2 : r2, sf ? 0.0f : A[u].w, ax, ay, az, ph);
         }
     }
     for (; e < nf; e++) {
         const float4 A = sh.nsrc[e];
         const float rx = A.x - xox, ry = A.y - xoy, rz = A.z - xoz;
         const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-        const bool sf = r2 < k.h2;
+        float h2 = k.h2;
+        if (VARH) {
+            const float he = fmaxf(hi, sh.nsoft[e]);
+            h2 = he * he;
+        }
+        const bool sf = r2 < h2;
         soft |= sf;
-        newton_term(rx, ry, rz, sf ? k.h2 : r2, sf ? 0.0f : A.w, ax, ay, az, ph);
+        newton_term(rx, ry, rz, sf ? h2 : r2, sf ? 0.0f : A.w, ax, ay, az, ph);
     }
     if (__any_sync(0xffffffffu, soft)) {
         for (int q = 0; q < nf; q++) {
             const float4 A = sh.nsrc[q];
             const float rx = A.x - xox, ry = A.y - xoy, rz = A.z - xoz;
             const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-            if (r2 < k.h2)
+            if (VARH) {
+                const float he = fmaxf(hi, sh.nsoft[q]);
+                if (r2 < he * he)
+                    pair_term_h<false>(rx, ry, rz, r2, A.w, he, k, ax, ay, az, ph);
+            } else if (r2 < k.h2) {
                 pair_term<false>(rx, ry, rz, r2, A.w, k, ax, ay, az, ph);
+            }
         }
     }
 }
@@ -483,10 +541,10 @@ __device__ __forceinline__ void sweep_full(const GroupShared &sh, int nf, float 
 // (indices [kNodeCap - np, kNodeCap)): a lane not tagged adds a zero mass
 // (with r2 replaced by h2, since such a lane may sit on the node), and
 // entries inside the softening length are repaired as in sweep_full.
-template <bool PERIODIC, bool TREEPM>
+template <bool PERIODIC, bool TREEPM, bool VARH>
 __device__ __forceinline__ void sweep_partial(const GroupShared &sh, int np, unsigned lanebit, float xox, float xoy,
-                                              float xoz, const WalkConsts &k, float &ax, float &ay, float &az,
-                                              float &ph, uint32_t &cnt) {
+                                              float xoz, float hi, const WalkConsts &k, float &ax, float &ay,
+                                              float &az, float &ph, uint32_t &cnt) {
     const int e0 = kNodeCap - np;
     if (TREEPM || PERIODIC) {
         for (int e = e0; e < kNodeCap; e++) {
@@ -500,7 +558,11 @@ __device__ __forceinline__ void sweep_partial(const GroupShared &sh, int np, uns
             }
             const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
             cnt += mine ? 1u : 0u;
-            pair_term<TREEPM>(rx, ry, rz, mine ? r2 : 1.0f, mine ? E.w : 0.0f, k, ax, ay, az, ph);
+            if (VARH)
+                pair_term_h<TREEPM>(rx, ry, rz, mine ? r2 : 1.0f, mine ? E.w : 0.0f, fmaxf(hi, sh.nsoft[e]), k, ax,
+                                    ay, az, ph);
+            else
+                pair_term<TREEPM>(rx, ry, rz, mine ? r2 : 1.0f, mine ? E.w : 0.0f, k, ax, ay, az, ph);
             if (PERIODIC && !TREEPM)
                 ewald_term(rx, ry, rz, mine ? E.w : 0.0f, k, ax, ay, az, ph);
         }
@@ -513,27 +575,40 @@ __device__ __forceinline__ void sweep_partial(const GroupShared &sh, int np, uns
         const bool mine = (sh.nmask[e] & lanebit) != 0u;
         const float rx = E.x - xox, ry = E.y - xoy, rz = E.z - xoz;
         const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-        const bool sf = r2 < k.h2;
+        float h2 = k.h2;
+        if (VARH) {
+            const float he = fmaxf(hi, sh.nsoft[e]);
+            h2 = he * he;
+        }
+        const bool sf = r2 < h2;
         soft |= mine && sf;
         const bool use = mine && !sf;
         cnt += mine ? 1u : 0u;
-        newton_term(rx, ry, rz, use ? r2 : k.h2, use ? E.w : 0.0f, ax, ay, az, ph);
+        newton_term(rx, ry, rz, use ? r2 : h2, use ? E.w : 0.0f, ax, ay, az, ph);
     }
     if (__any_sync(0xffffffffu, soft)) {
         for (int e = e0; e < kNodeCap; e++) {
             const float4 E = sh.nsrc[e];
             const float rx = E.x - xox, ry = E.y - xoy, rz = E.z - xoz;
             const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-            if ((sh.nmask[e] & lanebit) && r2 < k.h2)
+            if (!(sh.nmask[e] & lanebit))
+                continue;
+            if (VARH) {
+                const float he = fmaxf(hi, sh.nsoft[e]);
+                if (r2 < he * he)
+                    pair_term_h<false>(rx, ry, rz, r2, E.w, he, k, ax, ay, az, ph);
+            } else if (r2 < k.h2) {
                 pair_term<false>(rx, ry, rz, r2, E.w, k, ax, ay, az, ph);
+            }
         }
     }
 }
 
 // Sweeps the queued opened leaves, particle by particle.
-template <bool PERIODIC, bool TREEPM>
+template <bool PERIODIC, bool TREEPM, bool VARH>
 __device__ __forceinline__ void sweep_leaves(const GroupShared &sh, int nl, unsigned lanebit, uint32_t self,
-                                             float xox, float xoy, float xoz, const float4 *__restrict__ spart,
+                                             float xox, float xoy, float xoz, float hi,
+                                             const float4 *__restrict__ spart, const float *__restrict__ psoft,
                                              const WalkConsts &k, float &ax, float &ay, float &az, float &ph,
                                              uint32_t &cnt) {
     for (int e = 0; e < nl; e++) {
@@ -561,7 +636,10 @@ __device__ __forceinline__ void sweep_leaves(const GroupShared &sh, int nl, unsi
             }
             const float q2 = fmaf(qx, qx, fmaf(qy, qy, qz * qz));
             if (mine && (uint32_t)jj != self && (!TREEPM || q2 <= k.rcut2)) {
-                pair_term<TREEPM>(qx, qy, qz, q2, P.w, k, ax, ay, az, ph);
+                if (VARH)
+                    pair_term_h<TREEPM>(qx, qy, qz, q2, P.w, fmaxf(hi, __ldg(&psoft[jj])), k, ax, ay, az, ph);
+                else
+                    pair_term<TREEPM>(qx, qy, qz, q2, P.w, k, ax, ay, az, ph);
                 if (PERIODIC && !TREEPM)
                     ewald_term(qx, qy, qz, P.w, k, ax, ay, az, ph);
                 cnt++;
@@ -576,6 +654,7 @@ struct TreeView {
     const float4 *bcen, *bcom;
     const int4 *blink;
     const float4 *spart;
+    const float *psoft, *bsoft;  // per-particle softening, else null
     const uint64_t *key;
     const uint32_t *perm;
     const double *pos;
@@ -584,7 +663,7 @@ struct TreeView {
 
 // Walks the tree for the group of gcount <= 32 active particles at positions
 // [g0, g0 + gcount) of the sorted active list (one per lane).
-template <bool PERIODIC, bool RELATIVE, bool TREEPM>
+template <bool PERIODIC, bool RELATIVE, bool TREEPM, bool VARH>
 __device__ __forceinline__ void group_walk(const TreeView &T, const WalkConsts &k, GroupShared &sh,
                                            const uint32_t *__restrict__ sidx, const uint32_t *__restrict__ slot,
                                            int64_t g0, int gcount, const float *__restrict__ a_old,
@@ -628,6 +707,11 @@ __device__ __forceinline__ void group_walk(const TreeView &T, const WalkConsts &
     float thr = k.thr_const;
     if (RELATIVE)
         thr = valid ? k.alpha_over_G * fabsf(a_old[out]) : 0.0f;
+    const float hi = VARH ? __ldg(&T.psoft[s]) : 0.0f;  // this particle's spline support
+    float hmin_g = VARH && valid ? hi : __int_as_float(0x7f800000);
+    if (VARH)
+        for (int o = 16; o > 0; o >>= 1)
+            hmin_g = fminf(hmin_g, __shfl_xor_sync(FULL, hmin_g, o));
 
     // group bounding box and criterion thresholds over the valid lanes
     const float inf = __int_as_float(0x7f800000);
@@ -700,14 +784,17 @@ __device__ __forceinline__ void group_walk(const TreeView &T, const WalkConsts &
         float4 C = make_float4(0.f, 0.f, 0.f, 0.f), O = C;
         int4 Lk = make_int4(0, 0, 0, 0);
         float dcx = 0.f, dcy = 0.f, dcz = 0.f;
+        float hsig = 0.0f;  // the node's largest softening, negative when mixed
         if (lane < ncand) {
             const uint2 cd = sh.cand[lane];
             nmask = cd.y;
             C = __ldg(&bcen[cd.x]);
             O = __ldg(&bcom[cd.x]);
             Lk = __ldg(&blink[cd.x]);
-            cls = classify_group<PERIODIC, RELATIVE, TREEPM>(C, O, gcx, gcy, gcz, lox, loy, loz, hix, hiy, hiz, tmin,
-                                                             tmax, wide, k, dcx, dcy, dcz);
+            if (VARH)
+                hsig = __ldg(&T.bsoft[cd.x]);
+            cls = classify_group<PERIODIC, RELATIVE, TREEPM, VARH>(C, O, gcx, gcy, gcz, lox, loy, loz, hix, hiy, hiz,
+                                                                   tmin, tmax, wide, hsig, hmin_g, k, dcx, dcy, dcz);
         }
         __syncwarp();
         const bool is_leaf = Lk.y == 0;
@@ -723,6 +810,8 @@ __device__ __forceinline__ void group_walk(const TreeView &T, const WalkConsts &
             sh.nsrc[at] = make_float4(dcx + O.x, dcy + O.y, dcz + O.z, O.w);
             sh.nmask[at] = nmask;
             sh.nwrap[at] = wrapf ? 1 : 0;
+            if (VARH)
+                sh.nsoft[at] = fabsf(hsig);
         }
         nf += __popc(bf);
         np += __popc(bq);
@@ -763,6 +852,7 @@ __device__ __forceinline__ void group_walk(const TreeView &T, const WalkConsts &
             const float MOx = __shfl_sync(FULL, O.x, t), MOy = __shfl_sync(FULL, O.y, t),
                         MOz = __shfl_sync(FULL, O.z, t), MOm = __shfl_sync(FULL, O.w, t);
             const int l0 = __shfl_sync(FULL, lk0, t), l1 = __shfl_sync(FULL, lk1, t);
+            const float hs = VARH ? __shfl_sync(FULL, hsig, t) : 0.0f;
             const bool act = (mm & lanebit) != 0u;
             const float dx = MCx - gcx, dy = MCy - gcy, dz = MCz - gcz;  // exact
             float px = xox - dx, py = xoy - dy, pz = xoz - dz;
@@ -786,10 +876,15 @@ __device__ __forceinline__ void group_walk(const TreeView &T, const WalkConsts &
             }
             const float gl = 0.6f * L;
             const bool guard = k.box_guard && fabsf(px) <= gl && fabsf(py) <= gl && fabsf(pz) <= gl;
-            const bool crit = RELATIVE ? (MOm * L * L > thr * r2 * r2) : (L * L > thr * r2);
+            bool crit = RELATIVE ? (MOm * L * L > thr * r2 * r2) : (L * L > thr * r2);
+            if (VARH)  // Sec. 3.2: a node of mixed softenings is opened inside its largest one
+                crit = crit || (hs < 0.0f && hi < -hs && r2 < hs * hs);
             const bool open = act && !far && (guard || crit);
             if (act && !far && !open) {
-                pair_term<TREEPM>(rx, ry, rz, r2, MOm, k, ax, ay, az, ph);
+                if (VARH)
+                    pair_term_h<TREEPM>(rx, ry, rz, r2, MOm, fmaxf(hi, fabsf(hs)), k, ax, ay, az, ph);
+                else
+                    pair_term<TREEPM>(rx, ry, rz, r2, MOm, k, ax, ay, az, ph);
                 if (EWALD)
                     ewald_term(rx, ry, rz, MOm, k, ax, ay, az, ph);
                 cnt++;
@@ -824,21 +919,23 @@ __device__ __forceinline__ void group_walk(const TreeView &T, const WalkConsts &
         }
         __syncwarp();
         if (nf + np >= kNodeFlush) {
-            sweep_full<PERIODIC, TREEPM>(sh, nf, xox, xoy, xoz, k, ax, ay, az, ph);
-            sweep_partial<PERIODIC, TREEPM>(sh, np, lanebit, xox, xoy, xoz, k, ax, ay, az, ph, cnt);
+            sweep_full<PERIODIC, TREEPM, VARH>(sh, nf, xox, xoy, xoz, hi, k, ax, ay, az, ph);
+            sweep_partial<PERIODIC, TREEPM, VARH>(sh, np, lanebit, xox, xoy, xoz, hi, k, ax, ay, az, ph, cnt);
             cnt += valid ? (uint32_t)nf : 0u;
             nf = np = 0;
         }
         if (nl >= kLeafFlush) {
-            sweep_leaves<PERIODIC, TREEPM>(sh, nl, lanebit, s, xox, xoy, xoz, spart, k, ax, ay, az, ph, cnt);
+            sweep_leaves<PERIODIC, TREEPM, VARH>(sh, nl, lanebit, s, xox, xoy, xoz, hi, spart, T.psoft, k, ax, ay, az,
+                                                 ph, cnt);
             nl = 0;
         }
         __syncwarp();
     }
-    sweep_full<PERIODIC, TREEPM>(sh, nf, xox, xoy, xoz, k, ax, ay, az, ph);
-    sweep_partial<PERIODIC, TREEPM>(sh, np, lanebit, xox, xoy, xoz, k, ax, ay, az, ph, cnt);
+    sweep_full<PERIODIC, TREEPM, VARH>(sh, nf, xox, xoy, xoz, hi, k, ax, ay, az, ph);
+    sweep_partial<PERIODIC, TREEPM, VARH>(sh, np, lanebit, xox, xoy, xoz, hi, k, ax, ay, az, ph, cnt);
     cnt += (uint32_t)nf;
-    sweep_leaves<PERIODIC, TREEPM>(sh, nl, lanebit, s, xox, xoy, xoz, spart, k, ax, ay, az, ph, cnt);
+    sweep_leaves<PERIODIC, TREEPM, VARH>(sh, nl, lanebit, s, xox, xoy, xoz, hi, spart, T.psoft, k, ax, ay, az, ph,
+                                         cnt);
     if (!valid)
         return;
     if (EWALD)  // the particle's own images and the background
@@ -863,7 +960,7 @@ __device__ __forceinline__ void group_walk(const TreeView &T, const WalkConsts &
 
 
 // One warp per group of `gsize` consecutive active particles.
-template <bool PERIODIC, bool RELATIVE, bool TREEPM>
+template <bool PERIODIC, bool RELATIVE, bool TREEPM, bool VARH>
 __global__ void __launch_bounds__(kGroupWarps * 32)
     k_walk_group(TreeView T, const uint32_t *__restrict__ sidx, const uint32_t *__restrict__ slot,
                  const float *__restrict__ a_old, int64_t n_act, int gsize, WalkConsts k, float *__restrict__ acc,
@@ -875,7 +972,8 @@ __global__ void __launch_bounds__(kGroupWarps * 32)
     if (g0 >= n_act)
         return;  // whole warp
     const int gcount = (int)min((int64_t)gsize, n_act - g0);
-    group_walk<PERIODIC, RELATIVE, TREEPM>(T, k, sh, sidx, slot, g0, gcount, a_old, acc, pot, nint, accumulate, err);
+    group_walk<PERIODIC, RELATIVE, TREEPM, VARH>(T, k, sh, sidx, slot, g0, gcount, a_old, acc, pot, nint, accumulate,
+                                                 err);
 }
 
 // One request of a batch: which tree, with which constants and criterion.
@@ -910,27 +1008,31 @@ __global__ void __launch_bounds__(kGroupWarps * 32)
         const TreeView T = R.T;
         const WalkConsts k = R.k;
         if (R.relative)
-            group_walk<PERIODIC, true, TREEPM>(T, k, sh, sidx, slot, G.x, (int)G.y, a_old, acc, pot, nint, 0, err);
+            group_walk<PERIODIC, true, TREEPM, false>(T, k, sh, sidx, slot, G.x, (int)G.y, a_old, acc, pot, nint, 0,
+                                                      err);
         else
-            group_walk<PERIODIC, false, TREEPM>(T, k, sh, sidx, slot, G.x, (int)G.y, a_old, acc, pot, nint, 0, err);
+            group_walk<PERIODIC, false, TREEPM, false>(T, k, sh, sidx, slot, G.x, (int)G.y, a_old, acc, pot, nint, 0,
+                                                       err);
         __syncwarp();
     }
 }
 
-template <bool P, bool R, bool T>
+template <bool P, bool R, bool T, bool V>
 void launch(const System *s, const WalkRequest &r, const WalkConsts &k, bool lanes, int *err, cudaStream_t st) {
     const int64_t warps = (r.n_act + 31) / 32;
     if (lanes) {
         const int64_t blocks = (warps * 32 + kWalkThreads - 1) / kWalkThreads;
-        k_walk<P, R, T><<<(unsigned)blocks, kWalkThreads, 0, st>>>(
+        k_walk<P, R, T, V><<<(unsigned)blocks, kWalkThreads, 0, st>>>(
             s->ncen, s->ncom, s->nlink, s->spart, s->key, s->perm, s->pos, s->x0[0], s->x0[1], s->x0[2], s->L0,
-            (int)s->nnodes, r.sorted_idx, r.slot, r.a_old, r.n_act, k, r.acc, r.pot, r.nint, r.accumulate);
+            (int)s->nnodes, s->psoft, s->nsoft, r.sorted_idx, r.slot, r.a_old, r.n_act, k, r.acc, r.pot, r.nint,
+            r.accumulate);
         count_launch();
     } else {
         const int64_t blocks = (warps + kGroupWarps - 1) / kGroupWarps;
         const size_t smem = kGroupWarps * sizeof(GroupShared);
-        TreeView tv{s->bcen, s->bcom, s->blink, s->spart, s->key, s->perm, s->pos, s->x0[0], s->x0[1], s->x0[2], s->L0};
-        k_walk_group<P, R, T><<<(unsigned)blocks, kGroupWarps * 32, smem, st>>>(
+        TreeView tv{s->bcen, s->bcom, s->blink, s->spart, s->psoft, s->bsoft, s->key,
+                    s->perm, s->pos,  s->x0[0], s->x0[1],  s->x0[2], s->L0};
+        k_walk_group<P, R, T, V><<<(unsigned)blocks, kGroupWarps * 32, smem, st>>>(
             tv, r.sorted_idx, r.slot, r.a_old, r.n_act, 32, k, r.acc, r.pot, r.nint, r.accumulate, err);
         count_launch();
     }
@@ -989,7 +1091,7 @@ size_t batch_req_bytes() { return sizeof(BatchReq); }
 
 void fill_batch_req(void *dst, const System *s, const tpm_force_params *p) {
     BatchReq r{};
-    r.T = TreeView{s->bcen, s->bcom, s->blink, s->spart, s->key, s->perm, s->pos, s->x0[0], s->x0[1], s->x0[2], s->L0};
+    r.T = TreeView{s->bcen, s->bcom, s->blink, s->spart, s->psoft, s->bsoft, s->key, s->perm, s->pos, s->x0[0], s->x0[1], s->x0[2], s->L0};
     r.k = make_consts(s, p);
     r.relative = p->crit == TPM_CRIT_RELATIVE ? 1 : 0;
     memcpy(dst, &r, sizeof r);
@@ -1027,22 +1129,27 @@ int walk_device(Ctx *c, const System *s, const tpm_force_params *p, const WalkRe
     const int ov = walk_override();
     const bool lanes = ov == 1 || (ov == 0 && per);
     int *err = s->err;
-    if (!per && !rel && !tpm)
-        launch<false, false, false>(s, r, k, lanes, err, st);
-    else if (!per && rel && !tpm)
-        launch<false, true, false>(s, r, k, lanes, err, st);
-    else if (!per && !rel && tpm)
-        launch<false, false, true>(s, r, k, lanes, err, st);
-    else if (!per && rel && tpm)
-        launch<false, true, true>(s, r, k, lanes, err, st);
-    else if (per && !rel && tpm)
-        launch<true, false, true>(s, r, k, lanes, err, st);
-    else if (per && rel && tpm)
-        launch<true, true, true>(s, r, k, lanes, err, st);
-    else if (per && !rel)
-        launch<true, false, false>(s, r, k, lanes, err, st);
+    const bool varh = s->psoft != nullptr;  // per-particle softening (open boundaries only)
+    if (varh && per) {
+        set_error("per-particle softening is available with open boundaries");
+        return TPM_EINVAL;
+    }
+    if (!per && !tpm)
+        rel ? (varh ? launch<false, true, false, true>(s, r, k, lanes, err, st)
+                    : launch<false, true, false, false>(s, r, k, lanes, err, st))
+            : (varh ? launch<false, false, false, true>(s, r, k, lanes, err, st)
+                    : launch<false, false, false, false>(s, r, k, lanes, err, st));
+    else if (!per && tpm)
+        rel ? (varh ? launch<false, true, true, true>(s, r, k, lanes, err, st)
+                    : launch<false, true, true, false>(s, r, k, lanes, err, st))
+            : (varh ? launch<false, false, true, true>(s, r, k, lanes, err, st)
+                    : launch<false, false, true, false>(s, r, k, lanes, err, st));
+    else if (tpm)
+        rel ? launch<true, true, true, false>(s, r, k, lanes, err, st)
+            : launch<true, false, true, false>(s, r, k, lanes, err, st);
     else
-        launch<true, true, false>(s, r, k, lanes, err, st);
+        rel ? launch<true, true, false, false>(s, r, k, lanes, err, st)
+            : launch<true, false, false, false>(s, r, k, lanes, err, st);
     TPM_CUDA(cudaGetLastError());
     return TPM_OK;
 }

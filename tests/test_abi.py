@@ -54,3 +54,12 @@ def test_version_and_clean_failure_without_device(lib):
         pytest.skip("a GPU is present")
     with pytest.raises(tpm.TreePMError):
         tpm.Context(0)
+
+
+def test_every_declared_function_has_a_binding_signature(lib):
+    # without argtypes ctypes passes Python ints as 32-bit C ints: a device
+    # pointer would arrive truncated
+    import paper_1909_04667_gb300 as tpm
+
+    missing = [n for n in declared_functions() if getattr(tpm._lib, n).argtypes is None]
+    assert not missing, missing
