@@ -238,6 +238,8 @@ def run_ours(args, rank, world):
     isolated = None if args.no_isolated else run_isolated(ctx, tpm, torch, dev, stream, flush, pos_d, mass_d,
                                                           max(2, min(args.steps, 5)))
     ewald = None if args.no_ewald else run_ewald(ctx, tpm, torch, dev, stream, flush, max(2, min(args.steps, 3)))
+    species = None if args.no_species else run_two_species(ctx, tpm, torch, dev, stream, flush,
+                                                           max(2, min(args.steps, 5)))
 
     ctx.close()
     serving = None if args.no_serving else run_serving(tpm, torch, dev)
@@ -277,6 +279,7 @@ def run_ours(args, rank, world):
         hierarchy=hierarchy,
         isolated_treepm=isolated,
         periodic_ewald_tree=ewald,
+        two_species_softening=species,
         serving=serving,
     )
 
@@ -551,6 +554,42 @@ def run_ewald(ctx, tpm, torch, dev, stream, flush, steps):
             "interactions_per_particle": inter / n}
 
 
+def run_two_species(ctx, tpm, torch, dev, stream, flush, steps):
+    """Per-particle softening: a Hernquist 2^20 halo (support 0.005) with a
+    compact stellar Plummer component of 2^18 particles (support 0.001); one
+    step = build + relative walk (|a_old| from a geometric first pass)."""
+    cfg = HERNQUIST
+    pos, mass, hs, _ = W.two_species(1 << 20, 1 << 18, W.CONFIG_SEEDS[2])
+    n = len(pos)
+    pos_d, mass_d, hs_d = (torch.from_numpy(x).to(dev) for x in (pos, mass, hs))
+    bp = lambda k: tpm.BuildParams(G=cfg["G"], h=cfg["h"], shift=root_shift(k, 8), leaf_bucket=cfg["bucket"])
+    fp_bh = tpm.ForceParams(crit=tpm.CRIT_BH, theta=cfg["theta"])
+    fp_rel = tpm.ForceParams(crit=tpm.CRIT_RELATIVE, alpha=cfg["alpha"])
+    s = ctx.build_tree(pos_d, mass_d, bp(0), hsoft=hs_d)
+    acc, pot, nint = s.compute_forces(fp=fp_bh)
+    s.release()
+    a_old = torch.linalg.vector_norm(acc, dim=1).contiguous()
+    res = []
+    for k in range(steps + 2):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        l2_flush(flush)
+        ev[0].record(stream)
+        sy = ctx.build_tree(pos_d, mass_d, bp(100 + k), hsoft=hs_d)
+        ev[1].record(stream)
+        sy.compute_forces(a_old=a_old, fp=fp_rel, acc=acc, pot=pot, n_int=nint)
+        ev[2].record(stream)
+        sy.release()
+        torch.cuda.synchronize()
+        if k >= 2:
+            res.append([ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])])
+    r = np.array(res).mean(0)
+    ms = float(r.sum())
+    inter = int(nint.to(torch.int64).sum().item())
+    return {"workload": "two_species_hernquist2^20_h0.005_plummer2^18_h0.001_relative_alpha%g" % cfg["alpha"],
+            "value": n / (ms * 1e-3), "unit": "forces/s", "ms_per_step": ms, "build_ms": float(r[0]),
+            "walk_ms": float(r[1]), "interactions_per_particle": inter / n}
+
+
 def run_isolated(ctx, tpm, torch, dev, stream, flush, pos_d, mass_d, steps):
     """TreePM with open boundaries on the Hernquist 2^20 set: zero-padded
     (2 pm_n)^3 mesh over the root cube, r_s = a_s mesh cells; one step =
@@ -669,6 +708,7 @@ def main():
     ap.add_argument("--no-hierarchy", action="store_true", help="skip the KDK time-bin hierarchy measurement")
     ap.add_argument("--no-isolated", action="store_true", help="skip the open-boundary TreePM measurement")
     ap.add_argument("--no-ewald", action="store_true", help="skip the periodic Ewald-tree measurement")
+    ap.add_argument("--no-species", action="store_true", help="skip the two-species softening measurement")
     args = ap.parse_args()
     if args.bucket:
         HERNQUIST["bucket"] = args.bucket
