@@ -166,6 +166,7 @@ def run_ours(args, rank, world):
     # first force: geometric criterion
     s = ctx.build_tree(pos_d, mass_d, bp(0))
     acc, pot, nint = s.compute_forces(fp=fp_bh)
+    s.sync_status()  # the walk's device status (stack capacity) before timing anything
     s.release()
     a_old = torch.linalg.vector_norm(acc, dim=1).contiguous()
     acc_buf = torch.empty((n, 3), dtype=torch.float32, device=dev)

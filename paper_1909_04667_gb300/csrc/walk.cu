@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(kWalkThreads)
 // ranges (children are contiguous in breadth-first order).
 // ======================================================================
 constexpr int kGroupWarps = 4;
-constexpr int kStackCap = 256;
+constexpr int kStackCap = 192;
 constexpr int kStackSafe = kStackCap - 64;  // above this, take one candidate at a time
 constexpr int kNodeFlush = 64;              // sweep once this many node entries are queued
 constexpr int kNodeCap = kNodeFlush + 32;   // one batch adds at most 32 (one per candidate)
