@@ -40,8 +40,8 @@ FLOPS_PER_INTERACTION = 20  # monopole pair term with potential, FP32 (the design doc
 # DRAM bytes (read + write) of one k_walk_group launch of the headline step,
 # from the ncu capture summarised in profiles/k_walk_group_hernquist_2p20_relative.md,
 # valid only for the walk source it was taken from
-WALK_TRAFFIC = {"bytes": 98.628352e6 + 12.795648e6,
-                "walk_cu_sha256": "41a448d2611dc070086950d46b9094c2d0f7bfc79987d141e8f9ab4b9f357f70"}
+WALK_TRAFFIC = {"bytes": 98.642688e6 + 12.928000e6,
+                "walk_cu_sha256": "8eed3a5686b923ba076ca2c4df60897c42d86f07d89c62389bbef74478ddc62e"}
 
 
 def walk_traffic():
