@@ -28,6 +28,7 @@
 //      -- three 16-byte records loaded with one vector load each -- and per
 //      sorted particle its position relative to its leaf centre plus mass.
 #include <cub/cub.cuh>
+#include <cuda/atomic>
 
 #include <algorithm>
 #include <climits>
@@ -420,11 +421,12 @@ __global__ void k_multipole(NodeArrays t, int64_t total, const uint32_t *__restr
     uint32_t cur = (uint32_t)node;
     while (cur != 0) {
         const uint32_t p = t.parent[cur];
-        __threadfence();  // this node's sums are visible before the parent learns it is done
         const uint32_t nc = t.nchild[p];
-        if (atomicAdd(&t.arrive[p], 1u) != nc - 1)
+        // release: this node's sums are visible before the parent learns it is
+        // done; acquire: the last child sees all its siblings' sums
+        cuda::atomic_ref<uint32_t, cuda::thread_scope_device> arrive(t.arrive[p]);
+        if (arrive.fetch_add(1u, cuda::memory_order_acq_rel) != nc - 1)
             return;  // a sibling still works; it will carry on upwards
-        __threadfence();
         m = sx = sy = sz = 0.0;
         hi = 0.0f;
         lo = INFINITY;
