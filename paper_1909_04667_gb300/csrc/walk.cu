@@ -401,14 +401,14 @@ __device__ __forceinline__ int classify_group(float4 C, float4 O, float gcx, flo
                 nz = fmaxf(fmaxf(az0, -az1), 0.0f);  // nearest |p - c|
     const float fx = fmaxf(fabsf(ax0), fabsf(ax1)), fy = fmaxf(fabsf(ay0), fabsf(ay1)),
                 fz = fmaxf(fabsf(az0), fabsf(az1));  // farthest |p - c|
+    bool maybe_far = false;  // some particles may see the node beyond the cutoff
     if (TREEPM) {
         const float hL = 0.5f * L;
         const float ex = fmaxf(nx - hL, 0.0f), ey = fmaxf(ny - hL, 0.0f), ez = fmaxf(nz - hL, 0.0f);
         if (fmaf(ex, ex, fmaf(ey, ey, ez * ez)) > k.rcut2 * up)
             return kSkip;
         const float gx = fmaxf(fx - hL, 0.0f), gy = fmaxf(fy - hL, 0.0f), gz = fmaxf(fz - hL, 0.0f);
-        if (fmaf(gx, gx, fmaf(gy, gy, gz * gz)) > k.rcut2 * dn)
-            return kMixed;  // some particles may see the node beyond the cutoff
+        maybe_far = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) > k.rcut2 * dn;
     }
     const float gl = 0.6f * L;
     const bool guard_all = k.box_guard && fmaxf(fx, fmaxf(fy, fz)) <= gl * dn;
@@ -439,9 +439,13 @@ __device__ __forceinline__ int classify_group(float4 C, float4 O, float gcx, flo
     }
     if (VARH && hsig < 0.0f && hmin_g < -hsig && dmin2 < hsig * hsig)
         acc_all = false;  // Sec. 3.2: some particle may have to open this node of mixed softenings
+    // Opening for all is exact even when the node lies beyond the cutoff for
+    // some particles: for them every descendant does too, and the leaf sweep
+    // drops pairs beyond the cutoff, so they gain no interaction.  Accepting
+    // needs every particle inside the cutoff.
     if (guard_all || open_all)
         return kOpen;
-    if (guard_none && acc_all)
+    if (!maybe_far && guard_none && acc_all)
         return kAccept;
     return kMixed;
 }
