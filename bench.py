@@ -17,6 +17,7 @@ Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|referenc
 from __future__ import annotations
 
 import argparse
+import collections
 import json
 import math
 import os
@@ -56,8 +57,9 @@ def walk_traffic():
 
 # ------------------------------------------------------------------ configs
 HERNQUIST = dict(n=1 << 20, seed=W.CONFIG_SEEDS[2], h=0.005, G=1.0, bucket=8, theta=0.5, alpha=0.0025)
-SERVING = dict(seed=W.CONFIG_SEEDS[5], n_systems=48, n_requests=600, rate=200.0, nmin=1 << 12, nmax=1 << 20,
-               overcommit=1.5, bytes_per_particle=118, round_ids=1 << 21)
+SERVING = dict(seed=W.CONFIG_SEEDS[5], budget_gb=60, n_requests=2000, warmup_requests=4000, rate=200.0,
+               load_factors=(1, 8), nmin=1 << 12, nmax=1 << 20, overcommit=1.5, bytes_per_particle=118,
+               round_ids=1 << 21)
 TIMEBINS = dict(nbins=8, seed=W.CONFIG_SEEDS[4], req_lo=64, req_hi=65536)
 HIERARCHY = dict(nbins=8, dt_tick=0.005, c_grav=0.025)
 ISOLATED = dict(pm_n=64, asmth=2.5, rcut=4.5)
@@ -409,42 +411,53 @@ def run_batching(ctx, tpm, torch, dev, stream, pos_d, mass_d, reps=3):
             "speedup": ms_req / ms_b, "max_rel_diff_vs_per_request": float(e.max())}
 
 
-def serving_workload(torch):
-    """Catalogue (host particles, pinned), and the request stream."""
+def serving_workload():
+    """Catalogue and request stream: systems with N log-uniform in [2^12, 2^20]
+    until their resident footprint (~118 B per particle) is overcommit x the
+    HBM budget; Poisson arrivals; each request a random system and a random
+    window of 1-100% of its particles (the particles are drawn in random
+    order, so a window is a uniform random subset)."""
     cfg = SERVING
-    cat = W.serving_catalogue(cfg["n_systems"], cfg["seed"], cfg["nmin"], cfg["nmax"])
-    parts = {}
-    for spec in cat:
-        pos, mass = spec.particles()
-        parts[spec.sid] = (torch.from_numpy(pos).pin_memory(), torch.from_numpy(mass).pin_memory(), spec)
+    budget = int(cfg["budget_gb"] * (1 << 30))
+    big = W.serving_catalogue(20000, cfg["seed"], cfg["nmin"], cfg["nmax"])
+    cat, footprint = [], 0
+    for spec in big:
+        if footprint >= cfg["overcommit"] * budget:
+            break
+        cat.append(spec)
+        footprint += spec.n * cfg["bytes_per_particle"]
     rng = np.random.Generator(np.random.PCG64(cfg["seed"] + 1))
-    arrivals = W.poisson_arrivals(cfg["n_requests"], cfg["rate"], cfg["seed"] + 2)
+    nw = cfg["warmup_requests"]
+    arrivals = W.poisson_arrivals(nw + cfg["n_requests"], cfg["rate"], cfg["seed"] + 2)
+    arrivals = np.concatenate([np.zeros(nw), arrivals[nw:] - arrivals[nw]])  # the warm-up prefix is not paced
     reqs = []
     for k, t in enumerate(arrivals):
         sid = int(rng.integers(0, len(cat)))
         n = cat[sid].n
         m = max(1, int(n * rng.uniform(0.01, 1.0)))
-        reqs.append((k, sid, np.sort(rng.choice(n, m, replace=False)).astype(np.int32), float(t)))
-    footprint = sum(s.n for s in cat) * cfg["bytes_per_particle"]
-    return cat, parts, reqs, footprint
+        off = int(rng.integers(0, n))
+        reqs.append((k, sid, ((off + np.arange(m)) % n).astype(np.int32), float(t)))
+    return cat, reqs, footprint, budget
 
 
 def run_serving(tpm, torch, dev):
-    """Continuous-batching server vs one call per request, on the same budget."""
+    """Continuous-batching server vs one call per request, on the same HBM
+    admission budget; particles drawn on the device when a system is built."""
     from paper_1909_04667_gb300.serve import ForceServer, ServeRequest, serve_per_request
 
     cfg = SERVING
-    cat, parts, reqs, footprint = serving_workload(torch)
-    # resident trees ~118 B per particle; the budget holds 1/1.5 of the
-    # catalogue plus the round plan (~30 B per id) and the largest build's peak
-    budget = int(footprint / cfg["overcommit"]) + 30 * cfg["round_ids"] + (200 << 20)
+    cat, reqs, footprint, budget = serving_workload()
 
     def source(sid):
-        pos, mass, spec = parts[sid]
+        spec = cat[sid]
+        pos, mass = spec.particles_on_device(torch, dev)
         return pos, mass, tpm.BuildParams(G=1.0, h=spec.h, shift=tuple(W.root_shift(spec.seed)), leaf_bucket=8)
 
-    def make():
-        return [ServeRequest(k, sid, ids, t) for k, sid, ids, t in reqs]
+    nw = cfg["warmup_requests"]
+
+    def make(warm):
+        sel = reqs[:nw] if warm else reqs[nw:]
+        return [ServeRequest(k, sid, ids, t) for k, sid, ids, t in sel]
 
     def stats(out, wall):
         lat = np.array([r.latency for r in out]) * 1e3
@@ -453,23 +466,40 @@ def run_serving(tpm, torch, dev):
                 "latency_ms_p99": float(np.percentile(lat, 99)), "makespan_s": wall,
                 "relative_criterion_share": float(np.mean([r.criterion == tpm.CRIT_RELATIVE for r in out]))}
 
+    # each arm first serves the warm-up prefix untimed until the budget holds a
+    # steady-state resident set, then the timed requests at their arrival times:
+    # at the stream's rate, then (saturation) the same requests at a multiple
+    def paced(factor):
+        out = make(False)
+        for r in out:
+            r.arrival /= factor
+        return out
+
     res = {}
     ctx = tpm.Context(dev.index, budget_bytes=budget)
-    srv = ForceServer(ctx, source, max_round_ids=cfg["round_ids"], max_round_requests=512, policy="adaptive")
-    srv.serve(make()[:20], realtime=False)  # warm-up (builds, module loading)
+    srv = ForceServer(ctx, source, max_round_ids=cfg["round_ids"], max_round_requests=512, policy="adaptive",
+                      keep_results=False)
+    srv.serve(make(True), realtime=False)
+    for f in cfg["load_factors"]:
+        b0, e0 = srv.builds, srv.evictions
+        t0 = time.perf_counter()
+        out = srv.serve(paced(f), realtime=True)
+        key = "continuous_batching" if f == 1 else "continuous_batching_x%d" % f
+        res[key] = dict(stats(out, time.perf_counter() - t0), builds=srv.builds - b0, evictions=srv.evictions - e0)
     srv.close()
-    srv = ForceServer(ctx, source, max_round_ids=cfg["round_ids"], max_round_requests=512, policy="adaptive")
-    t0 = time.perf_counter()
-    out = srv.serve(make(), realtime=True)
-    res["continuous_batching"] = dict(stats(out, time.perf_counter() - t0), builds=srv.builds,
-                                      evictions=srv.evictions)
-    srv.close()
-    t0 = time.perf_counter()
-    out = serve_per_request(ctx, source, make(), policy="adaptive", realtime=True)
-    res["per_request"] = stats(out, time.perf_counter() - t0)
+    resident = collections.OrderedDict()
+    serve_per_request(ctx, source, make(True), policy="adaptive", realtime=False, keep_results=False,
+                      resident=resident)
+    for f in cfg["load_factors"]:
+        t0 = time.perf_counter()
+        out = serve_per_request(ctx, source, paced(f), policy="adaptive", realtime=True, keep_results=False,
+                                resident=resident)
+        res["per_request" if f == 1 else "per_request_x%d" % f] = stats(out, time.perf_counter() - t0)
+    for system, _, _ in resident.values():
+        system.release()
     ctx.close()
-    res.update(workload="serving_%d_systems_N2^12-2^20_poisson%dHz_%d_requests" % (
-        cfg["n_systems"], int(cfg["rate"]), cfg["n_requests"]), hbm_budget_bytes=budget,
+    res.update(workload="serving_%d_systems_N2^12-2^20_poisson%dHz_%d_requests_after_%d_budget%dGB" % (
+        len(cat), int(cfg["rate"]), cfg["n_requests"], nw, cfg["budget_gb"]), hbm_budget_bytes=budget,
         catalogue_bytes=footprint)
     return res
 
@@ -710,9 +740,13 @@ def main():
     ap.add_argument("--no-isolated", action="store_true", help="skip the open-boundary TreePM measurement")
     ap.add_argument("--no-ewald", action="store_true", help="skip the periodic Ewald-tree measurement")
     ap.add_argument("--no-species", action="store_true", help="skip the two-species softening measurement")
+    ap.add_argument("--serving-requests", type=int, default=None,
+                    help="requests of the serving measurement (default 2000; 10000 is the full stream)")
     args = ap.parse_args()
     if args.bucket:
         HERNQUIST["bucket"] = args.bucket
+    if args.serving_requests:
+        SERVING["n_requests"] = args.serving_requests
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

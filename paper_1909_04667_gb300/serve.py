@@ -74,7 +74,8 @@ class ForceServer:
     arrays (pinned memory keeps the uploads asynchronous)."""
 
     def __init__(self, ctx: Context, source, max_round_ids: int = 1 << 21, max_round_requests: int = 512,
-                 theta: float = 0.5, alpha: float = 0.0025, policy: str = "adaptive", group_size: int = None):
+                 theta: float = 0.5, alpha: float = 0.0025, policy: str = "adaptive", group_size: int = None,
+                 keep_results: bool = True):
         import torch
 
         self.torch = torch
@@ -91,6 +92,14 @@ class ForceServer:
         self.resident: "collections.OrderedDict[int, _Resident]" = collections.OrderedDict()
         self.builds = 0
         self.evictions = 0
+        self.keep_results = keep_results  # False: time the results' return, then drop them
+        # pinned staging, reused by every round (one round is in flight at a
+        # time): ids in, results out -- asynchronous copies need pinned memory
+        m = self.max_ids
+        self.ids_h = torch.empty(m, dtype=torch.int32).pin_memory()
+        self.acc_h = torch.empty((m, 3), dtype=torch.float32).pin_memory()
+        self.pot_h = torch.empty(m, dtype=torch.float32).pin_memory()
+        self.nint_h = torch.empty(m, dtype=torch.int32).pin_memory()
 
     def close(self):
         for r in self.resident.values():
@@ -115,7 +124,8 @@ class ForceServer:
         if sid in self.resident:
             self.resident.move_to_end(sid)
             return True
-        pos, mass, bp = self.source(sid)
+        with torch.cuda.stream(self.build_stream):  # a source may draw the particles on the device
+            pos, mass, bp = self.source(sid)
         while True:
             try:
                 system = self.ctx.build_tree(pos, mass, bp, stream=self.build_stream.cuda_stream)
@@ -146,8 +156,11 @@ class ForceServer:
         with torch.cuda.stream(self.walk_stream):
             sizes = [len(r.ids) for r in reqs]
             off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
-            ids_h = torch.from_numpy(np.concatenate([r.ids for r in reqs]).astype(np.int32)).pin_memory()
-            ids_d = ids_h.to(self.dev, non_blocking=True)
+            n = int(off[-1])
+            ids_np = self.ids_h.numpy()
+            for k, r in enumerate(reqs):
+                ids_np[off[k]:off[k + 1]] = r.ids
+            ids_d = self.ids_h[:n].to(self.dev, non_blocking=True)
             systems, params, aolds = [], [], []
             for k, r in enumerate(reqs):
                 res = self.resident[r.sid]
@@ -159,7 +172,6 @@ class ForceServer:
                 params.append(fp)
                 aolds.append(res.aold[part])
             a_old = torch.cat(aolds).contiguous()
-            n = int(off[-1])
             acc = torch.empty((n, 3), dtype=torch.float32, device=self.dev)
             pot = torch.empty(n, dtype=torch.float32, device=self.dev)
             nint = torch.empty(n, dtype=torch.int32, device=self.dev)
@@ -172,12 +184,12 @@ class ForceServer:
                 part = ids_d[off[k]:off[k + 1]].long()
                 res.aold[part] = amag[off[k]:off[k + 1]]
                 res.aold_valid[r.ids] = True
-            acc_h = acc.to("cpu", non_blocking=True)
-            pot_h = pot.to("cpu", non_blocking=True)
-            nint_h = nint.to("cpu", non_blocking=True)
+            self.acc_h[:n].copy_(acc, non_blocking=True)
+            self.pot_h[:n].copy_(pot, non_blocking=True)
+            self.nint_h[:n].copy_(nint, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(self.walk_stream)
-        return _Round(reqs, acc_h, pot_h, nint_h, off, ev, [r.sid for r in reqs])
+        return _Round(reqs, self.acc_h[:n], self.pot_h[:n], self.nint_h[:n], off, ev, [r.sid for r in reqs])
 
     def _complete(self, rnd: _Round, t0: float):
         rnd.event.synchronize()
@@ -185,7 +197,8 @@ class ForceServer:
         acc, pot, nint = rnd.acc.numpy(), rnd.pot.numpy(), rnd.nint.numpy()
         for k, r in enumerate(rnd.reqs):
             lo, hi = rnd.offsets[k], rnd.offsets[k + 1]
-            r.acc, r.pot, r.n_int = acc[lo:hi], pot[lo:hi], nint[lo:hi]
+            if self.keep_results:  # copies: the pinned buffers serve the next round
+                r.acc, r.pot, r.n_int = acc[lo:hi].copy(), pot[lo:hi].copy(), nint[lo:hi].copy()
             r.t_done = now
             res = self.resident.get(r.sid)
             if res is not None:
@@ -236,15 +249,17 @@ class ForceServer:
 
 
 def serve_per_request(ctx: Context, source, requests, theta: float = 0.5, alpha: float = 0.0025,
-                      policy: str = "adaptive", realtime: bool = True):
+                      policy: str = "adaptive", realtime: bool = True, keep_results: bool = True, resident=None):
     """Baseline: requests in arrival order, each with its own build (if the
     system is not resident), ``tpm_compute_forces`` call and synchronisation;
     LRU eviction under the same budget, for a build or for the scratch memory
-    of a force call."""
+    of a force call.  ``resident`` (an OrderedDict) keeps the resident systems
+    across calls; without it they are released at the end."""
     import torch
 
     dev = torch.device("cuda", ctx.device)
-    resident = collections.OrderedDict()
+    keep = resident is not None
+    resident = resident if keep else collections.OrderedDict()
     reqs = sorted(requests, key=lambda r: r.arrival)
     t0 = time.perf_counter()
     for r in reqs:
@@ -286,8 +301,11 @@ def serve_per_request(ctx: Context, source, requests, theta: float = 0.5, alpha:
                 resident.pop(victim)[0].release()
         aold[part] = torch.linalg.vector_norm(acc, dim=1)
         valid[r.ids] = True
-        r.acc, r.pot, r.n_int = acc.cpu().numpy(), pot.cpu().numpy(), nint.cpu().numpy()
+        a_h, p_h, n_h = acc.cpu().numpy(), pot.cpu().numpy(), nint.cpu().numpy()
+        if keep_results:
+            r.acc, r.pot, r.n_int = a_h, p_h, n_h
         r.t_done = time.perf_counter() - t0
-    for system, _, _ in resident.values():
-        system.release()
+    if not keep:
+        for system, _, _ in resident.values():
+            system.release()
     return reqs

@@ -251,6 +251,26 @@ class SystemSpec:
             return plummer(self.n, self.seed)
         return hernquist(self.n, self.seed)
 
+    def particles_on_device(self, torch, device):
+        """The same profile drawn on ``device`` with torch's generator seeded
+        from ``seed`` (another sample than ``particles()``; for large served
+        catalogues whose host generation would dominate): FP64 positions,
+        FP32 masses, both device tensors."""
+        g = torch.Generator(device=device)
+        g.manual_seed(self.seed)
+        u = torch.rand(self.n, dtype=torch.float64, device=device, generator=g)
+        if self.profile == "plummer":
+            u = u.clamp(1e-300, 1.0 - 1e-16)
+            r = 1.0 / torch.sqrt(u ** (-2.0 / 3.0) - 1.0)
+        else:
+            rs = torch.sqrt(u * (100.0 / 101.0) ** 2)
+            r = rs / (1.0 - rs)
+        d = torch.randn(self.n, 3, dtype=torch.float64, device=device, generator=g)
+        d = d / torch.linalg.vector_norm(d, dim=1, keepdim=True).clamp_min(1e-300)
+        pos = (r[:, None] * d).contiguous()
+        mass = torch.full((self.n,), 1.0 / self.n, dtype=torch.float32, device=device)
+        return pos, mass
+
 
 def serving_catalogue(count: int, seed: int, nmin: int = 1 << 12, nmax: int = 1 << 20):
     """``count`` system specs: N log-uniform in [nmin, nmax], profile 50/50,
