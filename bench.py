@@ -41,8 +41,8 @@ FLOPS_PER_INTERACTION = 20  # monopole pair term with potential, FP32 (the design doc
 # DRAM bytes (read + write) of one k_walk_group launch of the headline step,
 # from the ncu capture summarised in profiles/k_walk_group_hernquist_2p20_relative.md,
 # valid only for the walk source it was taken from
-WALK_TRAFFIC = {"bytes": 98.642688e6 + 12.928000e6,
-                "walk_cu_sha256": "8eed3a5686b923ba076ca2c4df60897c42d86f07d89c62389bbef74478ddc62e"}
+WALK_TRAFFIC = {"bytes": 98.656512e6 + 12.715264e6,
+                "walk_cu_sha256": "788332476922d758fe050b7bd71c46f0276af500f49992b55c4a4764e492aaf9"}
 
 
 def walk_traffic():
