@@ -18,10 +18,11 @@
 //      ranges, skip indices and parents follow from searches in the sorted
 //      keys.  No level-by-level passes and no host round trip but one (the
 //      node count, to size the node tables)
-//   4. FP64 masses and mass-weighted positions summed bottom-up, children in
-//      ascending octant order and a leaf's particles in sorted order, with
-//      explicit round-to-nearest operations (no contraction), so the result
-//      is the same bit for bit on any correct implementation of that order
+//   4. FP64 masses and mass-weighted positions summed bottom-up in one pass,
+//      children in ascending octant order and a leaf's particles in sorted
+//      order, with explicit round-to-nearest operations (no contraction), so
+//      the result is the same bit for bit on any correct implementation of
+//      that order
 //   5. pre-order and breadth-first tables for the walks: per node the FP32 geometric
 //      centre (exact: it lies on the 2^-22 L0 grid), side, centre of mass
 //      relative to the centre, mass, skip index, particle range and leaf flag
@@ -188,6 +189,24 @@ __global__ void k_root(BuildState *__restrict__ st, int periodic, double box, do
     st->scale = __ddiv_rn(ldexp(1.0, kMaxLevel), st->L0);
 }
 
+// floor(v) clamped to [0, 2^21 - 1], read off the bits of v (integer
+// operations only: FP64 arithmetic is scarce on this GPU).  v = m 2^(e - 52)
+// with the 53-bit significand m; for 1 <= v < 2^21 the integer part is
+// m >> (52 - e); negative v (sign bit set) and v < 1 give 0, v >= 2^21 (and
+// non-finite v) the largest coordinate.
+__device__ __forceinline__ uint32_t cell_coord(double v) {
+    const long long b = __double_as_longlong(v);
+    if (b < 0)
+        return 0u;
+    const int e = (int)(b >> 52) - 1023;
+    if (e < 0)
+        return 0u;
+    if (e >= kMaxLevel)
+        return (1u << kMaxLevel) - 1u;
+    const uint64_t m = ((uint64_t)b & 0xfffffffffffffull) | (1ull << 52);
+    return (uint32_t)(m >> (52 - e));
+}
+
 // K1: Morton keys of the 21-bit cell coordinates q = floor((x - x0) 2^21 / L0).
 __global__ void k_keys(const double *__restrict__ pos, int64_t n, const BuildState *__restrict__ st,
                        uint64_t *__restrict__ key, uint32_t *__restrict__ idx) {
@@ -198,15 +217,8 @@ __global__ void k_keys(const double *__restrict__ pos, int64_t n, const BuildSta
     const double scale = st->scale;
     uint64_t k = 0;
 #pragma unroll
-    for (int a = 0; a < 3; a++) {
-        double f = floor(__dmul_rn(__dsub_rn(pos[3 * i + a], o[a]), scale));
-        long long q = (long long)f;
-        if (f < 0.0)
-            q = 0;
-        if (f > (double)((1 << kMaxLevel) - 1))
-            q = (1 << kMaxLevel) - 1;
-        k |= spread3((uint64_t)q) << a;
-    }
+    for (int a = 0; a < 3; a++)
+        k |= spread3(cell_coord(__dmul_rn(__dsub_rn(pos[3 * i + a], o[a]), scale))) << a;
     key[i] = k;
     idx[i] = (uint32_t)i;
 }
@@ -387,7 +399,10 @@ __global__ void k_nodes(const uint64_t *__restrict__ key, int64_t n, const uint3
 // and so on up to the root.  Sums are stored by breadth-first index, where a
 // node's children are contiguous, so the children's sums load independently.
 // Explicit round-to-nearest adds / muls, so every sum has the same fixed
-// order and value whichever thread computes it.
+// order and value whichever thread computes it.  The climb is a chain of
+// dependent memory round trips, so each step loads the links it needs next
+// (parent, child count, breadth-first indices: read-only here) before its
+// atomic, and a leaf loads its particles four at a time before summing them.
 __global__ void k_multipole(NodeArrays t, int64_t total, const uint32_t *__restrict__ pre2bfs,
                             const double *__restrict__ spos, const float *__restrict__ smass, double *__restrict__ M,
                             double *__restrict__ S, const float *__restrict__ psoft, float *__restrict__ hmx,
@@ -395,21 +410,37 @@ __global__ void k_multipole(NodeArrays t, int64_t total, const uint32_t *__restr
     const int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (node >= total || t.nchild[node] != 0)
         return;
+    const uint32_t f = t.first[node], e = f + t.count[node];
+    uint32_t p = node ? t.parent[node] : 0u;  // the climb's first parent
+    uint32_t q = pre2bfs[node];
     double m = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
     float hi = 0.0f, lo = INFINITY;  // largest / smallest softening (per-particle softening only)
-    const uint32_t f = t.first[node], e = f + t.count[node];
-    for (uint32_t s = f; s < e; s++) {
-        const double ms = (double)smass[s];
-        m = __dadd_rn(m, ms);
-        sx = __dadd_rn(sx, __dmul_rn(ms, spos[3 * s]));
-        sy = __dadd_rn(sy, __dmul_rn(ms, spos[3 * s + 1]));
-        sz = __dadd_rn(sz, __dmul_rn(ms, spos[3 * s + 2]));
-        if (psoft) {
-            hi = fmaxf(hi, psoft[s]);
-            lo = fminf(lo, psoft[s]);
+    for (uint32_t s = f; s < e; s += 4) {
+        double ms[4], px[4], py[4], pz[4];
+        float hs[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            const uint32_t j = min(s + u, e - 1);
+            ms[u] = (double)smass[j];
+            px[u] = spos[3 * j];
+            py[u] = spos[3 * j + 1];
+            pz[u] = spos[3 * j + 2];
+            hs[u] = psoft ? psoft[j] : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            if (s + u < e) {
+                m = __dadd_rn(m, ms[u]);
+                sx = __dadd_rn(sx, __dmul_rn(ms[u], px[u]));
+                sy = __dadd_rn(sy, __dmul_rn(ms[u], py[u]));
+                sz = __dadd_rn(sz, __dmul_rn(ms[u], pz[u]));
+                if (psoft) {
+                    hi = fmaxf(hi, hs[u]);
+                    lo = fminf(lo, hs[u]);
+                }
+            }
         }
     }
-    uint32_t q = pre2bfs[node];
     M[q] = m;
     S[3 * q] = sx;
     S[3 * q + 1] = sy;
@@ -420,8 +451,11 @@ __global__ void k_multipole(NodeArrays t, int64_t total, const uint32_t *__restr
     }
     uint32_t cur = (uint32_t)node;
     while (cur != 0) {
-        const uint32_t p = t.parent[cur];
+        // links of this step, loaded ahead of the atomic
         const uint32_t nc = t.nchild[p];
+        const uint32_t c0 = pre2bfs[p + 1];  // first child; the others follow it
+        const uint32_t pq = pre2bfs[p];
+        const uint32_t pp = p ? t.parent[p] : 0u;
         // release: this node's sums are visible before the parent learns it is
         // done; acquire: the last child sees all its siblings' sums
         cuda::atomic_ref<uint32_t, cuda::thread_scope_device> arrive(t.arrive[p]);
@@ -430,7 +464,6 @@ __global__ void k_multipole(NodeArrays t, int64_t total, const uint32_t *__restr
         m = sx = sy = sz = 0.0;
         hi = 0.0f;
         lo = INFINITY;
-        const uint32_t c0 = pre2bfs[p + 1];  // first child; the others follow it
         for (uint32_t c = c0; c < c0 + nc; c++) {
             m = __dadd_rn(m, __ldcg(&M[c]));
             sx = __dadd_rn(sx, __ldcg(&S[3 * c]));
@@ -441,16 +474,16 @@ __global__ void k_multipole(NodeArrays t, int64_t total, const uint32_t *__restr
                 lo = fminf(lo, __ldcg(&hmn[c]));
             }
         }
-        q = pre2bfs[p];
-        M[q] = m;
-        S[3 * q] = sx;
-        S[3 * q + 1] = sy;
-        S[3 * q + 2] = sz;
+        M[pq] = m;
+        S[3 * pq] = sx;
+        S[3 * pq + 1] = sy;
+        S[3 * pq + 2] = sz;
         if (psoft) {
-            hmx[q] = hi;
-            hmn[q] = lo;
+            hmx[pq] = hi;
+            hmn[pq] = lo;
         }
         cur = p;
+        p = pp;
     }
 }
 
@@ -465,7 +498,6 @@ struct NodeOut {
     int4 *link;
     uint8_t *level;
     uint64_t *prefix;
-    double *mass, *comd;
     float4 *bcen, *bcom;
     int4 *blink;
     float4 *spart;
@@ -474,7 +506,11 @@ struct NodeOut {
 
 // K5: walk tables.  Pre-order: FP32 geometric centre (exact, on the 2^-22 L0
 // grid) and side, centre of mass relative to the centre and mass, (skip,
-// first particle, count, leaf flag), plus the FP64 values for export.
+// first particle, count, leaf flag), plus level and key prefix for export.
+// The FP32 centre-of-mass offset takes S / m as S times the correctly rounded
+// 1 / m (one FP64 reciprocal instead of three divisions; the FP64 product is
+// within an ulp of the quotient, far below the FP32 rounding of the offset).
+// The exact FP64 centre of mass S / m is formed when the tree is exported.
 // Breadth-first (level by level, each level in key order, so that a node's
 // children are contiguous): the same records with (first child, child count,
 // first particle, count).  A leaf also writes its particles relative to its
@@ -491,7 +527,8 @@ __global__ void k_finalize(NodeArrays t, const uint32_t *__restrict__ pre2bfs, i
     const uint64_t pre = t.prefix[p];
     const uint32_t q = pre2bfs[p];
     const double m = M[q];
-    const double cx = __ddiv_rn(S[3 * q], m), cy = __ddiv_rn(S[3 * q + 1], m), cz = __ddiv_rn(S[3 * q + 2], m);
+    const double rm = __drcp_rn(m);
+    const double cx = __dmul_rn(S[3 * q], rm), cy = __dmul_rn(S[3 * q + 1], rm), cz = __dmul_rn(S[3 * q + 2], rm);
     const double half = ldexp(L0, -(lvl + 1));
     const double rx = (double)(2 * (uint64_t)compact3(pre) + 1) * half;
     const double ry = (double)(2 * (uint64_t)compact3(pre >> 1) + 1) * half;
@@ -504,10 +541,6 @@ __global__ void k_finalize(NodeArrays t, const uint32_t *__restrict__ pre2bfs, i
     o.link[p] = make_int4((int)t.skip[p], (int)f, (int)c, nch == 0);
     o.level[p] = (uint8_t)lvl;
     o.prefix[p] = pre;
-    o.mass[p] = m;
-    o.comd[3 * p] = cx;
-    o.comd[3 * p + 1] = cy;
-    o.comd[3 * p + 2] = cz;
     o.bcen[q] = cen;
     o.bcom[q] = com;
     o.blink[q] = make_int4(nch ? (int)pre2bfs[p + 1] : 0, (int)nch, (int)f, (int)c);
@@ -651,7 +684,6 @@ int build_tree_device(Ctx *c, System *s, const double *pos_in, const float *mass
 
     // ---- nodes in pre-order
     NodeArrays t{};
-    double *M, *S;
     TPM_CHECK(tmp.get(&t.first, nn, st));
     TPM_CHECK(tmp.get(&t.count, nn, st));
     TPM_CHECK(tmp.get(&t.skip, nn, st));
@@ -661,8 +693,10 @@ int build_tree_device(Ctx *c, System *s, const double *pos_in, const float *mass
     TPM_CHECK(tmp.get(&t.order, nn, st));
     TPM_CHECK(tmp.get(&t.level, nn, st));
     TPM_CHECK(tmp.get(&t.prefix, nn, st));
-    TPM_CHECK(tmp.get(&M, nn, st));
-    TPM_CHECK(tmp.get(&S, 3 * nn, st));
+    // FP64 sums by breadth-first index, kept with the system for export
+    TPM_CHECK(s->mem.get(&s->msum, nn, st));
+    TPM_CHECK(s->mem.get(&s->ssum, 3 * nn, st));
+    double *M = s->msum, *S = s->ssum;
     TPM_CUDA(cudaMemsetAsync(t.nchild, 0, nn * sizeof(uint32_t), st));
     TPM_CUDA(cudaMemsetAsync(t.arrive, 0, nn * sizeof(uint32_t), st));
     k_nodes<<<blocks_for(n), kThreads, 0, st>>>(s->key, n, base, top_level, leaf_level, t);
@@ -671,10 +705,11 @@ int build_tree_device(Ctx *c, System *s, const double *pos_in, const float *mass
 
     // ---- breadth-first order: a stable sort of the pre-order by level
     uint8_t *level_sorted;
-    uint32_t *bfs2pre, *pre2bfs;
+    uint32_t *bfs2pre;
     TPM_CHECK(tmp.get(&level_sorted, nn, st));
     TPM_CHECK(tmp.get(&bfs2pre, nn, st));
-    TPM_CHECK(tmp.get(&pre2bfs, nn, st));
+    TPM_CHECK(s->mem.get(&s->pre2bfs, nn, st));
+    uint32_t *pre2bfs = s->pre2bfs;
     size_t lsort_bytes = 0;
     TPM_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, lsort_bytes, t.level, level_sorted, t.order, bfs2pre, (int)nn,
                                              0, 5, st));
@@ -706,13 +741,11 @@ int build_tree_device(Ctx *c, System *s, const double *pos_in, const float *mass
     TPM_CHECK(s->mem.get(&s->nlink, nn, st));
     TPM_CHECK(s->mem.get(&s->nlevel, nn, st));
     TPM_CHECK(s->mem.get(&s->nprefix, nn, st));
-    TPM_CHECK(s->mem.get(&s->nmass, nn, st));
-    TPM_CHECK(s->mem.get(&s->ncomd, 3 * nn, st));
     TPM_CHECK(s->mem.get(&s->bcen, nn, st));
     TPM_CHECK(s->mem.get(&s->bcom, nn, st));
     TPM_CHECK(s->mem.get(&s->blink, nn, st));
-    NodeOut o{s->ncen,  s->ncom, s->nlink, s->nlevel, s->nprefix, s->nmass,
-              s->ncomd, s->bcen, s->bcom,  s->blink,  s->spart,  s->nsoft, s->bsoft};
+    NodeOut o{s->ncen, s->ncom,  s->nlink, s->nlevel, s->nprefix, s->bcen,
+              s->bcom, s->blink, s->spart, s->nsoft,  s->bsoft};
     k_finalize<<<blocks_for(nn), kThreads, 0, st>>>(t, pre2bfs, nn, M, S, spos, smass, hmx, hmn, s->x0[0], s->x0[1],
                                                     s->x0[2], s->L0, o);
     count_launch();

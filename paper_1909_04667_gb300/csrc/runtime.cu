@@ -628,10 +628,23 @@ int tpm_tree_export(tpm_ctx *h, tpm_sys sid, uint64_t *key, uint32_t *perm, uint
         TPM_CUDA(cudaMemcpy(level, s->nlevel, m, cudaMemcpyDeviceToHost));
     if (prefix)
         TPM_CUDA(cudaMemcpy(prefix, s->nprefix, m * 8, cudaMemcpyDeviceToHost));
-    if (mass)
-        TPM_CUDA(cudaMemcpy(mass, s->nmass, m * 8, cudaMemcpyDeviceToHost));
-    if (com)
-        TPM_CUDA(cudaMemcpy(com, s->ncomd, 3 * m * 8, cudaMemcpyDeviceToHost));
+    if (mass || com) {
+        // FP64 sums by breadth-first index; the centre of mass is S / m
+        // (IEEE division, correctly rounded as on the device)
+        std::vector<double> M(m), S(3 * m);
+        std::vector<uint32_t> q(m);
+        TPM_CUDA(cudaMemcpy(M.data(), s->msum, m * 8, cudaMemcpyDeviceToHost));
+        TPM_CUDA(cudaMemcpy(S.data(), s->ssum, 3 * m * 8, cudaMemcpyDeviceToHost));
+        TPM_CUDA(cudaMemcpy(q.data(), s->pre2bfs, m * 4, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < m; i++) {
+            const double mi = M[q[i]];
+            if (mass)
+                mass[i] = mi;
+            if (com)
+                for (int a = 0; a < 3; a++)
+                    com[3 * i + a] = S[3 * (size_t)q[i] + a] / mi;
+        }
+    }
     if (xtree)
         TPM_CUDA(cudaMemcpy(xtree, s->pos, 3 * n * 8, cudaMemcpyDeviceToHost));
     if (first || count || skip) {

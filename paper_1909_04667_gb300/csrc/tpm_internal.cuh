@@ -122,8 +122,11 @@ struct System {
     int4 *blink = nullptr;
     uint8_t *nlevel = nullptr;
     uint64_t *nprefix = nullptr;
-    double *nmass = nullptr;  // FP64
-    double *ncomd = nullptr;  // FP64 centre of mass, n x 3
+    // FP64 mass and mass-weighted position sums by breadth-first index, and
+    // the pre-order -> breadth-first map (for export)
+    double *msum = nullptr;
+    double *ssum = nullptr;
+    uint32_t *pre2bfs = nullptr;
 
     // device status word: bit 0 an active id was out of range, bit 1 the group
     // walk's candidate stack overflowed (read and cleared by tpm_sync_status)

@@ -464,11 +464,12 @@ __device__ __forceinline__ void newton_term(float rx, float ry, float rz, float 
 
 // Node entries accepted by every particle of the group sit at the front of the
 // node queue: no lane masks, straight-line Newtonian terms four at a time.
-// An entry closer than the softening length h contributes nothing in this
-// pass (its mass is zeroed, its distance replaced by h so rsqrt stays finite)
-// and gets its spline term in a second pass, taken only when some lane met
-// such an entry.  With per-particle softening (VARH) the support of an entry
-// is the larger of the lane's own (hi) and the node's largest (Sec. 3.2).
+// With one softening length h every entry first gets the Newtonian term at
+// max(r, h); when some lane met an entry closer than h (its smallest r^2 is
+// below h^2, rare for accepted nodes), a second pass takes the h-term of those
+// entries out again and adds their spline term.  With per-particle softening
+// (VARH) the support of an entry is the larger of the lane's own (hi) and the
+// node's largest (Sec. 3.2), and such entries add zero mass in the first pass.
 template <bool PERIODIC, bool TREEPM, bool VARH>
 __device__ __forceinline__ void sweep_full(const GroupShared &sh, int nf, float xox, float xoy, float xoz, float hi,
                                            const WalkConsts &k, float &ax, float &ay, float &az, float &ph) {
@@ -488,6 +489,42 @@ __device__ __forceinline__ void sweep_full(const GroupShared &sh, int nf, float 
                 pair_term<TREEPM>(rx, ry, rz, r2, A.w, k, ax, ay, az, ph);
             if (PERIODIC && !TREEPM)
                 ewald_term(rx, ry, rz, A.w, k, ax, ay, az, ph);
+        }
+        return;
+    }
+    if (!VARH) {
+        float rmin = __int_as_float(0x7f800000);
+        int e = 0;
+        for (; e + 3 < nf; e += 4) {
+            float4 A[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                A[u] = sh.nsrc[e + u];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const float rx = A[u].x - xox, ry = A[u].y - xoy, rz = A[u].z - xoz;
+                const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+                rmin = fminf(rmin, r2);
+                newton_term(rx, ry, rz, fmaxf(r2, k.h2), A[u].w, ax, ay, az, ph);
+            }
+        }
+        for (; e < nf; e++) {
+            const float4 A = sh.nsrc[e];
+            const float rx = A.x - xox, ry = A.y - xoy, rz = A.z - xoz;
+            const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+            rmin = fminf(rmin, r2);
+            newton_term(rx, ry, rz, fmaxf(r2, k.h2), A.w, ax, ay, az, ph);
+        }
+        if (__any_sync(0xffffffffu, rmin < k.h2)) {
+            for (int q = 0; q < nf; q++) {
+                const float4 A = sh.nsrc[q];
+                const float rx = A.x - xox, ry = A.y - xoy, rz = A.z - xoz;
+                const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+                if (r2 < k.h2) {
+                    newton_term(rx, ry, rz, k.h2, -A.w, ax, ay, az, ph);
+                    pair_term<false>(rx, ry, rz, r2, A.w, k, ax, ay, az, ph);
+                }
+            }
         }
         return;
     }
@@ -543,8 +580,8 @@ __device__ __forceinline__ void sweep_full(const GroupShared &sh, int nf, float 
 
 // Node entries for a subset of the lanes sit at the back of the node queue
 // (indices [kNodeCap - np, kNodeCap)): a lane not tagged adds a zero mass
-// (with r2 replaced by h2, since such a lane may sit on the node), and
-// entries inside the softening length are repaired as in sweep_full.
+// (at max(r, h), since such a lane may sit on the node), and entries inside
+// the softening length are repaired as in sweep_full.
 template <bool PERIODIC, bool TREEPM, bool VARH>
 __device__ __forceinline__ void sweep_partial(const GroupShared &sh, int np, unsigned lanebit, float xox, float xoy,
                                               float xoz, float hi, const WalkConsts &k, float &ax, float &ay,
@@ -569,6 +606,31 @@ __device__ __forceinline__ void sweep_partial(const GroupShared &sh, int np, uns
                 pair_term<TREEPM>(rx, ry, rz, mine ? r2 : 1.0f, mine ? E.w : 0.0f, k, ax, ay, az, ph);
             if (PERIODIC && !TREEPM)
                 ewald_term(rx, ry, rz, mine ? E.w : 0.0f, k, ax, ay, az, ph);
+        }
+        return;
+    }
+    if (!VARH) {
+        float rmin = __int_as_float(0x7f800000);
+#pragma unroll 2
+        for (int e = e0; e < kNodeCap; e++) {
+            const float4 E = sh.nsrc[e];
+            const bool mine = (sh.nmask[e] & lanebit) != 0u;
+            const float rx = E.x - xox, ry = E.y - xoy, rz = E.z - xoz;
+            const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+            rmin = fminf(rmin, r2);
+            cnt += mine ? 1u : 0u;
+            newton_term(rx, ry, rz, fmaxf(r2, k.h2), mine ? E.w : 0.0f, ax, ay, az, ph);
+        }
+        if (__any_sync(0xffffffffu, rmin < k.h2)) {
+            for (int e = e0; e < kNodeCap; e++) {
+                const float4 E = sh.nsrc[e];
+                const float rx = E.x - xox, ry = E.y - xoy, rz = E.z - xoz;
+                const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+                if ((sh.nmask[e] & lanebit) && r2 < k.h2) {
+                    newton_term(rx, ry, rz, k.h2, -E.w, ax, ay, az, ph);
+                    pair_term<false>(rx, ry, rz, r2, E.w, k, ax, ay, az, ph);
+                }
+            }
         }
         return;
     }
