@@ -38,14 +38,18 @@ import workloads as W  # noqa: E402
 METRIC = "active-particle forces/s and interactions/s at p99 rel. force err <=5e-3; p50/p99 latency"
 FLOPS_PER_INTERACTION = 20  # monopole pair term with potential, FP32
 
-# DRAM bytes (read + write) of one k_walk_group launch of the headline step,
-# from the ncu capture summarised in profiles/k_walk_group_hernquist_2p20_relative.md,
-# valid only for the walk source it was taken from
-WALK_TRAFFIC = {"bytes": 98.656512e6 + 12.715264e6,
-                "walk_cu_sha256": "788332476922d758fe050b7bd71c46f0276af500f49992b55c4a4764e492aaf9"}
+# From the ncu capture of one k_walk_group launch of the headline step
+# summarised in profiles/k_walk_group_hernquist_2p20_relative.md, valid only
+# for the walk source it was taken from: DRAM bytes (read + write), and the
+# FP32 flops the kernel executed per cycle over the whole GPU (fadd + fmul +
+# 2 ffma thread instructions) against the FP32 peak per cycle (SMs x 128 x 2)
+WALK_TRAFFIC = {"bytes": 98.881024e6 + 12.670976e6,
+                "fp32_flops_per_cycle": 1765.031176 + 1458.107789 + 2 * 1421.878237,
+                "walk_cu_sha256": "78f3594bb7832061014dd0ac7393cb00ab9aa17a353742d4a9f22414de263445"}
 
 
-def walk_traffic():
+def walk_capture():
+    """The capture's figures if walk.cu is the captured source, else None."""
     import hashlib
 
     path = os.path.join(ROOT, "paper_1909_04667_gb300", "csrc", "walk.cu")
@@ -53,7 +57,7 @@ def walk_traffic():
         digest = hashlib.sha256(open(path, "rb").read()).hexdigest()
     except OSError:
         return None
-    return WALK_TRAFFIC["bytes"] if digest == WALK_TRAFFIC["walk_cu_sha256"] else None
+    return WALK_TRAFFIC if digest == WALK_TRAFFIC["walk_cu_sha256"] else None
 
 # ------------------------------------------------------------------ configs
 HERNQUIST = dict(n=1 << 20, seed=W.CONFIG_SEEDS[2], h=0.005, G=1.0, bucket=8, theta=0.5, alpha=0.0025)
@@ -249,6 +253,7 @@ def run_ours(args, rank, world):
     pk, pk_kind = peaks()
     sm_max = pk.get("sm_max_mhz", 2070.0)
     fp32_peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+    cap = walk_capture()
     achieved = interactions * FLOPS_PER_INTERACTION / (walk_ms * 1e-3) / 1e12
     n_levels = None
     clocks = clk.summary()
@@ -268,7 +273,10 @@ def run_ours(args, rank, world):
         e2e={"value": world * n / (e2e_ms * 1e-3), "unit": "forces/s", "ms_per_step": e2e_ms,
              "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         roofline={"bound": "alu", "kernel": "k_walk_group (relative criterion)", "achieved": achieved,
-                  "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": walk_traffic(),
+                  "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                  "traffic": cap["bytes"] if cap else None,
+                  "executed_fp32_frac_ncu": (cap["fp32_flops_per_cycle"] / (props.multi_processor_count * 128 * 2)
+                                             if cap else None),
                   "frac_at_run_clock": (achieved / (fp32_peak * clocks["sm_mhz"] / sm_max)
                                         if clocks.get("sm_mhz") else None),
                   "peak_kind": "FP32 CUDA-core peak = SMs x 128 x 2 x %.0f MHz (%s sm_max)" % (sm_max, pk_kind),

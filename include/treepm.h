@@ -22,10 +22,13 @@
  * - Pointers may be host or device memory; the library tells them apart with
  *   cudaPointerGetAttributes.  Device pointers must belong to the context's
  *   device.  With host pointers a call copies inputs in, runs, copies results
- *   out and synchronises the stream before returning; with device pointers a
- *   call is stream-ordered on `stream` (a cudaStream_t, NULL = legacy default
- *   stream) and returns once the work is enqueued (the tree build itself
- *   synchronises `stream` once, to read the node count).
+ *   out and synchronises the stream before returning, except that the tree
+ *   build reads page-locked host inputs (cudaHostAlloc, cudaHostRegister) in
+ *   place through their mapped device address (the CPU-GPU link is coherent
+ *   on this platform); with device pointers a call is stream-ordered on
+ *   `stream` (a cudaStream_t, NULL = legacy default stream) and returns once
+ *   the work is enqueued (the tree build itself synchronises `stream` once,
+ *   to read the node count, after its last read of the inputs).
  * - The caller owns every buffer it passes.  Inputs are read during the call
  *   (host) or before the stream reaches the end of the call's work (device)
  *   and may be reused afterwards.  The library owns the resident trees and

@@ -81,6 +81,29 @@ bool is_device_ptr(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Address through which kernels reach p: device or managed memory as it is;
+// page-locked host memory through its mapped device address (kernels read it
+// in place across the coherent CPU-GPU link, no staging copy); nullptr for
+// pageable host memory.  Used for the tree build's inputs, each read once in
+// a coalesced stream; the force call stages its host arguments (per-group
+// reads of a_old and scattered writes of results in place cost more than one
+// bulk copy each way).
+const void *device_view(const void *p) {
+    if (!p)
+        return nullptr;
+    cudaPointerAttributes a{};
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)
+        return p;
+    if (a.type == cudaMemoryTypeHost && a.devicePointer)
+        return a.devicePointer;
+    return nullptr;
+}
+
 System *find(Ctx *c, tpm_sys id) {
     std::lock_guard<std::mutex> lk(c->mu);
     auto it = c->systems.find(id);
@@ -295,10 +318,10 @@ int build_entry(tpm_ctx *h, const double *pos, const float *mass, const float *h
     s->bp = *p;
     AllocSet stage;
     stage.ctx = c;
-    const double *dpos = pos;
-    const float *dmass = mass;
+    const double *dpos = static_cast<const double *>(device_view(pos));
+    const float *dmass = static_cast<const float *>(device_view(mass));
     int rc = TPM_OK;
-    if (!is_device_ptr(pos)) {
+    if (!dpos) {
         double *d;
         rc = stage.get(&d, 3 * n, st);
         if (rc == TPM_OK && cudaMemcpyAsync(d, pos, 3 * n * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess) {
@@ -307,7 +330,7 @@ int build_entry(tpm_ctx *h, const double *pos, const float *mass, const float *h
         }
         dpos = d;
     }
-    if (rc == TPM_OK && !is_device_ptr(mass)) {
+    if (rc == TPM_OK && !dmass) {
         float *d;
         rc = stage.get(&d, n, st);
         if (rc == TPM_OK && cudaMemcpyAsync(d, mass, n * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess) {
@@ -316,8 +339,8 @@ int build_entry(tpm_ctx *h, const double *pos, const float *mass, const float *h
         }
         dmass = d;
     }
-    const float *dsoft = hsoft;
-    if (rc == TPM_OK && hsoft && !is_device_ptr(hsoft)) {
+    const float *dsoft = static_cast<const float *>(device_view(hsoft));
+    if (rc == TPM_OK && hsoft && !dsoft) {
         float *d;
         rc = stage.get(&d, n, st);
         if (rc == TPM_OK && cudaMemcpyAsync(d, hsoft, n * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess) {

@@ -180,6 +180,50 @@ def test_active_subset_in_caller_order(oracle_mod, tpm, ctx, torch_dev):
     s.release()
 
 
+def test_page_locked_host_buffers(tpm, ctx, torch_dev):
+    """The tree build reads page-locked host inputs in place (no staging
+    copy), the force call stages page-locked and pageable host arguments
+    alike; the tree and the forces equal those of device buffers bit for bit,
+    for the build inputs, the active ids, a_old and every output."""
+    import torch
+
+    n = 20000
+    pos, mass = W.hernquist(n, 21)
+    bp = tpm.BuildParams(G=1.0, h=0.005, shift=tuple(W.root_shift(21)), leaf_bucket=8)
+    ids = np.random.default_rng(5).choice(n, 4321, replace=False).astype(np.uint32)
+    pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory()
+    s_dev = ctx.build_tree(to_dev(pos, torch_dev), to_dev(mass, torch_dev), bp)
+    s_pin = ctx.build_tree(pin(pos), pin(mass), bp)
+    s_pag = ctx.build_tree(pos, mass, bp)
+    ex = [s.tree_export() for s in (s_dev, s_pin, s_pag)]
+    for k in ("key", "perm", "level", "prefix", "first", "count", "skip", "mass", "com", "xtree"):
+        np.testing.assert_array_equal(ex[1][k], ex[0][k], err_msg=k)
+        np.testing.assert_array_equal(ex[2][k], ex[0][k], err_msg=k)
+    a0, _, _ = s_dev.compute_forces(active_ids=to_dev(ids, torch_dev), fp=tpm.ForceParams(theta=0.5))
+    a_old = np.linalg.norm(a0.cpu().numpy(), axis=1).astype(np.float32)
+    fp = tpm.ForceParams(crit=tpm.CRIT_RELATIVE, alpha=0.0025)
+    acc_d, pot_d, nint_d = s_dev.compute_forces(active_ids=to_dev(ids, torch_dev), a_old=to_dev(a_old, torch_dev),
+                                                fp=fp)
+    ref = (acc_d.cpu().numpy(), pot_d.cpu().numpy(), nint_d.cpu().numpy().astype(np.uint32))
+    acc_p = torch.zeros((len(ids), 3), dtype=torch.float32).pin_memory()
+    pot_p = torch.zeros(len(ids), dtype=torch.float32).pin_memory()
+    nint_p = torch.zeros(len(ids), dtype=torch.int32).pin_memory()
+    s_pin.compute_forces(active_ids=pin(ids.view(np.int32)), a_old=pin(a_old), fp=fp, acc=acc_p, pot=pot_p,
+                         n_int=nint_p)
+    np.testing.assert_array_equal(acc_p.numpy(), ref[0])
+    np.testing.assert_array_equal(pot_p.numpy(), ref[1])
+    np.testing.assert_array_equal(nint_p.numpy().astype(np.uint32), ref[2])
+    acc_h = np.zeros((len(ids), 3), np.float32)
+    pot_h = np.zeros(len(ids), np.float32)
+    nint_h = np.zeros(len(ids), np.uint32)
+    s_pag.compute_forces(active_ids=ids, a_old=a_old, fp=fp, acc=acc_h, pot=pot_h, n_int=nint_h)
+    np.testing.assert_array_equal(acc_h, ref[0])
+    np.testing.assert_array_equal(pot_h, ref[1])
+    np.testing.assert_array_equal(nint_h, ref[2])
+    for s in (s_dev, s_pin, s_pag):
+        s.release()
+
+
 def test_walk_deterministic(tpm, ctx, torch_dev):
     pos, mass = W.hernquist(30000, 3)
     bp = tpm.BuildParams(G=1.0, h=0.005, shift=tuple(W.root_shift(3)), leaf_bucket=8)
