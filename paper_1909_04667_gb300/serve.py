@@ -55,6 +55,15 @@ class _Resident:
     aold: object          # torch float32 (n,), on the device
     aold_valid: object    # numpy bool (n,), on the host: which particles have an |a|
     inflight: int = 0
+    n_valid: int = 0      # particles with an |a| (once all have one, no per-id checks)
+
+    def all_valid(self, ids) -> bool:
+        return self.n_valid == len(self.aold_valid) or bool(self.aold_valid[ids].all())
+
+    def mark_valid(self, ids):
+        if self.n_valid < len(self.aold_valid):
+            self.aold_valid[ids] = True
+            self.n_valid = int(np.count_nonzero(self.aold_valid))
 
 
 @dataclass
@@ -64,7 +73,8 @@ class _Round:
     pot: object
     nint: object
     offsets: np.ndarray
-    event: object
+    event: object          # results copied to the host
+    done: object = None    # and the |a| bookkeeping after them
     sids: list = field(default_factory=list)
 
 
@@ -100,6 +110,12 @@ class ForceServer:
         self.acc_h = torch.empty((m, 3), dtype=torch.float32).pin_memory()
         self.pot_h = torch.empty(m, dtype=torch.float32).pin_memory()
         self.nint_h = torch.empty(m, dtype=torch.int32).pin_memory()
+        # and their device counterparts (the walk stream orders the rounds)
+        with torch.cuda.stream(self.walk_stream):
+            self.ids_d = torch.empty(m, dtype=torch.int32, device=self.dev)
+            self.acc_d = torch.empty((m, 3), dtype=torch.float32, device=self.dev)
+            self.pot_d = torch.empty(m, dtype=torch.float32, device=self.dev)
+            self.nint_d = torch.empty(m, dtype=torch.int32, device=self.dev)
 
     def close(self):
         for r in self.resident.values():
@@ -146,11 +162,14 @@ class ForceServer:
     def _params_for(self, res: _Resident, ids) -> ForceParams:
         if self.policy == "bh":
             return ForceParams(crit=CRIT_BH, theta=self.theta)
-        if self.policy == "relative" or (self.policy == "adaptive" and bool(res.aold_valid[ids].all())):
+        if self.policy == "relative" or (self.policy == "adaptive" and res.all_valid(ids)):
             return ForceParams(crit=CRIT_RELATIVE, alpha=self.alpha)
         return ForceParams(crit=CRIT_BH, theta=self.theta)
 
     def _launch(self, reqs) -> _Round:
+        """Enqueues one round: the walk and the copies of its results come
+        first (the round is complete when they are), the bookkeeping of |a|
+        for later criteria after them, overlapping the walk."""
         torch = self.torch
         self.walk_stream.wait_stream(self.build_stream)
         with torch.cuda.stream(self.walk_stream):
@@ -160,40 +179,43 @@ class ForceServer:
             ids_np = self.ids_h.numpy()
             for k, r in enumerate(reqs):
                 ids_np[off[k]:off[k + 1]] = r.ids
-            ids_d = self.ids_h[:n].to(self.dev, non_blocking=True)
-            systems, params, aolds = [], [], []
+            ids_d = self.ids_d[:n]
+            ids_d.copy_(self.ids_h[:n], non_blocking=True)
+            systems, params, aolds, parts = [], [], [], []
             for k, r in enumerate(reqs):
                 res = self.resident[r.sid]
                 res.inflight += 1
-                part = ids_d[off[k]:off[k + 1]].long()
+                part = ids_d[off[k]:off[k + 1]]
                 fp = self._params_for(res, r.ids)
                 r.criterion = fp.crit
                 systems.append(res.system)
                 params.append(fp)
-                aolds.append(res.aold[part])
-            a_old = torch.cat(aolds).contiguous()
-            acc = torch.empty((n, 3), dtype=torch.float32, device=self.dev)
-            pot = torch.empty(n, dtype=torch.float32, device=self.dev)
-            nint = torch.empty(n, dtype=torch.int32, device=self.dev)
+                parts.append(part)
+                aolds.append(torch.index_select(res.aold, 0, part))
+            a_old = aolds[0] if len(aolds) == 1 else torch.cat(aolds)
+            acc, pot, nint = self.acc_d[:n], self.pot_d[:n], self.nint_d[:n]
             self.plan.compute_forces_batch(systems, off, params, ids_d, acc, a_old=a_old, pot=pot, n_int=nint,
                                            stream=self.walk_stream.cuda_stream)
-            # |a| of this evaluation becomes a_old of later ones
-            amag = torch.linalg.vector_norm(acc, dim=1)
-            for k, r in enumerate(reqs):
-                res = self.resident[r.sid]
-                part = ids_d[off[k]:off[k + 1]].long()
-                res.aold[part] = amag[off[k]:off[k + 1]]
-                res.aold_valid[r.ids] = True
             self.acc_h[:n].copy_(acc, non_blocking=True)
             self.pot_h[:n].copy_(pot, non_blocking=True)
             self.nint_h[:n].copy_(nint, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(self.walk_stream)
-        return _Round(reqs, self.acc_h[:n], self.pot_h[:n], self.nint_h[:n], off, ev, [r.sid for r in reqs])
+            # |a| of this evaluation becomes a_old of later ones (stream-ordered
+            # before any later round)
+            amag = torch.linalg.vector_norm(acc, dim=1)
+            for k, r in enumerate(reqs):
+                res = self.resident[r.sid]
+                res.aold.index_copy_(0, parts[k].long(), amag[off[k]:off[k + 1]])
+                res.mark_valid(r.ids)
+            done = torch.cuda.Event()
+            done.record(self.walk_stream)
+        return _Round(reqs, self.acc_h[:n], self.pot_h[:n], self.nint_h[:n], off, ev, done, [r.sid for r in reqs])
 
     def _complete(self, rnd: _Round, t0: float):
         rnd.event.synchronize()
         now = time.perf_counter() - t0
+        rnd.done.synchronize()  # a system the round used may be evicted after this
         acc, pot, nint = rnd.acc.numpy(), rnd.pot.numpy(), rnd.nint.numpy()
         for k, r in enumerate(rnd.reqs):
             lo, hi = rnd.offsets[k], rnd.offsets[k + 1]
@@ -280,11 +302,12 @@ def serve_per_request(ctx: Context, source, requests, theta: float = 0.5, alpha:
                         raise
                     _, (old, _, _) = resident.popitem(last=False)
                     old.release()
-            resident[r.sid] = (system, torch.zeros(system.n, device=dev), np.zeros(system.n, dtype=bool))
+            resident[r.sid] = (system, torch.zeros(system.n, device=dev),
+                               _Resident(None, None, np.zeros(system.n, dtype=bool)))
         system, aold, valid = resident[r.sid]
         ids_d = torch.from_numpy(r.ids.astype(np.int32)).to(dev)
         part = ids_d.long()
-        if policy == "bh" or (policy == "adaptive" and not bool(valid[r.ids].all())):
+        if policy == "bh" or (policy == "adaptive" and not valid.all_valid(r.ids)):
             fp = ForceParams(crit=CRIT_BH, theta=theta)
         else:
             fp = ForceParams(crit=CRIT_RELATIVE, alpha=alpha)
@@ -300,7 +323,7 @@ def serve_per_request(ctx: Context, source, requests, theta: float = 0.5, alpha:
                     raise
                 resident.pop(victim)[0].release()
         aold[part] = torch.linalg.vector_norm(acc, dim=1)
-        valid[r.ids] = True
+        valid.mark_valid(r.ids)
         a_h, p_h, n_h = acc.cpu().numpy(), pot.cpu().numpy(), nint.cpu().numpy()
         if keep_results:
             r.acc, r.pot, r.n_int = a_h, p_h, n_h
