@@ -36,11 +36,11 @@ if ROOT not in sys.path:
 import workloads as W  # noqa: E402
 
 METRIC = "active-particle forces/s and interactions/s at p99 rel. force err <=5e-3; p50/p99 latency"
-FLOPS_PER_INTERACTION = 20  # monopole pair term with potential, FP32
+FLOPS_PER_INTERACTION = 20  # monopole pair term with potential, FP32: offset 3, r^2 5, rsqrt 1, products 3, acc 6, pot 1
 
-# From the ncu capture of one k_walk_group launch of the headline step
-# summarised in profiles/k_walk_group_hernquist_2p20_relative.md, valid only
-# for the walk source it was taken from: DRAM bytes (read + write), and the
+# From the ncu capture of one k_walk_group launch of the headline step (its
+# summary is under profiles/), valid only for the walk source it was taken
+# from: DRAM bytes (read + write), and the
 # FP32 flops the kernel executed per cycle over the whole GPU (fadd + fmul +
 # 2 ffma thread instructions) against the FP32 peak per cycle (SMs x 128 x 2)
 WALK_TRAFFIC = {"bytes": 98.881024e6 + 12.670976e6,
