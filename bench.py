@@ -668,6 +668,49 @@ def run_isolated(ctx, tpm, torch, dev, stream, flush, pos_d, mass_d, steps):
             "pm_ms": float(r[1]), "walk_interp_ms": float(r[2]), "interactions_per_particle": inter / n}
 
 
+def run_profile(name):
+    """One workload alone, for a profiler's launch list: a geometric first
+    force, then three relative-criterion steps of `periodic` (the 128^3 TreePM
+    box: build, mesh, short-range walk with interpolation) or `hernquist` (the
+    headline 2^20 set: build and walk).  Prints the mean step times."""
+    import torch
+
+    import paper_1909_04667_gb300 as tpm
+
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    ctx = tpm.Context(0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    if name == "periodic":
+        out = run_periodic(ctx, tpm, torch, dev, stream, flush, 1)
+    else:
+        cfg = HERNQUIST
+        pos, mass = hernquist_inputs()
+        pos_d, mass_d = torch.from_numpy(pos).to(dev), torch.from_numpy(mass).to(dev)
+        bp = lambda k: tpm.BuildParams(G=cfg["G"], h=cfg["h"], shift=root_shift(k, 2), leaf_bucket=cfg["bucket"])
+        s = ctx.build_tree(pos_d, mass_d, bp(0))
+        acc, pot, nint = s.compute_forces(fp=tpm.ForceParams(crit=tpm.CRIT_BH, theta=cfg["theta"]))
+        s.release()
+        a_old = torch.linalg.vector_norm(acc, dim=1).contiguous()
+        fp = tpm.ForceParams(crit=tpm.CRIT_RELATIVE, alpha=cfg["alpha"])
+        res = []
+        for k in range(3):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            l2_flush(flush)
+            ev[0].record(stream)
+            sy = ctx.build_tree(pos_d, mass_d, bp(1000 + k))
+            ev[1].record(stream)
+            sy.compute_forces(a_old=a_old, fp=fp, acc=acc, pot=pot, n_int=nint)
+            ev[2].record(stream)
+            sy.release()
+            torch.cuda.synchronize()
+            res.append([ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])])
+        r = np.array(res).mean(0)
+        out = {"workload": "hernquist_n2^20_relative_alpha0.0025", "build_ms": float(r[0]), "walk_ms": float(r[1])}
+    ctx.close()
+    print(json.dumps(out))
+
+
 # ------------------------------------------------------------------ CPU oracle
 def run_oracle_sample(sample: int, nthreads: int = 0):
     """The FP64 oracle (as it stands) on a bounded sample of the headline
@@ -748,6 +791,8 @@ def main():
     ap.add_argument("--no-isolated", action="store_true", help="skip the open-boundary TreePM measurement")
     ap.add_argument("--no-ewald", action="store_true", help="skip the periodic Ewald-tree measurement")
     ap.add_argument("--no-species", action="store_true", help="skip the two-species softening measurement")
+    ap.add_argument("--profile-workload", choices=["periodic", "hernquist"], default=None,
+                    help="run one workload alone (first force + three steps) for a profiler, print its step times")
     ap.add_argument("--serving-requests", type=int, default=None,
                     help="requests of the serving measurement (default 2000; 10000 is the full stream)")
     args = ap.parse_args()
@@ -757,6 +802,9 @@ def main():
         SERVING["n_requests"] = args.serving_requests
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
+    if args.profile_workload:
+        run_profile(args.profile_workload)
+        return
     if args.impl == "reference":
         out = run_reference(args, rank, world)
         if out is not None:

@@ -8,15 +8,19 @@
 //       W(k) = prod_a sinc^2(k_a dx / 2) (one window for assignment, one for
 //       interpolation), with the k = 0 mode removed (the mean density does not
 //       source the potential) and the inverse-FFT normalisation folded in.
-//       The same pass also forms the three force spectra: the 4-point
-//       finite difference dPhi/dx ~ [4/3 (Phi_{+1} - Phi_{-1})/2 -
-//       1/3 (Phi_{+2} - Phi_{-2})/4] / dx is a circular convolution on the
-//       periodic mesh, so it equals multiplication by its transfer function
-//       i [4/3 sin(theta) - 1/6 sin(2 theta)] / dx, theta = 2 pi n / N.
-//       Applying it in k-space gives the finite-difference force mesh without
-//       the FP32 cancellation of differencing a smooth potential.
-//   --  one batched complex-to-real FFT -> potential and 3 force meshes
-//   K8  per active particle: CIC interpolation of force and potential
+//   --  complex-to-real FFT -> the potential mesh (64 MiB at 256^3: it stays
+//       in the 129 MB L2 for the interpolation)
+//   K8  per active particle: the 4-point finite difference
+//       dPhi/dx ~ [2/3 (Phi_{+1} - Phi_{-1}) - 1/12 (Phi_{+2} - Phi_{-2})] / dx
+//       at each of the 8 CIC mesh points around the particle (circular on the
+//       mesh), CIC-interpolated, and the CIC-interpolated potential.  The
+//       difference is a circular convolution, so forming it in k-space (its
+//       transfer function i [4/3 sin(theta) - 1/6 sin(2 theta)] / dx) would
+//       give the same force meshes; differencing the one potential mesh here
+//       saves three inverse transforms and four mesh passes, at the price of
+//       FP32 cancellation in differences of a smooth potential (a relative
+//       error near 1e-5 of the mesh force at the box scale, far below the
+//       method's own).
 //
 // Open boundaries (Sec. 3.3: zero padding and the Green's function of
 // isolated boundaries).  The mesh covers a cube of the tree root's side
@@ -28,10 +32,8 @@
 // convolution equals the open one on the physical region.  The transform of
 // the kernel (in mesh units, per padded size and split scale in cells) is
 // computed once per context; K7 multiplies by it (scaled by G / dx) instead
-// of the periodic Green's function, keeps k = 0, and forms the same
-// finite-difference force spectra on the padded mesh, which equal the
-// real-space differences wherever the stencil stays inside the physical
-// region.
+// of the periodic Green's function and keeps k = 0; K8 differences the padded
+// potential mesh circularly, like the periodic one.
 #include <map>
 
 #include "tpm_internal.cuh"
@@ -95,39 +97,46 @@ __global__ void k_cic_deposit(const double *__restrict__ pos, const float *__res
 // ~4e-7, i.e. a relative error of ~3e-5 at the fundamental mode of a 256^3 mesh.
 __device__ __forceinline__ float sinc_f(float x) { return x == 0.0f ? 1.0f : sinf(x) / x; }
 
-// K7 on the r2c half spectrum [ng][ng][ng/2+1]: spec[0] (in place) becomes the
-// potential spectrum, spec[1..3] the x, y, z force spectra.
-__global__ void k_green(cufftComplex *__restrict__ spec, int64_t nspec, int ng, float kfund, float dx, float rs2,
-                        float pref) {
+// Per-axis factors of the Green's functions for mesh index i of an m-point
+// axis (frequency n = i or i - m): tab[i] = (kfund n)^2 and tab[m + i] =
+// sinc^2(theta / 2) with theta = 2 pi n / m (the CIC window of one axis).
+__device__ __forceinline__ void green_axis_table(float *tab, int m, float kfund) {
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+        const int n = i < m / 2 ? i : i - m;
+        const float ka = kfund * (float)n;
+        tab[i] = ka * ka;
+        const float sc = sinc_f((float)kPi * (float)n / (float)m);
+        tab[m + i] = sc * sc;
+    }
+    __syncthreads();
+}
+
+constexpr int kGreenThreads = 256;
+
+// K7 on the r2c half spectrum [ng][ng][ng/2+1], in place: the potential
+// spectrum.  A warp takes whole rows (ix, iy) and walks iz, so no index needs
+// a division; the per-axis factors come from a table in shared memory, filled
+// once per block.
+__global__ void __launch_bounds__(kGreenThreads)
+    k_green(cufftComplex *__restrict__ spec, int ng, float kfund, float rs2, float pref) {
+    extern __shared__ float tab[];
+    green_axis_table(tab, ng, kfund);
     const int nzh = ng / 2 + 1;
-    const float inv_dx = 1.0f / dx;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nspec;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int iz = (int)(e % nzh);
-        const int iy = (int)((e / nzh) % ng);
-        const int ix = (int)(e / ((int64_t)nzh * ng));
-        const int n3[3] = {ix < ng / 2 ? ix : ix - ng, iy < ng / 2 ? iy : iy - ng, iz};
-        float k2 = 0.0f, w = 1.0f, d[3];
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            const float ka = kfund * n3[a];
-            k2 = fmaf(ka, ka, k2);
-            w *= sinc_f(0.5f * ka * dx);
-            const float th = 2.0f * (float)n3[a] / (float)ng;  // theta / pi
-            d[a] = (4.0f / 3.0f * sinpif(th) - 1.0f / 6.0f * sinpif(2.0f * th)) * inv_dx;
+    const int64_t rows = (int64_t)ng * ng;
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int64_t r = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); r < rows; r += (int64_t)gridDim.x * wpb) {
+        const int ix = (int)(r / ng), iy = (int)(r - (int64_t)ix * ng);
+        const float kxy = tab[ix] + tab[iy], wxy = tab[ng + ix] * tab[ng + iy];
+        cufftComplex *__restrict__ row = spec + r * nzh;
+        for (int iz = lane; iz < nzh; iz += 32) {
+            const float k2 = kxy + tab[iz];
+            const float w2 = wxy * tab[ng + iz];  // W(k) = prod_a sinc^2(k_a dx / 2)
+            float g = 0.0f;
+            if (k2 > 0.0f)
+                g = pref * __expf(-k2 * rs2) / (k2 * w2 * w2);
+            const cufftComplex v = row[iz];
+            row[iz] = make_float2(v.x * g, v.y * g);
         }
-        cufftComplex v = spec[e];
-        float g = 0.0f;
-        if (k2 > 0.0f) {
-            const float w2 = w * w;  // sinc^2 per axis
-            g = pref * __expf(-k2 * rs2) / (k2 * w2 * w2);
-        }
-        const float re = v.x * g, im = v.y * g;
-        spec[e] = make_float2(re, im);
-        // force = -grad Phi: multiply by -i d
-#pragma unroll
-        for (int a = 0; a < 3; a++)
-            spec[(a + 1) * nspec + e] = make_float2(d[a] * im, -d[a] * re);
     }
 }
 
@@ -178,41 +187,100 @@ __global__ void k_real_part(const cufftComplex *__restrict__ spec, int64_t nspec
         out[e] = spec[e].x;  // the kernel is real and even: its transform is real
 }
 
-// K7 for open boundaries on the padded half spectrum [n2][n2][n2/2+1]:
-// Phi_k = m_k g_k / W(k)^2 (pref = G / dx / n2^3 scales the mesh-unit kernel
-// transform and folds in the inverse-FFT normalisation), then the force
-// spectra of the 4-point difference as in k_green.
-__global__ void k_green_iso(cufftComplex *__restrict__ spec, int64_t nspec, int n2, const float *__restrict__ gk,
-                            float dx, float pref) {
+// K7 for open boundaries on the padded half spectrum [n2][n2][n2/2+1], in
+// place: Phi_k = m_k g_k / W(k)^2 (pref = G / dx / n2^3 scales the mesh-unit
+// kernel transform and folds in the inverse-FFT normalisation); rows as in
+// k_green.
+__global__ void __launch_bounds__(kGreenThreads)
+    k_green_iso(cufftComplex *__restrict__ spec, int n2, const float *__restrict__ gk, float pref) {
+    extern __shared__ float tab[];
+    green_axis_table(tab, n2, 0.0f);
     const int nzh = n2 / 2 + 1;
-    const float inv_dx = 1.0f / dx;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nspec;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int iz = (int)(e % nzh);
-        const int iy = (int)((e / nzh) % n2);
-        const int ix = (int)(e / ((int64_t)nzh * n2));
-        const int n3[3] = {ix < n2 / 2 ? ix : ix - n2, iy < n2 / 2 ? iy : iy - n2, iz};
-        float w = 1.0f, d[3];
-#pragma unroll
-        for (int a = 0; a < 3; a++) {
-            const float th = 2.0f * (float)n3[a] / (float)n2;  // theta / pi
-            w *= sinc_f(0.5f * (float)kPi * th);                // sinc(k_a dx / 2)
-            d[a] = (4.0f / 3.0f * sinpif(th) - 1.0f / 6.0f * sinpif(2.0f * th)) * inv_dx;
+    const int64_t rows = (int64_t)n2 * n2;
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int64_t r = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); r < rows; r += (int64_t)gridDim.x * wpb) {
+        const int ix = (int)(r / n2), iy = (int)(r - (int64_t)ix * n2);
+        const float wxy = tab[n2 + ix] * tab[n2 + iy];
+        cufftComplex *__restrict__ row = spec + r * nzh;
+        const float *__restrict__ grow = gk + r * nzh;
+        for (int iz = lane; iz < nzh; iz += 32) {
+            const float w2 = wxy * tab[n2 + iz];
+            const float g = pref * grow[iz] / (w2 * w2);
+            const cufftComplex v = row[iz];
+            row[iz] = make_float2(v.x * g, v.y * g);
         }
-        const float w2 = w * w;
-        const float g = pref * gk[e] / (w2 * w2);
-        const cufftComplex v = spec[e];
-        const float re = v.x * g, im = v.y * g;
-        spec[e] = make_float2(re, im);
-#pragma unroll
-        for (int a = 0; a < 3; a++)
-            spec[(a + 1) * nspec + e] = make_float2(d[a] * im, -d[a] * re);
     }
 }
 
-// K8 for open boundaries: CIC interpolation from the padded meshes.
-__global__ void k_pm_interp_iso(const float *__restrict__ mesh, int64_t ncell, int n2, double cx, double cy,
-                                double cz, double cells_per_len, const double *__restrict__ pos,
+__device__ __forceinline__ int wrapi(int i, int ng) {
+    i %= ng;
+    return i < 0 ? i + ng : i;
+}
+
+// K8 core: potential and force at a particle whose CIC cell starts at mesh
+// point i0 with fractions f, from the m^3 potential mesh, indices circular.
+// The force at each of the 8 CIC points is minus the 4-point difference of
+// the potential along each axis.  The six mesh values of a line along an axis
+// through two neighbouring CIC points give both points' differences; the 8
+// CIC points' own values come from the x lines and are kept for the y and z
+// lines (56 loads, all within 3 cells of the particle).
+__device__ __forceinline__ void pm_interp_point(const float *__restrict__ phi, int m, const int i0[3],
+                                                const float f[3], float inv_dx, float &ph, float &gx, float &gy,
+                                                float &gz) {
+    int x[6], y[6], z[6];  // circular indices i0 - 2 .. i0 + 3 per axis
+#pragma unroll
+    for (int t = 0; t < 6; t++) {
+        x[t] = wrapi(i0[0] - 2 + t, m);
+        y[t] = wrapi(i0[1] - 2 + t, m);
+        z[t] = wrapi(i0[2] - 2 + t, m);
+    }
+    const float wx[2] = {1.0f - f[0], f[0]}, wy[2] = {1.0f - f[1], f[1]}, wz[2] = {1.0f - f[2], f[2]};
+    const float c1 = 2.0f / 3.0f * inv_dx, c2 = 1.0f / 12.0f * inv_dx;
+    auto at = [&](int a, int b, int c) { return __ldg(&phi[((size_t)a * m + b) * m + c]); };
+    float core[2][2][2];  // the CIC points' potentials [dx][dy][dz]
+    ph = gx = gy = gz = 0.0f;
+#pragma unroll
+    for (int u = 0; u < 2; u++)
+#pragma unroll
+        for (int v = 0; v < 2; v++) {  // x line through (y[2 + u], z[2 + v])
+            float l[6];
+#pragma unroll
+            for (int t = 0; t < 6; t++)
+                l[t] = at(x[t], y[2 + u], z[2 + v]);
+#pragma unroll
+            for (int d = 0; d < 2; d++) {
+                core[d][u][v] = l[2 + d];
+                const float w = wx[d] * wy[u] * wz[v];
+                ph = fmaf(w, l[2 + d], ph);
+                gx = fmaf(w, c2 * (l[4 + d] - l[d]) - c1 * (l[3 + d] - l[1 + d]), gx);
+            }
+        }
+#pragma unroll
+    for (int u = 0; u < 2; u++)
+#pragma unroll
+        for (int v = 0; v < 2; v++) {
+            {  // y line through (x[2 + u], z[2 + v])
+                const float l[6] = {at(x[2 + u], y[0], z[2 + v]), at(x[2 + u], y[1], z[2 + v]), core[u][0][v],
+                                    core[u][1][v], at(x[2 + u], y[4], z[2 + v]), at(x[2 + u], y[5], z[2 + v])};
+#pragma unroll
+                for (int d = 0; d < 2; d++)
+                    gy = fmaf(wx[u] * wy[d] * wz[v], c2 * (l[4 + d] - l[d]) - c1 * (l[3 + d] - l[1 + d]), gy);
+            }
+            {  // z line through (x[2 + u], y[2 + v])
+                const float l[6] = {at(x[2 + u], y[2 + v], z[0]), at(x[2 + u], y[2 + v], z[1]), core[u][v][0],
+                                    core[u][v][1], at(x[2 + u], y[2 + v], z[4]), at(x[2 + u], y[2 + v], z[5])};
+#pragma unroll
+                for (int d = 0; d < 2; d++)
+                    gz = fmaf(wx[u] * wy[v] * wz[d], c2 * (l[4 + d] - l[d]) - c1 * (l[3 + d] - l[1 + d]), gz);
+            }
+        }
+}
+
+// K8 for open boundaries: from the padded potential mesh.  (Gather-bound:
+// 64 registers admit four blocks per SM, 213 vs 223 us at 72 on the 256^3
+// box.)
+__global__ void __launch_bounds__(kThreads, 4) k_pm_interp_iso(const float *__restrict__ phi, int n2, double cx, double cy, double cz,
+                                double cells_per_len, float inv_dx, const double *__restrict__ pos,
                                 const uint32_t *__restrict__ perm, const uint32_t *__restrict__ sidx,
                                 const uint32_t *__restrict__ slot, int64_t n_act, float *__restrict__ acc,
                                 float *__restrict__ pot) {
@@ -232,17 +300,8 @@ __global__ void k_pm_interp_iso(const float *__restrict__ mesh, int64_t ncell, i
         f[a] = (float)(t - fl);
         i0[a] = min(max((int)fl, 0), n2 - 2);
     }
-    float ph = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
-#pragma unroll
-    for (int c = 0; c < 8; c++) {
-        const int dx = c & 1, dy = (c >> 1) & 1, dz = (c >> 2) & 1;
-        const float w = (dx ? f[0] : 1.0f - f[0]) * (dy ? f[1] : 1.0f - f[1]) * (dz ? f[2] : 1.0f - f[2]);
-        const size_t idx = ((size_t)(i0[0] + dx) * n2 + (i0[1] + dy)) * n2 + (i0[2] + dz);
-        ph = fmaf(w, __ldg(&mesh[idx]), ph);
-        gx = fmaf(w, __ldg(&mesh[ncell + idx]), gx);
-        gy = fmaf(w, __ldg(&mesh[2 * ncell + idx]), gy);
-        gz = fmaf(w, __ldg(&mesh[3 * ncell + idx]), gz);
-    }
+    float ph, gx, gy, gz;
+    pm_interp_point(phi, n2, i0, f, inv_dx, ph, gx, gy, gz);
     acc[3 * (size_t)out] = gx;
     acc[3 * (size_t)out + 1] = gy;
     acc[3 * (size_t)out + 2] = gz;
@@ -250,13 +309,8 @@ __global__ void k_pm_interp_iso(const float *__restrict__ mesh, int64_t ncell, i
         pot[out] = ph;
 }
 
-__device__ __forceinline__ int wrapi(int i, int ng) {
-    i %= ng;
-    return i < 0 ? i + ng : i;
-}
-
-// K8: CIC interpolation of the force meshes and the potential mesh.
-__global__ void k_pm_interp(const float *__restrict__ mesh, int64_t ncell, int ng, double cells_per_len,
+// K8: from the periodic potential mesh.
+__global__ void __launch_bounds__(kThreads, 4) k_pm_interp(const float *__restrict__ phi, int ng, double cells_per_len, float inv_dx,
                             const double *__restrict__ pos, const uint32_t *__restrict__ perm,
                             const uint32_t *__restrict__ sidx, const uint32_t *__restrict__ slot, int64_t n_act,
                             float *__restrict__ acc, float *__restrict__ pot) {
@@ -275,21 +329,8 @@ __global__ void k_pm_interp(const float *__restrict__ mesh, int64_t ncell, int n
         f[a] = (float)(t - fl);
         i0[a] = wrapi((int)fl, ng);
     }
-    float ph = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
-#pragma unroll
-    for (int c = 0; c < 8; c++) {
-        const int dx = c & 1, dy = (c >> 1) & 1, dz = (c >> 2) & 1;
-        const float w = (dx ? f[0] : 1.0f - f[0]) * (dy ? f[1] : 1.0f - f[1]) * (dz ? f[2] : 1.0f - f[2]);
-        int x = i0[0] + dx, y = i0[1] + dy, z = i0[2] + dz;
-        x -= x >= ng ? ng : 0;
-        y -= y >= ng ? ng : 0;
-        z -= z >= ng ? ng : 0;
-        const size_t idx = ((size_t)x * ng + y) * ng + z;
-        ph = fmaf(w, __ldg(&mesh[idx]), ph);
-        gx = fmaf(w, __ldg(&mesh[ncell + idx]), gx);
-        gy = fmaf(w, __ldg(&mesh[2 * ncell + idx]), gy);
-        gz = fmaf(w, __ldg(&mesh[3 * ncell + idx]), gz);
-    }
+    float ph, gx, gy, gz;
+    pm_interp_point(phi, ng, i0, f, inv_dx, ph, gx, gy, gz);
     acc[3 * (size_t)out] = gx;
     acc[3 * (size_t)out + 1] = gy;
     acc[3 * (size_t)out + 2] = gz;
@@ -297,7 +338,7 @@ __global__ void k_pm_interp(const float *__restrict__ mesh, int64_t ncell, int n
         pot[out] = ph;
 }
 
-// cuFFT plans for an m^3 mesh (R2C, and C2R batched over four fields), cached.
+// cuFFT plans for an m^3 mesh (R2C and C2R), cached.
 int fft_plans_for(Ctx *c, int m, cufftHandle *fwd, cufftHandle *inv) {
     std::lock_guard<std::mutex> lk(c->mu);
     auto it = c->fft_plans.find(m);
@@ -310,10 +351,9 @@ int fft_plans_for(Ctx *c, int m, cufftHandle *fwd, cufftHandle *inv) {
         set_error("cufftPlan3d (R2C, %d^3) failed", m);
         return TPM_ECUDA;
     }
-    int dims[3] = {m, m, m};
-    if (cufftPlanMany(inv, 3, dims, nullptr, 1, 0, nullptr, 1, 0, CUFFT_C2R, 4) != CUFFT_SUCCESS) {
+    if (cufftPlan3d(inv, m, m, m, CUFFT_C2R) != CUFFT_SUCCESS) {
         cufftDestroy(*fwd);
-        set_error("cufftPlanMany (C2R x 4, %d^3) failed", m);
+        set_error("cufftPlan3d (C2R, %d^3) failed", m);
         return TPM_ECUDA;
     }
     c->fft_plans[m] = {*fwd, *inv};
@@ -385,7 +425,7 @@ int pm_solve_iso(Ctx *c, System *s, const tpm_force_params *p, cudaStream_t st) 
         s->pm_mem.release(st);
         s->phi = nullptr;
         s->pm_mem.ctx = c;
-        TPM_CHECK(s->pm_mem.get(&s->phi, 4 * ncell, st));
+        TPM_CHECK(s->pm_mem.get(&s->phi, ncell, st));
         s->pm_mesh = n2;
     }
     s->pm_n = ng;
@@ -399,7 +439,7 @@ int pm_solve_iso(Ctx *c, System *s, const tpm_force_params *p, cudaStream_t st) 
         ~Guard() { t.release(st); }
     } guard{tmp, st};
     cufftComplex *spec;
-    TPM_CHECK(tmp.get(&spec, 4 * nspec, st));
+    TPM_CHECK(tmp.get(&spec, nspec, st));
     float *rho = s->phi;
     TPM_CUDA(cudaMemsetAsync(rho, 0, ncell * sizeof(float), st));
     k_cic_deposit_iso<<<(unsigned)((s->n + kThreads - 1) / kThreads), kThreads, 0, st>>>(
@@ -411,7 +451,8 @@ int pm_solve_iso(Ctx *c, System *s, const tpm_force_params *p, cudaStream_t st) 
         return TPM_ECUDA;
     }
     const double pref = s->bp.G / dx / (double)ncell;
-    k_green_iso<<<(unsigned)(c->num_sms * 8), kThreads, 0, st>>>(spec, nspec, n2, gk, (float)dx, (float)pref);
+    k_green_iso<<<(unsigned)(c->num_sms * 8), kGreenThreads, 2 * n2 * sizeof(float), st>>>(spec, n2, gk,
+                                                                                              (float)pref);
     count_launch();
     TPM_CUDA(cudaGetLastError());
     if (cufftSetStream(inv, st) != CUFFT_SUCCESS || cufftExecC2R(inv, spec, s->phi) != CUFFT_SUCCESS) {
@@ -439,7 +480,7 @@ int pm_solve_device(Ctx *c, System *s, const tpm_force_params *p, cudaStream_t s
         s->pm_mem.release(st);
         s->phi = nullptr;
         s->pm_mem.ctx = c;
-        TPM_CHECK(s->pm_mem.get(&s->phi, 4 * ncell, st));  // potential, then x, y, z force
+        TPM_CHECK(s->pm_mem.get(&s->phi, ncell, st));
         s->pm_mesh = ng;
     }
     s->pm_n = ng;
@@ -451,8 +492,8 @@ int pm_solve_device(Ctx *c, System *s, const tpm_force_params *p, cudaStream_t s
         ~Guard() { t.release(st); }
     } guard{tmp, st};
     cufftComplex *spec;
-    TPM_CHECK(tmp.get(&spec, 4 * nspec, st));
-    float *rho = s->phi;  // the density occupies the potential slot until the inverse FFT
+    TPM_CHECK(tmp.get(&spec, nspec, st));
+    float *rho = s->phi;  // the density occupies the potential mesh until the inverse FFT
     TPM_CUDA(cudaMemsetAsync(rho, 0, ncell * sizeof(float), st));
     const double cpl = ng / box;
     k_cic_deposit<<<(unsigned)((s->n + kThreads - 1) / kThreads), kThreads, 0, st>>>(s->pos, s->mass, s->perm, s->n,
@@ -466,8 +507,8 @@ int pm_solve_device(Ctx *c, System *s, const tpm_force_params *p, cudaStream_t s
     const double dx = box / ng;
     // density = mass / dx^3; inverse FFT normalisation 1 / ng^3
     const double pref = -4.0 * kPi * s->bp.G / (dx * dx * dx) / (double)ncell;
-    k_green<<<(unsigned)(c->num_sms * 8), kThreads, 0, st>>>(spec, nspec, ng, (float)(2.0 * kPi / box), (float)dx,
-                                                            (float)(rs * rs), (float)pref);
+    k_green<<<(unsigned)(c->num_sms * 8), kGreenThreads, 2 * ng * sizeof(float), st>>>(
+        spec, ng, (float)(2.0 * kPi / box), (float)(rs * rs), (float)pref);
     count_launch();
     TPM_CUDA(cudaGetLastError());
     if (cufftSetStream(inv, st) != CUFFT_SUCCESS || cufftExecC2R(inv, spec, s->phi) != CUFFT_SUCCESS) {
@@ -485,8 +526,8 @@ int pm_interp_device(Ctx *, const System *s, const WalkRequest &r, cudaStream_t 
     if (!s->bp.periodic) {
         const int n2 = s->pm_mesh;
         k_pm_interp_iso<<<(unsigned)((r.n_act + kThreads - 1) / kThreads), kThreads, 0, st>>>(
-            s->phi, (int64_t)n2 * n2 * n2, n2, s->pm_corner[0], s->pm_corner[1], s->pm_corner[2], s->pm_n / s->L0,
-            s->pos, s->perm, r.sorted_idx, r.slot, r.n_act, r.acc, r.pot);
+            s->phi, n2, s->pm_corner[0], s->pm_corner[1], s->pm_corner[2], s->pm_n / s->L0,
+            (float)(s->pm_n / s->L0), s->pos, s->perm, r.sorted_idx, r.slot, r.n_act, r.acc, r.pot);
         count_launch();
         TPM_CUDA(cudaGetLastError());
         return TPM_OK;
@@ -494,7 +535,7 @@ int pm_interp_device(Ctx *, const System *s, const WalkRequest &r, cudaStream_t 
     const int ng = s->pm_n;
     const double box = s->bp.box;
     k_pm_interp<<<(unsigned)((r.n_act + kThreads - 1) / kThreads), kThreads, 0, st>>>(
-        s->phi, (int64_t)ng * ng * ng, ng, ng / box, s->pos, s->perm, r.sorted_idx, r.slot, r.n_act, r.acc, r.pot);
+        s->phi, ng, ng / box, (float)(ng / box), s->pos, s->perm, r.sorted_idx, r.slot, r.n_act, r.acc, r.pot);
     count_launch();
     TPM_CUDA(cudaGetLastError());
     return TPM_OK;
