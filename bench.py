@@ -90,11 +90,15 @@ def root_shift(step: int, base: int):
 
 # ------------------------------------------------------------------ helpers
 class ClockSampler:
-    """nvidia-smi clock / throttle samples during the timed region."""
+    """nvidia-smi clock / throttle samples, each stamped with its arrival time;
+    started before the warm-up (nvidia-smi takes longer to start than a short
+    timed region lasts), summarised over the samples inside the timed window
+    (`window(t0, t1)`, host perf_counter times), else the nearest one."""
 
     def __init__(self, device: int):
         self.device = device
         self.samples = []
+        self.t0 = self.t1 = None
         self._stop = threading.Event()
         self._proc = None
 
@@ -113,7 +117,10 @@ class ClockSampler:
 
     def _read(self):
         for line in self._proc.stdout:
-            self.samples.append([x.strip() for x in line.split(",")])
+            self.samples.append((time.perf_counter(), [x.strip() for x in line.split(",")]))
+
+    def window(self, t0, t1):
+        self.t0, self.t1 = t0, t1
 
     def __exit__(self, *a):
         if self._proc:
@@ -126,13 +133,23 @@ class ClockSampler:
     def summary(self):
         if not self.samples:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
-        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        picked = self.samples
+        where = "whole run"
+        if self.t0 is not None:
+            inside = [x for x in self.samples if self.t0 <= x[0] <= self.t1 + 0.03]  # + pipe latency
+            if inside:
+                picked, where = inside, "timed region"
+            else:
+                mid = 0.5 * (self.t0 + self.t1)
+                picked, where = [min(self.samples, key=lambda x: abs(x[0] - mid))], "nearest to the timed region"
+        samples = [x[1] for x in picked]
+        sm = [float(s[0]) for s in samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in samples if s[1].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for s in self.samples for i in range(4)
+        reasons = sorted({names[i] for s in samples for i in range(4)
                           if len(s) > 4 + i and s[4 + i].lower().startswith("active")})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.samples)}
+                "reasons": reasons, "samples": len(samples), "sampled": where}
 
 
 def peaks():
@@ -190,6 +207,10 @@ def run_ours(args, rank, world):
             ev[2].record(stream)
         sy.release()
 
+    clk = ClockSampler(dev.index).__enter__()
+    t_wait = time.perf_counter()
+    while not clk.samples and time.perf_counter() - t_wait < 5.0:  # the sampler is running
+        time.sleep(0.01)
     for k in range(args.warmup):
         step(1 + k)
         a_old.copy_(torch.linalg.vector_norm(acc_buf, dim=1))
@@ -200,11 +221,13 @@ def run_ours(args, rank, world):
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     t_build, t_walk, t_step = [], [], []
     k0, c0 = tpm.launch_counts()
-    with ClockSampler(dev.index) as clk:
-        for k in range(args.steps):
-            l2_flush(flush)
-            step(1000 + k, evs[k])
-        torch.cuda.synchronize()
+    t_host0 = time.perf_counter()
+    for k in range(args.steps):
+        l2_flush(flush)
+        step(1000 + k, evs[k])
+    torch.cuda.synchronize()
+    clk.window(t_host0, time.perf_counter())
+    clk.__exit__()
     k1, c1 = tpm.launch_counts()
     for e in evs:
         t_build.append(e[0].elapsed_time(e[1]))

@@ -322,7 +322,7 @@ int build_entry(tpm_ctx *h, const double *pos, const float *mass, const float *h
     const float *dmass = static_cast<const float *>(device_view(mass));
     int rc = TPM_OK;
     if (!dpos) {
-        double *d;
+        double *d = nullptr;
         rc = stage.get(&d, 3 * n, st);
         if (rc == TPM_OK && cudaMemcpyAsync(d, pos, 3 * n * sizeof(double), cudaMemcpyHostToDevice, st) != cudaSuccess) {
             set_error("copy of positions to the device failed");
@@ -331,7 +331,7 @@ int build_entry(tpm_ctx *h, const double *pos, const float *mass, const float *h
         dpos = d;
     }
     if (rc == TPM_OK && !dmass) {
-        float *d;
+        float *d = nullptr;
         rc = stage.get(&d, n, st);
         if (rc == TPM_OK && cudaMemcpyAsync(d, mass, n * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess) {
             set_error("copy of masses to the device failed");
@@ -341,7 +341,7 @@ int build_entry(tpm_ctx *h, const double *pos, const float *mass, const float *h
     }
     const float *dsoft = static_cast<const float *>(device_view(hsoft));
     if (rc == TPM_OK && hsoft && !dsoft) {
-        float *d;
+        float *d = nullptr;
         rc = stage.get(&d, n, st);
         if (rc == TPM_OK && cudaMemcpyAsync(d, hsoft, n * sizeof(float), cudaMemcpyHostToDevice, st) != cudaSuccess) {
             set_error("copy of softening lengths to the device failed");
