@@ -285,11 +285,7 @@ def run_ours(args, rank, world):
         metric=METRIC, value=value, unit="forces/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
         ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
         data="synthetic",
-        config={"workload": "hernquist_n2^20_relative_alpha0.0025", "n_particles": n, "n_active": n,
-                "softening_h": cfg["h"], "leaf_bucket": cfg["bucket"], "criterion": "relative",
-                "alpha": cfg["alpha"], "first_force": "geometric theta=0.5", "global_batch": n,
-                "parallelism": "replicas" if world > 1 else "single",
-                "l2": "flushed (256 MiB write) between timed steps"},
+        config=headline_config(world),
         interactions_per_s=world * interactions / (walk_ms * 1e-3),
         interactions_per_particle=interactions / n,
         build_ms=build_ms, walk_ms=walk_ms,
@@ -767,6 +763,17 @@ def cores():
         return os.cpu_count() or 1
 
 
+def headline_config(world):
+    """The headline workload, the same for both arms."""
+    cfg = HERNQUIST
+    n = cfg["n"]
+    return {"workload": "hernquist_n2^20_relative_alpha0.0025", "n_particles": n, "n_active": n,
+            "softening_h": cfg["h"], "leaf_bucket": cfg["bucket"], "criterion": "relative", "alpha": cfg["alpha"],
+            "first_force": "geometric theta=0.5", "global_batch": n,
+            "parallelism": "replicas" if world > 1 else "single",
+            "l2": "flushed (256 MiB write) between timed steps"}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
@@ -788,8 +795,7 @@ def run_reference(args, rank, world):
         impl="reference", metric=METRIC, value=v, unit="forces/s", n_gpus=world, steps=args.steps,
         warmup=args.warmup, ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
         data="synthetic",
-        config={"workload": "hernquist_n2^20_relative_alpha0.0025", "n_particles": 1 << 20, "leaf_bucket": 8,
-                "criterion": "relative", "alpha": 0.0025},
+        config=headline_config(world),
         cpu_baseline={"value": v, "unit": "forces/s", "cores": c, "kind": "oracle",
                       "sample": "whole tree build + relative walk of %d random active particles per step, "
                                 "extrapolated to all 2^20" % sample},
