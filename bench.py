@@ -406,6 +406,7 @@ def run_batching(ctx, tpm, torch, dev, stream, pos_d, mass_d, reps=3):
     systems = [sy] * n_req
     g_best, ms_tune = plan.autotune(systems, off, fp, ids_d, acc, a_old=aold, pot=pot, n_int=nint, presorted=True,
                                     reps=2)
+    depth_best = plan.stack_depth
     torch.cuda.synchronize()
     graph = torch.cuda.CUDAGraph()
     side = torch.cuda.Stream()
@@ -434,6 +435,7 @@ def run_batching(ctx, tpm, torch, dev, stream, pos_d, mass_d, reps=3):
             "requests_per_cycle": n_req, "interactions_per_force": inter / n_ids,
             "per_request_launches": {"ms_per_cycle": ms_req, "forces_per_s": n_ids / (ms_req * 1e-3)},
             "batched_graph": {"ms_per_cycle": ms_b, "forces_per_s": n_ids / (ms_b * 1e-3), "group_size": g_best,
+                              "stack_depth": depth_best,
                               "launch": "one persistent walk per cycle, captured in a CUDA graph"},
             "speedup": ms_req / ms_b, "max_rel_diff_vs_per_request": float(e.max())}
 

@@ -267,6 +267,13 @@ int tpm_plan_destroy(tpm_ctx *ctx, tpm_plan *plan);
 int tpm_plan_set_group_size(tpm_plan *plan, int group_size);
 int tpm_plan_group_size(const tpm_plan *plan);
 
+/* Capacity of the batched walk's per-warp candidate stack: 128, 192
+ * (default) or 256 entries (a deeper stack takes more shared memory per warp;
+ * above capacity - 64 entries the walk takes one candidate at a time), and its
+ * current value.  Errors: TPM_EINVAL for other values. */
+int tpm_plan_set_stack_depth(tpm_plan *plan, int depth);
+int tpm_plan_stack_depth(const tpm_plan *plan);
+
 /*
  * Forces for n_req requests in one launch.  Request r evaluates
  * tpm_compute_forces for system systems[r] with params[r] on the ids
@@ -290,9 +297,11 @@ int tpm_compute_forces_batch(tpm_ctx *ctx, tpm_plan *plan, int64_t n_req, const 
  * batches (TPM_EINVAL: an id out of range; TPM_ECUDA: walk stack overflow). */
 int tpm_plan_sync_status(tpm_ctx *ctx, tpm_plan *plan, void *stream);
 
-/* Times the batch for G in {8, 16, 32} (reps timed runs each, after one
- * warm-up), keeps the fastest in the plan and returns it with its median
- * time in milliseconds.  Synchronises.  Arguments as tpm_compute_forces_batch. */
+/* Times the batch for G in {8, 16, 32} x stack depth in {128, 192, 256}
+ * (reps timed runs each, after one warm-up), keeps the fastest pair in the
+ * plan and returns its G (read the depth with tpm_plan_stack_depth) with its
+ * median time in milliseconds.  Synchronises.  Arguments as
+ * tpm_compute_forces_batch. */
 int tpm_plan_autotune(tpm_ctx *ctx, tpm_plan *plan, int64_t n_req, const tpm_sys *systems, const int64_t *offsets,
                       const tpm_force_params *params, const uint32_t *ids, const float *a_old, float *acc,
                       float *pot, uint32_t *n_int, uint32_t flags, int reps, void *stream, int *best_group,

@@ -88,6 +88,8 @@ def _load():
         "tpm_plan_destroy": (i32, [vp, vp]),
         "tpm_plan_set_group_size": (i32, [vp, i32]),
         "tpm_plan_group_size": (i32, [vp]),
+        "tpm_plan_set_stack_depth": (i32, [vp, i32]),
+        "tpm_plan_stack_depth": (i32, [vp]),
         "tpm_compute_forces_batch": (i32, [vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, C.c_uint32, vp]),
         "tpm_plan_sync_status": (i32, [vp, vp, vp]),
         "tpm_plan_autotune": (i32, [vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, C.c_uint32, i32, vp,
@@ -232,6 +234,15 @@ class Plan:
     @group_size.setter
     def group_size(self, g: int):
         _check(_lib.tpm_plan_set_group_size(self._h, int(g)))
+
+    @property
+    def stack_depth(self) -> int:
+        """``tpm_plan_stack_depth``: the batched walk's candidate-stack capacity."""
+        return int(_lib.tpm_plan_stack_depth(self._h))
+
+    @stack_depth.setter
+    def stack_depth(self, d: int):
+        _check(_lib.tpm_plan_set_stack_depth(self._h, int(d)))
 
     def _args(self, systems, offsets, params):
         n_req = len(systems)

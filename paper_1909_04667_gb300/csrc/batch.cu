@@ -36,6 +36,7 @@ struct Plan {
     Ctx *ctx = nullptr;
     int64_t max_ids = 0, max_req = 0, max_groups = 0;
     int group_size = 32;
+    int stack_depth = 192;  // candidate-stack capacity of the batched walk
     AllocSet mem;
     uint64_t *keys = nullptr, *skeys = nullptr;
     uint32_t *vals = nullptr, *slot = nullptr, *sidx = nullptr;
@@ -241,8 +242,8 @@ int run_batch(Ctx *c, Plan *pl, int64_t n_req, const tpm_sys *systems, const int
     count_launch();
     TPM_CUDA(cudaMemsetAsync(pl->next, 0, sizeof(unsigned), st));
     TPM_CUDA(cudaGetLastError());
-    return launch_walk_batch(c, pl->reqs_dev, pl->groups, pl->ngroups, pl->next, pl->sidx, pl->slot, a_old, acc, pot,
-                             nint, pl->err, st);
+    return launch_walk_batch(c, pl->stack_depth, pl->reqs_dev, pl->groups, pl->ngroups, pl->next, pl->sidx, pl->slot,
+                             a_old, acc, pot, nint, pl->err, st);
 }
 
 }  // namespace
@@ -341,6 +342,18 @@ int tpm_plan_set_group_size(tpm_plan *plan, int group_size) {
 
 int tpm_plan_group_size(const tpm_plan *plan) { return plan ? plan->p.group_size : 0; }
 
+int tpm_plan_set_stack_depth(tpm_plan *plan, int depth) {
+    clear_error();
+    if (!plan || (depth != 128 && depth != 192 && depth != 256)) {
+        set_error("stack depth must be 128, 192 or 256");
+        return TPM_EINVAL;
+    }
+    plan->p.stack_depth = depth;
+    return TPM_OK;
+}
+
+int tpm_plan_stack_depth(const tpm_plan *plan) { return plan ? plan->p.stack_depth : 0; }
+
 int tpm_compute_forces_batch(tpm_ctx *h, tpm_plan *plan, int64_t n_req, const tpm_sys *systems,
                              const int64_t *offsets, const tpm_force_params *params, const uint32_t *ids,
                              const float *a_old, float *acc, float *pot, uint32_t *n_int, uint32_t flags,
@@ -399,12 +412,14 @@ int tpm_plan_autotune(tpm_ctx *h, tpm_plan *plan, int64_t n_req, const tpm_sys *
     cudaEvent_t e0, e1;
     TPM_CUDA(cudaEventCreate(&e0));
     TPM_CUDA(cudaEventCreate(&e1));
-    const int cand[3] = {8, 16, 32};
-    int best = plan->p.group_size;
+    const int groups[3] = {8, 16, 32}, depths[3] = {128, 192, 256};
+    int best = plan->p.group_size, best_depth = plan->p.stack_depth;
     float best_t = 1e30f;
     int rc = TPM_OK;
-    for (int g : cand) {
+    for (int cand = 0; cand < 9 && rc == TPM_OK; cand++) {
+        const int g = groups[cand / 3];
         plan->p.group_size = g;
+        plan->p.stack_depth = depths[cand % 3];
         rc = run_batch(c, &plan->p, n_req, systems, offsets, params, ids, a_old, acc, pot, n_int, flags, st);
         if (rc != TPM_OK)
             break;
@@ -429,11 +444,13 @@ int tpm_plan_autotune(tpm_ctx *h, tpm_plan *plan, int64_t n_req, const tpm_sys *
         if (med < best_t) {
             best_t = med;
             best = g;
+            best_depth = plan->p.stack_depth;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     plan->p.group_size = best;
+    plan->p.stack_depth = best_depth;
     if (best_group)
         *best_group = best;
     if (best_ms)

@@ -356,8 +356,12 @@ __global__ void __launch_bounds__(kWalkThreads)
 // ranges (children are contiguous in breadth-first order).
 // ======================================================================
 constexpr int kGroupWarps = 4;
+// Candidate-stack capacity: 192 for the plain walk; the batched walk is also
+// compiled at 128 and 256 for the plan's autotuner.  Above capacity - 64
+// entries the walk takes one candidate at a time, so the stack grows by at
+// most one batch of pushes (32) plus the tree depth (21) past that mark.
 constexpr int kStackCap = 192;
-constexpr int kStackSafe = kStackCap - 64;  // above this, take one candidate at a time
+constexpr int kStackDepths[3] = {128, 192, 256};
 constexpr int kNodeFlush = 64;              // sweep once this many node entries are queued
 constexpr int kNodeCap = kNodeFlush + 32;   // one batch adds at most 32 (one per candidate)
 constexpr int kLeafFlush = 32;
@@ -365,9 +369,12 @@ constexpr int kLeafCap = kLeafFlush + 64;
 constexpr uint32_t kLeafWrap = 0x80000000u, kLeafCount = 0x7fffffffu;
 enum { kSkip = 0, kAccept = 1, kOpen = 2, kMixed = 3, kNone = 4 };
 
-struct GroupShared {
-    uint2 stack[kStackCap];  // (first child, lane mask)
-    uint8_t scount[kStackCap];
+template <int STACK>
+struct GroupSharedT {
+    static constexpr int kStack = STACK;
+    static constexpr int kSafe = STACK - 64;  // above this, take one candidate at a time
+    uint2 stack[STACK];  // (first child, lane mask)
+    uint8_t scount[STACK];
     float4 nsrc[kNodeCap];   // accepted node: centre of mass (group frame) + mass
     float nsoft[kNodeCap];   // its largest spline support (per-particle softening only)
     uint32_t nmask[kNodeCap];
@@ -470,8 +477,8 @@ __device__ __forceinline__ void newton_term(float rx, float ry, float rz, float 
 // entries out again and adds their spline term.  With per-particle softening
 // (VARH) the support of an entry is the larger of the lane's own (hi) and the
 // node's largest (Sec. 3.2), and such entries add zero mass in the first pass.
-template <bool PERIODIC, bool TREEPM, bool VARH>
-__device__ __forceinline__ void sweep_full(const GroupShared &sh, int nf, float xox, float xoy, float xoz, float hi,
+template <bool PERIODIC, bool TREEPM, bool VARH, class SH>
+__device__ __forceinline__ void sweep_full(const SH &sh, int nf, float xox, float xoy, float xoz, float hi,
                                            const WalkConsts &k, float &ax, float &ay, float &az, float &ph) {
     if (TREEPM || PERIODIC) {
         for (int e = 0; e < nf; e++) {
@@ -582,8 +589,8 @@ __device__ __forceinline__ void sweep_full(const GroupShared &sh, int nf, float 
 // (indices [kNodeCap - np, kNodeCap)): a lane not tagged adds a zero mass
 // (at max(r, h), since such a lane may sit on the node), and entries inside
 // the softening length are repaired as in sweep_full.
-template <bool PERIODIC, bool TREEPM, bool VARH>
-__device__ __forceinline__ void sweep_partial(const GroupShared &sh, int np, unsigned lanebit, float xox, float xoy,
+template <bool PERIODIC, bool TREEPM, bool VARH, class SH>
+__device__ __forceinline__ void sweep_partial(const SH &sh, int np, unsigned lanebit, float xox, float xoy,
                                               float xoz, float hi, const WalkConsts &k, float &ax, float &ay,
                                               float &az, float &ph, uint32_t &cnt) {
     const int e0 = kNodeCap - np;
@@ -671,8 +678,8 @@ __device__ __forceinline__ void sweep_partial(const GroupShared &sh, int np, uns
 }
 
 // Sweeps the queued opened leaves, particle by particle.
-template <bool PERIODIC, bool TREEPM, bool VARH>
-__device__ __forceinline__ void sweep_leaves(const GroupShared &sh, int nl, unsigned lanebit, uint32_t self,
+template <bool PERIODIC, bool TREEPM, bool VARH, class SH>
+__device__ __forceinline__ void sweep_leaves(const SH &sh, int nl, unsigned lanebit, uint32_t self,
                                              float xox, float xoy, float xoz, float hi,
                                              const float4 *__restrict__ spart, const float *__restrict__ psoft,
                                              const WalkConsts &k, float &ax, float &ay, float &az, float &ph,
@@ -729,8 +736,8 @@ struct TreeView {
 
 // Walks the tree for the group of gcount <= 32 active particles at positions
 // [g0, g0 + gcount) of the sorted active list (one per lane).
-template <bool PERIODIC, bool RELATIVE, bool TREEPM, bool VARH>
-__device__ __forceinline__ void group_walk(const TreeView &T, const WalkConsts &k, GroupShared &sh,
+template <bool PERIODIC, bool RELATIVE, bool TREEPM, bool VARH, class SH>
+__device__ __forceinline__ void group_walk(const TreeView &T, const WalkConsts &k, SH &sh,
                                            const uint32_t *__restrict__ sidx, const uint32_t *__restrict__ slot,
                                            int64_t g0, int gcount, const float *__restrict__ a_old,
                                            float *__restrict__ acc, float *__restrict__ pot,
@@ -814,7 +821,7 @@ __device__ __forceinline__ void group_walk(const TreeView &T, const WalkConsts &
     __syncwarp();
     while (sn > 0) {
         // ---- take up to 32 candidates from the top child ranges
-        const int cap = sn > kStackSafe ? 1 : 32;
+        const int cap = sn > SH::kSafe ? 1 : 32;
         const int idx = sn - 1 - lane;
         uint2 R = make_uint2(0u, 0u);
         int c = 0;
@@ -891,14 +898,14 @@ __device__ __forceinline__ void group_walk(const TreeView &T, const WalkConsts &
         const unsigned bp = __ballot_sync(FULL, e_push);
         if (e_push) {
             const int at = sn + __popc(bp & lt_mask);
-            if (at < kStackCap) {
+            if (at < SH::kStack) {
                 sh.stack[at] = make_uint2((uint32_t)Lk.x, nmask);
                 sh.scount[at] = (uint8_t)Lk.y;
             } else {
                 atomicOr(err, 2);
             }
         }
-        sn = min(sn + __popc(bp), kStackCap);
+        sn = min(sn + __popc(bp), SH::kStack);
 
         // ---- nodes the bounds could not decide: per-particle decisions, as in
         // the lane walk.  A lane that accepts the node adds its monopole at
@@ -959,14 +966,14 @@ __device__ __forceinline__ void group_walk(const TreeView &T, const WalkConsts &
             if (om) {
                 if (l1 >= 0) {
                     if (lane == 0) {
-                        if (sn < kStackCap) {
+                        if (sn < SH::kStack) {
                             sh.stack[sn] = make_uint2((uint32_t)l0, om);
                             sh.scount[sn] = (uint8_t)l1;
                         } else {
                             atomicOr(err, 2);
                         }
                     }
-                    sn = min(sn + 1, kStackCap);
+                    sn = min(sn + 1, SH::kStack);
                 } else {
                     float wx = dx, wy = dy, wz = dz;  // node centre, group-centred nearest image
                     if (PERIODIC) {
@@ -1031,8 +1038,9 @@ __global__ void __launch_bounds__(kGroupWarps * 32)
     k_walk_group(TreeView T, const uint32_t *__restrict__ sidx, const uint32_t *__restrict__ slot,
                  const float *__restrict__ a_old, int64_t n_act, int gsize, WalkConsts k, float *__restrict__ acc,
                  float *__restrict__ pot, uint32_t *__restrict__ nint, int accumulate, int *__restrict__ err) {
+    using SH = GroupSharedT<kStackCap>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    GroupShared &sh = reinterpret_cast<GroupShared *>(smem_raw)[threadIdx.x >> 5];
+    SH &sh = reinterpret_cast<SH *>(smem_raw)[threadIdx.x >> 5];
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t g0 = warp * gsize;
     if (g0 >= n_act)
@@ -1051,15 +1059,17 @@ struct BatchReq {
 
 // Persistent batch walk: resident warps take groups (start, count, request)
 // from a device work queue until it is empty; groups of one launch may
-// belong to different requests and different trees.
-template <bool PERIODIC, bool TREEPM>
+// belong to different requests and different trees.  Compiled per candidate
+// stack capacity (the plan's autotuner chooses one).
+template <bool PERIODIC, bool TREEPM, int STACK>
 __global__ void __launch_bounds__(kGroupWarps * 32)
     k_walk_batch(const BatchReq *__restrict__ reqs, const uint4 *__restrict__ groups,
                  const unsigned *__restrict__ n_groups, unsigned *__restrict__ next, const uint32_t *__restrict__ sidx,
                  const uint32_t *__restrict__ slot, const float *__restrict__ a_old, float *__restrict__ acc,
                  float *__restrict__ pot, uint32_t *__restrict__ nint, int *__restrict__ err) {
+    using SH = GroupSharedT<STACK>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    GroupShared &sh = reinterpret_cast<GroupShared *>(smem_raw)[threadIdx.x >> 5];
+    SH &sh = reinterpret_cast<SH *>(smem_raw)[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const unsigned total = *n_groups;
     for (;;) {
@@ -1095,7 +1105,7 @@ void launch(const System *s, const WalkRequest &r, const WalkConsts &k, bool lan
         count_launch();
     } else {
         const int64_t blocks = (warps + kGroupWarps - 1) / kGroupWarps;
-        const size_t smem = kGroupWarps * sizeof(GroupShared);
+        const size_t smem = kGroupWarps * sizeof(GroupSharedT<kStackCap>);
         TreeView tv{s->bcen, s->bcom, s->blink, s->spart, s->psoft, s->bsoft, s->key,
                     s->perm, s->pos,  s->x0[0], s->x0[1],  s->x0[2], s->L0};
         k_walk_group<P, R, T, V><<<(unsigned)blocks, kGroupWarps * 32, smem, st>>>(
@@ -1163,22 +1173,44 @@ void fill_batch_req(void *dst, const System *s, const tpm_force_params *p) {
     memcpy(dst, &r, sizeof r);
 }
 
-int launch_walk_batch(Ctx *c, const void *reqs, const uint4 *groups, const unsigned *n_groups, unsigned *next,
-                      const uint32_t *sidx, const uint32_t *slot, const float *a_old, float *acc, float *pot,
-                      uint32_t *nint, int *err, cudaStream_t st) {
-    const size_t smem = kGroupWarps * sizeof(GroupShared);
-    static int blocks_per_sm = 0;
+template <int STACK>
+int launch_walk_batch_at(Ctx *c, const void *reqs, const uint4 *groups, const unsigned *n_groups, unsigned *next,
+                         const uint32_t *sidx, const uint32_t *slot, const float *a_old, float *acc, float *pot,
+                         uint32_t *nint, int *err, cudaStream_t st) {
+    const size_t smem = kGroupWarps * sizeof(GroupSharedT<STACK>);
+    static int blocks_per_sm = 0;  // resident blocks of this variant (one persistent wave)
     if (!blocks_per_sm) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_walk_batch<false, false>,
-                                                          kGroupWarps * 32, smem) != cudaSuccess ||
-            blocks_per_sm < 1)
-            blocks_per_sm = 1;
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_walk_batch<false, false, STACK>, kGroupWarps * 32,
+                                                          smem) != cudaSuccess ||
+            b < 1)
+            b = 1;
+        blocks_per_sm = b;
     }
-    k_walk_batch<false, false><<<(unsigned)(c->num_sms * blocks_per_sm), kGroupWarps * 32, smem, st>>>(
+    k_walk_batch<false, false, STACK><<<(unsigned)(c->num_sms * blocks_per_sm), kGroupWarps * 32, smem, st>>>(
         static_cast<const BatchReq *>(reqs), groups, n_groups, next, sidx, slot, a_old, acc, pot, nint, err);
     count_launch();
     TPM_CUDA(cudaGetLastError());
     return TPM_OK;
+}
+
+int launch_walk_batch(Ctx *c, int stack_depth, const void *reqs, const uint4 *groups, const unsigned *n_groups,
+                      unsigned *next, const uint32_t *sidx, const uint32_t *slot, const float *a_old, float *acc,
+                      float *pot, uint32_t *nint, int *err, cudaStream_t st) {
+    switch (stack_depth) {
+    case kStackDepths[0]:
+        return launch_walk_batch_at<kStackDepths[0]>(c, reqs, groups, n_groups, next, sidx, slot, a_old, acc, pot,
+                                                     nint, err, st);
+    case kStackDepths[1]:
+        return launch_walk_batch_at<kStackDepths[1]>(c, reqs, groups, n_groups, next, sidx, slot, a_old, acc, pot,
+                                                     nint, err, st);
+    case kStackDepths[2]:
+        return launch_walk_batch_at<kStackDepths[2]>(c, reqs, groups, n_groups, next, sidx, slot, a_old, acc, pot,
+                                                     nint, err, st);
+    default:
+        set_error("stack depth %d is not one of 128, 192, 256", stack_depth);
+        return TPM_EINVAL;
+    }
 }
 
 int walk_device(Ctx *c, const System *s, const tpm_force_params *p, const WalkRequest &r, cudaStream_t st) {

@@ -142,6 +142,26 @@ def test_autotune_and_errors(env):
     acc = torch.empty((len(ids), 3), device=dev)
     g, ms = plan.autotune([r[0] for r in reqs], off, [r[2] for r in reqs], ids, acc, a_old=a_old, reps=2)
     assert g in (8, 16, 32) and plan.group_size == g and ms > 0
+    assert plan.stack_depth in (128, 192, 256)
+    # every stack depth makes the same decisions (interaction counts); the
+    # order of the sums may differ where a shallower stack takes candidates one
+    # at a time earlier
+    ref = None
+    for depth in (192, 128, 256):
+        plan.stack_depth = depth
+        a = torch.empty((len(ids), 3), device=dev)
+        k = torch.empty(len(ids), dtype=torch.int32, device=dev)
+        plan.compute_forces_batch([r[0] for r in reqs], off, [r[2] for r in reqs], ids, a, a_old=a_old, n_int=k)
+        plan.sync_status()
+        a, k = a.cpu().numpy().astype(np.float64), k.cpu().numpy()
+        if ref is None:
+            ref = (a, k)
+            continue
+        np.testing.assert_array_equal(k, ref[1])
+        err = np.linalg.norm(a - ref[0], axis=1) / np.linalg.norm(ref[0], axis=1)
+        assert np.percentile(err, 99) < 1e-5 and err.max() < 1e-4
+    with pytest.raises(tpm.TreePMError, match="TPM_EINVAL"):
+        plan.stack_depth = 100
     with pytest.raises(tpm.TreePMError, match="TPM_EINVAL"):  # more requests than the plan holds
         plan.compute_forces_batch([reqs[0][0]] * (len(reqs) + 1), np.zeros(len(reqs) + 2, np.int64),
                                   tpm.ForceParams(), ids, acc)
