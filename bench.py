@@ -43,9 +43,9 @@ FLOPS_PER_INTERACTION = 20  # monopole pair term with potential, FP32: offset 3,
 # from: DRAM bytes (read + write), and the
 # FP32 flops the kernel executed per cycle over the whole GPU (fadd + fmul +
 # 2 ffma thread instructions) against the FP32 peak per cycle (SMs x 128 x 2)
-WALK_TRAFFIC = {"bytes": 98.881024e6 + 12.670976e6,
-                "fp32_flops_per_cycle": 1765.031176 + 1458.107789 + 2 * 1421.878237,
-                "walk_cu_sha256": "78f3594bb7832061014dd0ac7393cb00ab9aa17a353742d4a9f22414de263445"}
+WALK_TRAFFIC = {"bytes": 98.750464e6 + 13.277440e6,
+                "fp32_flops_per_cycle": 1761.259910 + 1454.992313 + 2 * 1418.840171,
+                "walk_cu_sha256": "9f18eb7c7639fa84dbc4947853cd28b6b02ba316f56f47b537d42f1ae7223bf3"}
 
 
 def walk_capture():
