@@ -240,6 +240,16 @@ def run_ours(args, rank, world):
     walk_ms = statistics.mean(t_walk)
     build_ms = statistics.mean(t_build)
 
+    # ---------------- FP64 conservation diagnostics of one relative step (untimed)
+    sy = ctx.build_tree(pos_d, mass_d, bp(9999))
+    sy.compute_forces(a_old=a_old, fp=fp_rel, acc=acc_buf, pot=pot_buf, n_int=nint_buf)
+    dg = sy.diagnostics(acc_buf, pot_buf)
+    sy.release()
+    diagnostics = {"total_force_over_scale": float(np.linalg.norm(dg["total_force"]) / dg["force_scale"]),
+                   "potential_energy": dg["potential_energy"],
+                   "note": "FP64 on the GPU: |sum m a| / sum m |a| (zero for exactly symmetric forces) and "
+                           "1/2 sum m phi of one relative-criterion step"}
+
     # ---------------- end to end through the C ABI with host buffers
     pos_h = torch.from_numpy(pos).pin_memory()
     mass_h = torch.from_numpy(mass).pin_memory()
@@ -302,6 +312,7 @@ def run_ours(args, rank, world):
                   "algorithmic": "%d flops x %d useful interactions per launch" % (FLOPS_PER_INTERACTION,
                                                                                     interactions)},
         gpu_launches=int(k1 - k0),
+        diagnostics=diagnostics,
         cub_calls=int(c1 - c0),
         clocks=clocks,
         periodic_treepm=periodic,

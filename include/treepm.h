@@ -313,6 +313,21 @@ int tpm_plan_autotune(tpm_ctx *ctx, tpm_plan *plan, int64_t n_req, const tpm_sys
  * if the walk's candidate stack overflowed; TPM_OK otherwise. */
 int tpm_sync_status(tpm_ctx *ctx, tpm_sys s, void *stream);
 
+/* FP64 conservation diagnostics of forces on all n particles of system s
+ * (the momentum and energy checks of a gravity solver, Sec. 7).  acc (n x 3
+ * FP32), pot (n FP32, may be NULL) and vel (n x 3 FP64, may be NULL) are
+ * DEVICE arrays in the caller's particle order; the masses are the system's.
+ * out (host, 9 doubles): [0..2] total force sum_i m_i a_i (zero for an
+ * exactly symmetric interaction; a tree leaves a residual of the size of its
+ * force errors), [3] potential energy 1/2 sum_i m_i phi_i (0 without pot),
+ * [4] kinetic energy 1/2 sum_i m_i |v_i|^2 and [5..7] momentum sum_i m_i v_i
+ * (0 without vel), [8] sum_i m_i |a_i|, the scale of [0..2].  FP64 sums in a
+ * fixed order (the same bits on every run on the same GPU model).
+ * Synchronises.  Errors: TPM_EINVAL (null or host arrays), TPM_ENOSYS_HANDLE,
+ * TPM_ECUDA. */
+int tpm_diagnostics(tpm_ctx *ctx, tpm_sys s, const float *acc, const float *pot, const double *vel, double *out,
+                    void *stream);
+
 /* Frees a resident system.  Waits for its outstanding work. */
 int tpm_release(tpm_ctx *ctx, tpm_sys s);
 

@@ -16,6 +16,8 @@ Pieces (paper section in brackets):
 * ``pm_potential`` / ``pm_interpolate``  periodic PM long-range part      [Sec. 3.3, 3.4]
 * ``insertion_tree``             the paper's one-by-one insertion build
                                  (brute force, for pinning the node set) [Sec. 3.1]
+* ``diagnostics``                total force, energies, momentum (FP64
+                                 sums as written)                        [Sec. 7]
 
 The C part (``treepm_oracle.c``) is compiled with gcc by ``build()``; the PM
 part is numpy with ``numpy.fft`` as the FFT step.  Every function is pinned by
@@ -488,6 +490,25 @@ def treepm_isolated(pos, mass, targets, ngrid: int, asmth: float, rcut_cells: fl
 
 
 # ---------------------------------------------------------------- insertion tree
+def diagnostics(mass, acc, pot=None, vel=None) -> dict:
+    """Conservation diagnostics of a force evaluation [Sec. 7], each a plain
+    FP64 sum over the particles: total force sum_i m_i a_i, its scale
+    sum_i m_i |a_i|, potential energy 1/2 sum_i m_i phi_i, kinetic energy
+    1/2 sum_i m_i |v_i|^2 and momentum sum_i m_i v_i (zero without pot / vel)."""
+    m = np.asarray(mass, np.float64)
+    a = np.asarray(acc, np.float64).reshape(-1, 3)
+    out = {"total_force": (m[:, None] * a).sum(axis=0),
+           "force_scale": float((m * np.sqrt((a * a).sum(axis=1))).sum()),
+           "potential_energy": 0.0, "kinetic_energy": 0.0, "momentum": np.zeros(3)}
+    if pot is not None:
+        out["potential_energy"] = float(0.5 * (m * np.asarray(pot, np.float64)).sum())
+    if vel is not None:
+        v = np.asarray(vel, np.float64).reshape(-1, 3)
+        out["kinetic_energy"] = float(0.5 * (m * (v * v).sum(axis=1)).sum())
+        out["momentum"] = (m[:, None] * v).sum(axis=0)
+    return out
+
+
 def insertion_tree(pos, x0, L0: float, bucket: int = 1, order=None):
     """The paper's construction (Sec. 3.1), brute force: start from the cubic
     root, insert particles one at a time, descending by comparing coordinates

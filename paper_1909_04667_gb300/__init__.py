@@ -89,6 +89,7 @@ def _load():
         "tpm_plan_set_group_size": (i32, [vp, i32]),
         "tpm_plan_group_size": (i32, [vp]),
         "tpm_plan_set_stack_depth": (i32, [vp, i32]),
+        "tpm_diagnostics": (i32, [vp, C.c_uint64, vp, vp, vp, vp, vp]),
         "tpm_plan_stack_depth": (i32, [vp]),
         "tpm_compute_forces_batch": (i32, [vp, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, C.c_uint32, vp]),
         "tpm_plan_sync_status": (i32, [vp, vp, vp]),
@@ -398,6 +399,16 @@ class System:
                                                C.byref(cp), _ptr(acc), _ptr(pot), _ptr(n_int),
                                                _stream(stream, self.ctx.device)))
         return acc, pot, n_int
+
+    def diagnostics(self, acc, pot=None, vel=None, stream=None) -> dict:
+        """``tpm_diagnostics``: FP64 total force, its scale sum m |a|, potential
+        energy, and with velocities kinetic energy and momentum, over all
+        particles (device tensors in the caller's order)."""
+        out = np.zeros(9, np.float64)
+        _check(_lib.tpm_diagnostics(self.ctx._h, self.handle, _ptr(acc), _ptr(pot), _ptr(vel), out.ctypes.data,
+                                    _stream(stream, self.ctx.device)))
+        return {"total_force": out[0:3].copy(), "potential_energy": float(out[3]), "kinetic_energy": float(out[4]),
+                "momentum": out[5:8].copy(), "force_scale": float(out[8])}
 
     def sync_status(self, stream=None):
         """``tpm_sync_status``: wait for the stream and raise if device work

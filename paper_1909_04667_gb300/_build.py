@@ -17,7 +17,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libtreepm.so")
-SOURCES = ["runtime.cu", "build.cu", "walk.cu", "pm.cu", "noalloc.cu", "batch.cu", "integrate.cu", "ewald.cu"]
+SOURCES = ["runtime.cu", "build.cu", "walk.cu", "pm.cu", "noalloc.cu", "batch.cu", "integrate.cu", "ewald.cu",
+           "diagnostics.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

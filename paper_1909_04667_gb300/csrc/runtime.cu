@@ -549,6 +549,27 @@ int tpm_compute_forces(tpm_ctx *h, tpm_sys sid, const uint32_t *active_ids, int6
     return TPM_OK;
 }
 
+int tpm_diagnostics(tpm_ctx *h, tpm_sys sid, const float *acc, const float *pot, const double *vel, double *out,
+                    void *stream) {
+    clear_error();
+    if (!h || !acc || !out) {
+        set_error("null ctx, acc or out");
+        return TPM_EINVAL;
+    }
+    Ctx *c = reinterpret_cast<Ctx *>(h);
+    System *s = find(c, sid);
+    if (!s) {
+        set_error("unknown system handle %llu", (unsigned long long)sid);
+        return TPM_ENOSYS_HANDLE;
+    }
+    if (!is_device_ptr(acc) || (pot && !is_device_ptr(pot)) || (vel && !is_device_ptr(vel))) {
+        set_error("acc, pot and vel must be device arrays");
+        return TPM_EINVAL;
+    }
+    TPM_CUDA(cudaSetDevice(c->device));
+    return diagnostics_device(c, s, acc, pot, vel, out, reinterpret_cast<cudaStream_t>(stream));
+}
+
 int tpm_sync_status(tpm_ctx *h, tpm_sys sid, void *stream) {
     clear_error();
     if (!h) {

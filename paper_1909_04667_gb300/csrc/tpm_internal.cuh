@@ -210,6 +210,13 @@ int launch_walk_batch(Ctx *c, int stack_depth, const void *reqs, const uint4 *gr
                       unsigned *next, const uint32_t *sidx, const uint32_t *slot, const float *a_old, float *acc,
                       float *pot, uint32_t *nint, int *err, cudaStream_t st);
 
+// FP64 conservation diagnostics over all particles of s (device arrays in the
+// caller's order): out_host[0..2] total force, [3] potential energy, [4]
+// kinetic energy, [5..7] momentum, [8] sum of m |a|.  Synchronous.
+constexpr int kDiagSums = 9;
+int diagnostics_device(Ctx *c, const System *s, const float *acc, const float *pot, const double *vel,
+                       double *out_host, cudaStream_t st);
+
 // Adds the CIC-interpolated mesh force and potential to acc / pot.
 int pm_interp_device(Ctx *c, const System *s, const WalkRequest &r, cudaStream_t st);
 
