@@ -194,8 +194,21 @@ class ForceServer:
                 aolds.append(torch.index_select(res.aold, 0, part))
             a_old = aolds[0] if len(aolds) == 1 else torch.cat(aolds)
             acc, pot, nint = self.acc_d[:n], self.pot_d[:n], self.nint_d[:n]
-            self.plan.compute_forces_batch(systems, off, params, ids_d, acc, a_old=a_old, pot=pot, n_int=nint,
-                                           stream=self.walk_stream.cuda_stream)
+            walked = False
+            if len(reqs) == 1 and self.plan.group_size == 32 and self.plan.stack_depth == 192:
+                # a round of one request (light load): the plain call runs the
+                # same walk without the batch's request sort and group table;
+                # its scratch comes from the budget, else the batch path runs
+                try:
+                    systems[0].compute_forces(active_ids=ids_d, a_old=a_old, fp=params[0], acc=acc, pot=pot,
+                                              n_int=nint, stream=self.walk_stream.cuda_stream)
+                    walked = True
+                except TreePMError as e:
+                    if e.status != _EBUDGET:
+                        raise
+            if not walked:
+                self.plan.compute_forces_batch(systems, off, params, ids_d, acc, a_old=a_old, pot=pot, n_int=nint,
+                                               stream=self.walk_stream.cuda_stream)
             self.acc_h[:n].copy_(acc, non_blocking=True)
             self.pot_h[:n].copy_(pot, non_blocking=True)
             self.nint_h[:n].copy_(nint, non_blocking=True)
@@ -257,9 +270,12 @@ class ForceServer:
                     raise MemoryError("the tree of system %d does not fit in the HBM budget" % queue[0].sid)
                 inflight = self._launch(batch)
             elif queue and inflight is not None:
-                # admit while the GPU walks: build the trees the waiting requests need
+                # admit while the GPU walks: build a tree a waiting request
+                # needs -- one per pass, so that the round in flight is seen
+                # to finish between builds
                 for r in list(queue)[:self.max_req]:
-                    if r.sid not in self.resident and not self.ensure_resident(r.sid):
+                    if r.sid not in self.resident:
+                        self.ensure_resident(r.sid)
                         break
                 if not inflight.event.query():
                     time.sleep(0)
