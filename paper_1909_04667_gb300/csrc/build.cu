@@ -504,21 +504,31 @@ struct NodeOut {
     float *nsoft, *bsoft;  // per-particle softening only
 };
 
-// K5: walk tables.  Pre-order: FP32 geometric centre (exact, on the 2^-22 L0
-// grid) and side, centre of mass relative to the centre and mass, (skip,
-// first particle, count, leaf flag), plus level and key prefix for export.
-// The FP32 centre-of-mass offset takes S / m as S times the correctly rounded
-// 1 / m (one FP64 reciprocal instead of three divisions; the FP64 product is
-// within an ulp of the quotient, far below the FP32 rounding of the offset).
-// The exact FP64 centre of mass S / m is formed when the tree is exported.
-// Breadth-first (level by level, each level in key order, so that a node's
-// children are contiguous): the same records with (first child, child count,
-// first particle, count).  A leaf also writes its particles relative to its
-// centre (FP64 difference -> FP32) with their masses.
-__global__ void k_finalize(NodeArrays t, const uint32_t *__restrict__ pre2bfs, int64_t total,
-                           const double *__restrict__ M, const double *__restrict__ S, const double *__restrict__ spos,
-                           const float *__restrict__ smass, const float *__restrict__ hmx,
-                           const float *__restrict__ hmn, double x0, double y0, double z0, double L0, NodeOut o) {
+// Exact centre of node (lvl, pre) relative to x0: (2 i + 1) L0 2^-(lvl + 1)
+// per axis, i the cell index along the axis read off the key prefix; the
+// power of two is built from its bits (exact scaling, lvl <= 21).
+struct NodeGeom {
+    double rx, ry, rz, side;
+};
+__device__ __forceinline__ NodeGeom node_geom(uint64_t pre, int lvl, double L0) {
+    const double half = __dmul_rn(L0, __longlong_as_double((long long)(1022 - lvl) << 52));
+    NodeGeom g;
+    g.rx = __dmul_rn((double)(2 * (uint64_t)compact3(pre) + 1), half);
+    g.ry = __dmul_rn((double)(2 * (uint64_t)compact3(pre >> 1) + 1), half);
+    g.rz = __dmul_rn((double)(2 * (uint64_t)compact3(pre >> 2) + 1), half);
+    g.side = 2.0 * half;
+    return g;
+}
+
+// K5a: walk tables that do not need the monopoles, written while the monopole
+// pass climbs.  Pre-order: FP32 geometric centre (exact, on the 2^-22 L0 grid)
+// and side, (skip, first particle, count, leaf flag), level and key prefix
+// for export; breadth-first: centre and (first child, child count, first
+// particle, particle count); and every leaf's particles relative to the FP32
+// leaf centre (FP64 difference rounded to FP32) with their masses.
+__global__ void k_tables(NodeArrays t, const uint32_t *__restrict__ pre2bfs, int64_t total,
+                         const double *__restrict__ spos, const float *__restrict__ smass, double x0, double y0,
+                         double z0, double L0, NodeOut o) {
     const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (p >= total)
         return;
@@ -526,35 +536,47 @@ __global__ void k_finalize(NodeArrays t, const uint32_t *__restrict__ pre2bfs, i
     const int lvl = t.level[p];
     const uint64_t pre = t.prefix[p];
     const uint32_t q = pre2bfs[p];
-    const double m = M[q];
-    const double rm = __drcp_rn(m);
-    const double cx = __dmul_rn(S[3 * q], rm), cy = __dmul_rn(S[3 * q + 1], rm), cz = __dmul_rn(S[3 * q + 2], rm);
-    const double half = ldexp(L0, -(lvl + 1));
-    const double rx = (double)(2 * (uint64_t)compact3(pre) + 1) * half;
-    const double ry = (double)(2 * (uint64_t)compact3(pre >> 1) + 1) * half;
-    const double rz = (double)(2 * (uint64_t)compact3(pre >> 2) + 1) * half;  // centre relative to x0 (exact)
-    const float4 cen = make_float4((float)rx, (float)ry, (float)rz, (float)(2.0 * half));
-    const float4 com = make_float4((float)__dsub_rn(cx, __dadd_rn(x0, rx)), (float)__dsub_rn(cy, __dadd_rn(y0, ry)),
-                                   (float)__dsub_rn(cz, __dadd_rn(z0, rz)), (float)m);
+    const NodeGeom g = node_geom(pre, lvl, L0);
+    const float4 cen = make_float4((float)g.rx, (float)g.ry, (float)g.rz, (float)g.side);
     o.cen[p] = cen;
-    o.com[p] = com;
     o.link[p] = make_int4((int)t.skip[p], (int)f, (int)c, nch == 0);
     o.level[p] = (uint8_t)lvl;
     o.prefix[p] = pre;
     o.bcen[q] = cen;
-    o.bcom[q] = com;
     o.blink[q] = make_int4(nch ? (int)pre2bfs[p + 1] : 0, (int)nch, (int)f, (int)c);
-    if (hmx) {  // largest softening, negative when the node mixes softenings
-        const float v = hmn[q] < hmx[q] ? -hmx[q] : hmx[q];
-        o.nsoft[p] = v;
-        o.bsoft[q] = v;
-    }
-    if (nch == 0) {  // leaf particles relative to the leaf centre (FP64 difference -> FP32)
+    if (nch == 0) {
         const double ax = __dadd_rn(x0, (double)cen.x), ay = __dadd_rn(y0, (double)cen.y),
                      az = __dadd_rn(z0, (double)cen.z);
         for (uint32_t s = f; s < f + c; s++)
             o.spart[s] = make_float4((float)__dsub_rn(spos[3 * s], ax), (float)__dsub_rn(spos[3 * s + 1], ay),
                                      (float)__dsub_rn(spos[3 * s + 2], az), smass[s]);
+    }
+}
+
+// K5b: centre of mass relative to the exact geometric centre (FP32) and mass,
+// pre-order and breadth-first, and the largest softening per node (negative
+// when the node mixes softenings).  S / m is S times the correctly rounded
+// 1 / m: one FP64 reciprocal instead of three divisions; the FP64 product is
+// within an ulp of the quotient, far below the FP32 rounding of the offset.
+__global__ void k_com(NodeArrays t, const uint32_t *__restrict__ pre2bfs, int64_t total,
+                      const double *__restrict__ M, const double *__restrict__ S, const float *__restrict__ hmx,
+                      const float *__restrict__ hmn, double x0, double y0, double z0, double L0, NodeOut o) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (p >= total)
+        return;
+    const uint32_t q = pre2bfs[p];
+    const NodeGeom g = node_geom(t.prefix[p], t.level[p], L0);
+    const double m = M[q];
+    const double rm = __drcp_rn(m);
+    const double cx = __dmul_rn(S[3 * q], rm), cy = __dmul_rn(S[3 * q + 1], rm), cz = __dmul_rn(S[3 * q + 2], rm);
+    const float4 com = make_float4((float)__dsub_rn(cx, __dadd_rn(x0, g.rx)), (float)__dsub_rn(cy, __dadd_rn(y0, g.ry)),
+                                   (float)__dsub_rn(cz, __dadd_rn(z0, g.rz)), (float)m);
+    o.com[p] = com;
+    o.bcom[q] = com;
+    if (hmx) {
+        const float v = hmn[q] < hmx[q] ? -hmx[q] : hmx[q];
+        o.nsoft[p] = v;
+        o.bsoft[q] = v;
     }
 }
 
@@ -723,7 +745,9 @@ int build_tree_device(Ctx *c, System *s, const double *pos_in, const float *mass
     count_launch();
     TPM_CUDA(cudaGetLastError());
 
-    // ---- monopoles (and softening extremes), bottom-up in one pass
+    // ---- walk tables and monopoles.  The tables that need no monopole go on
+    // the context's side stream while the monopole pass climbs (its last
+    // levels leave most SMs idle); the centres of mass follow both.
     float *hmx = nullptr, *hmn = nullptr;
     if (s->psoft) {
         TPM_CHECK(tmp.get(&hmx, nn, st));
@@ -731,11 +755,6 @@ int build_tree_device(Ctx *c, System *s, const double *pos_in, const float *mass
         TPM_CHECK(s->mem.get(&s->nsoft, nn, st));
         TPM_CHECK(s->mem.get(&s->bsoft, nn, st));
     }
-    k_multipole<<<blocks_for(nn), kThreads, 0, st>>>(t, nn, pre2bfs, spos, smass, M, S, s->psoft, hmx, hmn);
-    count_launch();
-    TPM_CUDA(cudaGetLastError());
-
-    // ---- walk tables
     TPM_CHECK(s->mem.get(&s->ncen, nn, st));
     TPM_CHECK(s->mem.get(&s->ncom, nn, st));
     TPM_CHECK(s->mem.get(&s->nlink, nn, st));
@@ -746,8 +765,22 @@ int build_tree_device(Ctx *c, System *s, const double *pos_in, const float *mass
     TPM_CHECK(s->mem.get(&s->blink, nn, st));
     NodeOut o{s->ncen, s->ncom,  s->nlink, s->nlevel, s->nprefix, s->bcen,
               s->bcom, s->blink, s->spart, s->nsoft,  s->bsoft};
-    k_finalize<<<blocks_for(nn), kThreads, 0, st>>>(t, pre2bfs, nn, M, S, spos, smass, hmx, hmn, s->x0[0], s->x0[1],
-                                                    s->x0[2], s->L0, o);
+    TPM_CUDA(cudaEventRecord(c->ev_fork, st));
+    TPM_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    k_tables<<<blocks_for(nn), kThreads, 0, c->side>>>(t, pre2bfs, nn, spos, smass, s->x0[0], s->x0[1], s->x0[2],
+                                                       s->L0, o);
+    const cudaError_t e_tab = cudaGetLastError();
+    const cudaError_t e_join = cudaEventRecord(c->ev_join, c->side);
+    k_multipole<<<blocks_for(nn), kThreads, 0, st>>>(t, nn, pre2bfs, spos, smass, M, S, s->psoft, hmx, hmn);
+    const cudaError_t e_mp = cudaGetLastError();
+    // st waits for the side stream before anything (the scratch frees among
+    // them) follows on it
+    TPM_CUDA(cudaStreamWaitEvent(st, c->ev_join, 0));
+    TPM_CUDA(e_tab);
+    TPM_CUDA(e_join);
+    TPM_CUDA(e_mp);
+    count_launch(2);
+    k_com<<<blocks_for(nn), kThreads, 0, st>>>(t, pre2bfs, nn, M, S, hmx, hmn, s->x0[0], s->x0[1], s->x0[2], s->L0, o);
     count_launch();
     TPM_CUDA(cudaGetLastError());
     return TPM_OK;

@@ -227,10 +227,22 @@ int tpm_create(tpm_ctx **out, int device, size_t budget) {
     uint64_t thr = UINT64_MAX;
     cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &thr);
     e = cudaMallocHost(&c->pinned_state, kPinnedStateBytes);
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
     if (e != cudaSuccess) {
+        if (c->ev_fork)
+            cudaEventDestroy(c->ev_fork);
+        if (c->side)
+            cudaStreamDestroy(c->side);
+        if (c->pinned_state)
+            cudaFreeHost(c->pinned_state);
         cudaMemPoolDestroy(c->pool);
         delete c;
-        set_error("cudaMallocHost: %s", cudaGetErrorString(e));
+        set_error("context setup: %s", cudaGetErrorString(e));
         return TPM_ECUDA;
     }
     *out = reinterpret_cast<tpm_ctx *>(c);
@@ -261,6 +273,9 @@ int tpm_destroy(tpm_ctx *h) {
     cudaStreamSynchronize(0);
     cudaMemPoolDestroy(c->pool);
     cudaFreeHost(c->pinned_state);
+    cudaEventDestroy(c->ev_fork);
+    cudaEventDestroy(c->ev_join);
+    cudaStreamDestroy(c->side);
     delete c;
     return TPM_OK;
 }

@@ -152,6 +152,10 @@ struct Ctx {
     int device = 0;
     void *pinned_state = nullptr;  // host page for a build's device-side bookkeeping
     std::mutex build_mu;
+    // side stream of the tree build (work that overlaps the monopole pass) and
+    // its fork / join events; used under build_mu
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int num_sms = 0;
     size_t budget = 0;
     size_t used = 0;
