@@ -69,6 +69,35 @@ void ctx_free(Ctx *c, void *p, size_t bytes, cudaStream_t st) {
 
 namespace {
 
+// Host argument checks: a branch-free pass over fixed-size blocks (which the
+// compiler vectorises), and a scan of the one block that fails for the index
+// reported.  The index of the first failing element, or -1.
+constexpr int64_t kCheckBlock = 4096;
+
+template <class Bad, class T>
+int64_t first_failing(const T *x, int64_t n, Bad bad) {
+    int64_t b = 0;
+    for (; b + kCheckBlock <= n; b += kCheckBlock) {
+        const T *blk = x + b;
+        unsigned any = 0u;
+        for (int64_t k = 0; k < kCheckBlock; k++)
+            any |= bad(blk[k]) ? 1u : 0u;
+        if (any)
+            break;
+    }
+    for (int64_t k = b; k < n; k++)
+        if (bad(x[k]))
+            return k;
+    return -1;
+}
+
+// non-finite: all exponent bits set (infinity or NaN)
+inline bool nonfinite_bits(float v) {
+    uint32_t u;
+    memcpy(&u, &v, sizeof u);
+    return (u & 0x7f800000u) == 0x7f800000u;
+}
+
 bool is_device_ptr(const void *p) {
     if (!p)
         return false;
@@ -465,18 +494,21 @@ int tpm_compute_forces(tpm_ctx *h, tpm_sys sid, const uint32_t *active_ids, int6
 
     const bool ids_dev = is_device_ptr(active_ids), aold_dev = is_device_ptr(a_old);
     const bool acc_dev = is_device_ptr(acc), pot_dev = is_device_ptr(pot), nint_dev = is_device_ptr(n_int);
-    if (active_ids && !ids_dev)
-        for (int64_t k = 0; k < n_active; k++)
-            if (active_ids[k] >= (uint64_t)s->n) {
-                set_error("active_ids[%lld] = %u out of range", (long long)k, active_ids[k]);
-                return TPM_EINVAL;
-            }
-    if (a_old && !aold_dev && p->crit == TPM_CRIT_RELATIVE)
-        for (int64_t k = 0; k < n_active; k++)
-            if (!std::isfinite(a_old[k])) {
-                set_error("a_old[%lld] is not finite", (long long)k);
-                return TPM_ENAN;
-            }
+    if (active_ids && !ids_dev) {
+        const uint32_t lim = (uint32_t)s->n;  // n < 2^31 (checked when the tree was built)
+        const int64_t k = first_failing(active_ids, n_active, [lim](uint32_t v) { return v >= lim; });
+        if (k >= 0) {
+            set_error("active_ids[%lld] = %u out of range", (long long)k, active_ids[k]);
+            return TPM_EINVAL;
+        }
+    }
+    if (a_old && !aold_dev && p->crit == TPM_CRIT_RELATIVE) {
+        const int64_t k = first_failing(a_old, n_active, nonfinite_bits);
+        if (k >= 0) {
+            set_error("a_old[%lld] is not finite", (long long)k);
+            return TPM_ENAN;
+        }
+    }
 
     AllocSet tmp;
     tmp.ctx = c;
