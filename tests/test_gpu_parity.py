@@ -292,6 +292,33 @@ def test_errors(tpm, ctx):
         s.release()
 
 
+def test_host_argument_checks_report_first_index(tpm, ctx):
+    """Host a_old and active ids are checked block by block; the error names
+    the first failing element, also past the first block and in the tail."""
+    E = tpm.TreePMError
+    n = 20000
+    pos, mass = W.plummer(n, 6)
+    s = ctx.build_tree(pos, mass, tpm.BuildParams())
+    ids = np.arange(n, dtype=np.uint32)
+    fp = tpm.ForceParams(crit=tpm.CRIT_RELATIVE)
+    aold = np.full(n, np.finfo(np.float32).max, np.float32)  # large but finite
+    aold[::7] = np.float32(1e-42)  # subnormal, finite
+    s.compute_forces(active_ids=ids, a_old=aold, fp=fp)  # accepted
+    for bad_at in ([9001, 12288], [19999], [0, 5]):
+        a = aold.copy()
+        a[bad_at[0]] = np.nan
+        for k in bad_at[1:]:
+            a[k] = -np.inf
+        with pytest.raises(E, match=r"a_old\[%d\] is not finite" % bad_at[0]):
+            s.compute_forces(active_ids=ids, a_old=a, fp=fp)
+    for bad_at in ([17000, 17001], [4096], [19999]):
+        i = ids.copy()
+        i[bad_at] = n + np.arange(len(bad_at), dtype=np.uint32)
+        with pytest.raises(E, match=r"active_ids\[%d\] = %d out of range" % (bad_at[0], n)):
+            s.compute_forces(active_ids=i, fp=tpm.ForceParams())
+    s.release()
+
+
 def test_budget_admission_has_no_side_effects(tpm):
     small = tpm.Context(0, budget_bytes=8 << 20)
     pos, mass = W.hernquist(200000, 2)
