@@ -774,10 +774,12 @@ int build_tree_device(Ctx *c, System *s, const double *pos_in, const float *mass
     k_multipole<<<blocks_for(nn), kThreads, 0, st>>>(t, nn, pre2bfs, spos, smass, M, S, s->psoft, hmx, hmn);
     const cudaError_t e_mp = cudaGetLastError();
     // st waits for the side stream before anything (the scratch frees among
-    // them) follows on it
-    TPM_CUDA(cudaStreamWaitEvent(st, c->ev_join, 0));
+    // them) follows on it; if that cannot be enqueued, the host waits instead
+    const cudaError_t e_wait = e_join == cudaSuccess ? cudaStreamWaitEvent(st, c->ev_join, 0) : e_join;
+    if (e_wait != cudaSuccess)
+        cudaStreamSynchronize(c->side);
     TPM_CUDA(e_tab);
-    TPM_CUDA(e_join);
+    TPM_CUDA(e_wait);
     TPM_CUDA(e_mp);
     count_launch(2);
     k_com<<<blocks_for(nn), kThreads, 0, st>>>(t, pre2bfs, nn, M, S, hmx, hmn, s->x0[0], s->x0[1], s->x0[2], s->L0, o);
