@@ -235,6 +235,18 @@ def test_walk_deterministic(tpm, ctx, torch_dev):
         s.release()
     for x, y in zip(outs[0], outs[1]):
         np.testing.assert_array_equal(x, y)
+    # periodic TreePM: the short-range walk over one mesh gives the same bits
+    # twice (the mesh itself is summed with float atomics, so it is formed once)
+    pos, mass = W.zeldovich(32, 8)
+    s = ctx.build_tree(to_dev(pos, torch_dev), to_dev(mass, torch_dev),
+                       tpm.BuildParams(G=1.0, h=(1 / 32) / 40, periodic=True, box=1.0, shift=tuple(W.root_shift(8)),
+                                       leaf_bucket=8))
+    fp = tpm.ForceParams(crit=tpm.CRIT_BH, theta=0.5, treepm=True, pm_n=32, asmth=1.25, rcut=4.5)
+    s.pm_long_range(fp)
+    outs = [tuple(x.cpu().numpy() for x in s.compute_forces(fp=fp)) for _ in range(2)]
+    s.release()
+    for x, y in zip(outs[0], outs[1]):
+        np.testing.assert_array_equal(x, y)
 
 
 def test_theta_zero_is_direct_sum(oracle_mod, tpm, ctx, torch_dev):
