@@ -59,7 +59,8 @@ typedef enum {
     TPM_EBUDGET = -2,          /* admission refused: the call would exceed the HBM budget; no side effects */
     TPM_ENOSYS_HANDLE = -3,    /* unknown or released system handle */
     TPM_ECUDA = -4,            /* a CUDA runtime / cuFFT call failed; the message names it */
-    TPM_ETIMEDOUT = -5,        /* a bounded device wait gave up; the context stays usable */
+    TPM_ETIMEDOUT = -5,        /* reserved: no kernel of this library waits on another block or on a
+                                  flag, so no call returns it */
     TPM_ENAN = -6              /* non-finite input (position, mass, |a_old|) */
 } tpm_status;
 
