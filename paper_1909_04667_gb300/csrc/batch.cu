@@ -56,6 +56,10 @@ struct Plan {
     bool staged_pending = false;
 };
 
+// Per request (one block each): the sorted position of every requested id in
+// its own tree; either directly the walk's sorted index (requests given in key
+// order) or a (request, sorted position) sort key with the id's slot.  An id
+// out of range sets bit 0 of the status word and is read as particle 0.
 __global__ void k_batch_keys(const KeyReq *__restrict__ kr, const int64_t *__restrict__ off,
                              const uint32_t *__restrict__ ids, int presorted, uint64_t *__restrict__ keys,
                              uint32_t *__restrict__ vals, uint32_t *__restrict__ sidx, uint32_t *__restrict__ slot,
@@ -81,18 +85,22 @@ __global__ void k_batch_keys(const KeyReq *__restrict__ kr, const int64_t *__res
     }
 }
 
+// Sorted (request, position) keys back to sorted positions.
 __global__ void k_batch_unpack(const uint64_t *__restrict__ skeys, int64_t n, uint32_t *__restrict__ sidx) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n)
         sidx[i] = (uint32_t)skeys[i];
 }
 
+// Number of walk groups of at most g particles per request.
 __global__ void k_batch_gcount(const int64_t *__restrict__ off, int64_t n_req, int g, uint32_t *__restrict__ gcnt) {
     const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (r < n_req)
         gcnt[r] = (uint32_t)((off[r + 1] - off[r] + g - 1) / g);
 }
 
+// The group table of the persistent walk: (start, count, request, 0) for each
+// group of each request, from the scanned group counts; the total into ngroups.
 __global__ void k_batch_groups(const int64_t *__restrict__ off, const uint32_t *__restrict__ gcnt,
                                const uint32_t *__restrict__ goff, int64_t n_req, int g, uint4 *__restrict__ groups,
                                unsigned *__restrict__ ngroups) {

@@ -487,6 +487,7 @@ __global__ void k_multipole(NodeArrays t, int64_t total, const uint32_t *__restr
     }
 }
 
+// Inverse of the breadth-first -> pre-order map.
 __global__ void k_invert(const uint32_t *__restrict__ bfs2pre, int64_t total, uint32_t *__restrict__ pre2bfs) {
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q < total)

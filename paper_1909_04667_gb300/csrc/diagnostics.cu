@@ -30,6 +30,9 @@ __device__ __forceinline__ void block_sum(double (*sh)[kDiagThreads], double (&v
     }
 }
 
+// One partial of each diagnostic sum per block: a fixed grid-stride share of
+// the particles, summed per thread in index order and then over the block in
+// a fixed tree order, so the result does not depend on scheduling.
 __global__ void __launch_bounds__(kDiagThreads)
     k_diag_partial(const float *__restrict__ mass, const float *__restrict__ acc, const float *__restrict__ pot,
                    const double *__restrict__ vel, int64_t n, double *__restrict__ partial) {

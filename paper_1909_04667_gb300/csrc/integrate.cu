@@ -60,6 +60,8 @@ struct DueAt {
     }
 };
 
+// |a| of the selected particles' last force, in selection order (the relative
+// criterion's a_old for the coming force call).
 __global__ void k_gather_amag(const uint32_t *__restrict__ ids, const int *__restrict__ n_sel,
                               const float *__restrict__ amag, float *__restrict__ out) {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;

@@ -58,6 +58,9 @@ int scratch_on_device(int device, unsigned char **out) {
     return TPM_OK;
 }
 
+// Sort keys of the active set (sorted position of each id) and its slots, in
+// the no-allocation scratch; an id out of range sets bit 0 of the status word
+// and is read as particle 0.
 __global__ void k_noalloc_active_keys(const uint32_t *__restrict__ ids, int64_t n_act,
                                       const uint32_t *__restrict__ rank, int64_t n, uint32_t *__restrict__ keys,
                                       uint32_t *__restrict__ vals, int *__restrict__ bad) {

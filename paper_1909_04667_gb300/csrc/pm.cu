@@ -58,6 +58,10 @@ __device__ __forceinline__ void warp_add(float *__restrict__ rho, unsigned idx, 
         atomicAdd(&rho[idx], sum);
 }
 
+// CIC mass assignment (Sec. 3.3) onto the periodic ng^3 mesh: each particle,
+// taken in key order, adds its mass with trilinear weights to the 8 mesh
+// points around it (mesh points at i / cells_per_len, wrapped), one float
+// atomic per point.
 __global__ void k_cic_deposit(const double *__restrict__ pos, const float *__restrict__ mass,
                               const uint32_t *__restrict__ perm, int64_t n, int ng, double cells_per_len,
                               float *__restrict__ rho) {
@@ -181,6 +185,8 @@ __global__ void k_iso_kernel(float *__restrict__ g, int n2, double asmth) {
     }
 }
 
+// Real parts of a complex array (the transform of the real, even isolated
+// kernel).
 __global__ void k_real_part(const cufftComplex *__restrict__ spec, int64_t nspec, float *__restrict__ out) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nspec;
          e += (int64_t)gridDim.x * blockDim.x)

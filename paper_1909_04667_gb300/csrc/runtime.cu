@@ -175,6 +175,9 @@ int check_force_params(const System *s, const tpm_force_params *p) {
     return TPM_OK;
 }
 
+// Sort keys of the active set: each id's sorted position in the tree, with its
+// slot in the caller's order.  An id out of range sets bit 0 of the system's
+// status word and is read as particle 0, so every access stays in bounds.
 __global__ void k_active_keys(const uint32_t *__restrict__ ids, int64_t n_act, const uint32_t *__restrict__ rank,
                               int64_t n, uint32_t *__restrict__ keys, uint32_t *__restrict__ vals,
                               int *__restrict__ bad) {
