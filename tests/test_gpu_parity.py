@@ -142,6 +142,41 @@ def test_walk_bh_plummer(oracle_mod, tpm, ctx, torch_dev, bucket):
     np.testing.assert_allclose(pot, p_o, rtol=2e-5)
 
 
+def test_depth_cap_with_far_outlier(oracle_mod, tpm, ctx, torch_dev):
+    """One particle 10^7 scale lengths out makes the root cube 2^24 wide, so a
+    level-21 cell (the depth cap) is 8 wide and holds a large share of the
+    Plummer core: leaves of ~500 particles, far beyond the bucket of 8, and a
+    walk that is nearly a direct sum.  The tree equals the oracle's bit for
+    bit and every interaction count agrees.  The forces agree for every
+    particle except the 31 that share the outlier's 32-particle walk group:
+    their offsets are rounded to FP32 in that group's 2^24-wide frame (a
+    limit of the group frame, measured at up to 1.75 relative error there)."""
+    n = 4096
+    pos, mass = W.plummer(n, 77)
+    pos[-1] = [1.0e7, 0.0, 0.0]
+    shift = tuple(W.root_shift(77))
+    s = ctx.build_tree(to_dev(pos, torch_dev), to_dev(mass, torch_dev),
+                       tpm.BuildParams(G=1.0, h=0.01, shift=shift, leaf_bucket=8))
+    ex = s.tree_export()
+    ref = oracle_mod.Tree(pos, mass, bucket=8, shift=shift)
+    rx = ref.export()
+    assert ex["n_nodes"] == ref.nnodes and ex["L0"] == ref.L0
+    for k in ("key", "perm", "level", "prefix", "first", "count", "skip", "mass", "com"):
+        np.testing.assert_array_equal(ex[k], rx[k], err_msg=k)
+    assert ex["count"][ex["level"] == 21].max() > 400
+    # walk groups are 32 consecutive particles in key order (all active)
+    chunk = np.empty(n, np.int64)
+    chunk[ex["perm"].astype(np.int64)] = np.arange(n) // 32
+    ok = chunk != chunk[n - 1]
+    acc, pot, nint = s.compute_forces(fp=tpm.ForceParams(crit=tpm.CRIT_BH, theta=0.5))
+    s.sync_status()
+    s.release()
+    a_o, p_o, n_o = ref.walk(np.arange(n), 1.0, 0.01, theta=0.5)
+    nint = nint.cpu().numpy()
+    np.testing.assert_array_equal(nint, n_o)
+    compare_forces(acc.cpu().numpy().astype(np.float64)[ok], a_o[ok], nint[ok], n_o[ok])
+
+
 def test_walk_relative_hernquist(oracle_mod, tpm, ctx, torch_dev):
     n = 1 << 16
     pos, mass = W.hernquist(n, 1002)
