@@ -163,6 +163,25 @@ def test_walk_box_guard_never_accepts_own_node(oracle_mod):
     assert np.all(np.isfinite(a)) and np.all(n >= 1)
 
 
+@pytest.mark.parametrize("off,nint_guard", [(0.55, 4), (0.59, 4), (0.61, 3), (0.65, 3)])
+def test_walk_box_guard_is_1_2_L(oracle_mod, off, nint_guard):
+    # Sec. 3.1: a node is opened when the particle lies inside a cube of side
+    # 1.2 L about the node's geometric centre, whatever the opening angle.  The
+    # anchors fix the root (x0 = 0, L0 = 128); the pair at (65..66)^3 forms the
+    # level-5 node [64, 68)^3 (centre 66, side 4); the probe sits at
+    # x = 66 + off * 4 in its own leaf.  With theta = 100 only the guard can
+    # open the pair's node: 2 anchors + 2 pair particles when opened, 2 + 1
+    # monopole when not; without the guard the whole root is one monopole.
+    pos = np.array([[0, 0, 0], [100, 100, 100], [65, 65, 65], [66, 66, 66], [66 + off * 4, 66, 66]], float)
+    mass = np.full(5, 0.2, np.float32)
+    tree = oracle_mod.Tree(pos, mass, bucket=1, shift=(0.0, 0.0, 0.0))
+    assert list(tree.x0) == [0.0, 0.0, 0.0] and tree.L0 == 128.0
+    _, _, n = tree.walk([4], 1.0, 1e-3, theta=100.0, box_guard=True)
+    assert n[0] == nint_guard
+    _, _, n = tree.walk([4], 1.0, 1e-3, theta=100.0, box_guard=False)
+    assert n[0] == 1
+
+
 # ------------------------------------------------------------------ Ewald
 def test_ewald_splitting_independent(oracle_mod):
     pos, mass = W.zeldovich(8, 4, rms_frac=0.3)
