@@ -182,6 +182,23 @@ def test_walk_box_guard_is_1_2_L(oracle_mod, off, nint_guard):
     assert n[0] == 1
 
 
+@pytest.mark.parametrize("theta,nint", [(0.25, 4), (0.27, 3), (0.29, 3)])
+def test_walk_bh_distance_is_to_the_centre_of_mass(oracle_mod, theta, nint):
+    # Sec. 3.1 (reading A5): the geometric criterion compares L with theta
+    # times the distance to the node's centre of mass, not to its geometric
+    # centre.  The level-5 node [64, 68)^3 (side 4) holds a heavy particle
+    # near its -x face and a light one near its +x face; from the probe at
+    # x = 80, L / d is 0.258 to the centre of mass and 0.285 to the centre, so
+    # theta = 0.27 accepts the node (3 interactions: 2 anchors + 1 monopole)
+    # only under the centre-of-mass reading; the box guard is off.
+    pos = np.array([[0, 0, 0], [100, 100, 100], [64.5, 66.5, 66.5], [67.5, 66.5, 66.5], [80.0, 66.5, 66.5]], float)
+    mass = np.array([1e-6, 1e-6, 1.0, 1e-3, 1e-6], np.float32)
+    tree = oracle_mod.Tree(pos, mass, bucket=1, shift=(0.0, 0.0, 0.0))
+    assert list(tree.x0) == [0.0, 0.0, 0.0] and tree.L0 == 128.0
+    _, _, n = tree.walk([4], 1.0, 1e-3, theta=theta, box_guard=False)
+    assert n[0] == nint
+
+
 # ------------------------------------------------------------------ Ewald
 def test_ewald_splitting_independent(oracle_mod):
     pos, mass = W.zeldovich(8, 4, rms_frac=0.3)
