@@ -199,6 +199,26 @@ def test_walk_bh_distance_is_to_the_centre_of_mass(oracle_mod, theta, nint):
     assert n[0] == nint
 
 
+@pytest.mark.parametrize("f,nint", [(0.99, 4), (1.01, 3)])
+def test_relative_criterion_threshold(oracle_mod, f, nint):
+    # Sec. 3.1: the relative criterion opens a node when G M L^2 exceeds
+    # alpha |a_old| d^4 (d to the centre of mass, reading A6).  For the same
+    # level-5 node as above (M = 1.001, L = 4) seen from x = 80 with G = 2 and
+    # |a_old| = 1 the decision flips at alpha* = G M L^2 / d^4: just below it
+    # the node is opened (4 interactions), just above it accepted (3).  A d^2,
+    # a missing G or a missing M would move alpha* by far more than 1%.
+    pos = np.array([[0, 0, 0], [100, 100, 100], [64.5, 66.5, 66.5], [67.5, 66.5, 66.5], [80.0, 66.5, 66.5]], float)
+    mass = np.array([1e-6, 1e-6, 1.0, 1e-3, 1e-6], np.float32)
+    tree = oracle_mod.Tree(pos, mass, bucket=1, shift=(0.0, 0.0, 0.0))
+    M = float(mass[2]) + float(mass[3])
+    com = (pos[2] * float(mass[2]) + pos[3] * float(mass[3])) / M
+    d = np.linalg.norm(pos[4] - com)
+    G = 2.0
+    alpha_star = G * M * 4.0 ** 2 / d ** 4
+    _, _, n = tree.walk([4], G, 1e-3, crit="rel", alpha=f * alpha_star, a_old=np.array([1.0], np.float32))
+    assert n[0] == nint
+
+
 # ------------------------------------------------------------------ Ewald
 def test_ewald_splitting_independent(oracle_mod):
     pos, mass = W.zeldovich(8, 4, rms_frac=0.3)
