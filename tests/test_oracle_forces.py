@@ -219,6 +219,20 @@ def test_relative_criterion_threshold(oracle_mod, f, nint):
     assert n[0] == nint
 
 
+@pytest.mark.parametrize("rcut,nint", [(11.9, 0), (12.1, 1), (15.0, 1)])
+def test_treepm_cutoff_uses_the_distance_to_the_cube(oracle_mod, rcut, nint):
+    # Sec. 3.4 (reading A9): a node is skipped when the particle's smallest
+    # distance to the node's cube exceeds r_cut.  The level-5 node [64, 68)^3
+    # is 12 from the probe at x = 80 (its centre of mass 15.5, its centre 14.0);
+    # at theta = 0.4 the nodes above it open and it is accepted, so it adds one
+    # interaction for any r_cut above 12 and none below.
+    pos = np.array([[0, 0, 0], [100, 100, 100], [64.5, 66.5, 66.5], [67.5, 66.5, 66.5], [80.0, 66.5, 66.5]], float)
+    mass = np.array([1e-6, 1e-6, 1.0, 1e-3, 1e-6], np.float32)
+    tree = oracle_mod.Tree(pos, mass, bucket=1, shift=(0.0, 0.0, 0.0))
+    _, _, n = tree.walk([4], 1.0, 1e-3, theta=0.4, treepm=True, rs=rcut / 4.5, rcut=rcut)
+    assert n[0] == nint
+
+
 # ------------------------------------------------------------------ Ewald
 def test_ewald_splitting_independent(oracle_mod):
     pos, mass = W.zeldovich(8, 4, rms_frac=0.3)
