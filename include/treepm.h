@@ -221,7 +221,11 @@ int tpm_compute_forces(tpm_ctx *ctx, tpm_sys s, const uint32_t *active_ids, int6
  *   - active_ids is required and n_active must lie in [1, TPM_NOALLOC_MAX_ACTIVE];
  *     larger sets are rejected with TPM_EINVAL;
  *   - every array (active_ids, a_old, acc, pot, n_int) must be device memory
- *     (host arrays would need staging buffers): TPM_EINVAL otherwise;
+ *     of the context's GPU (host arrays would need staging buffers):
+ *     TPM_EINVAL otherwise;
+ *   - ids are not checked on the host: an id >= n is read as particle 0 and
+ *     sets the system's status word, which the next tpm_sync_status reports
+ *     as TPM_EINVAL (as for device ids given to tpm_compute_forces);
  *   - the call is stream-ordered and never synchronises;
  *   - on a periodic system without treepm the context's Ewald table must
  *     exist already (any tpm_compute_forces call of that kind builds it):

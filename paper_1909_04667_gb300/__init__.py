@@ -346,6 +346,33 @@ def _dtype_check(x, name):
         raise TypeError("expected %s, got %s" % (name, dt))
 
 
+def _numel(x) -> int:
+    return int(x.size) if isinstance(x, np.ndarray) else int(x.numel())
+
+
+def _check_force_arrays(n_act, active_ids, a_old, acc, pot, n_int):
+    """Types and sizes of a force call's arrays (the C ABI takes bare pointers,
+    so an undersized output would be written past its end)."""
+    if active_ids is not None and str(active_ids.dtype).replace("torch.", "") not in ("uint32", "int32"):
+        raise TypeError("active_ids must be 32-bit indices, got %s" % active_ids.dtype)
+    if a_old is not None:
+        _dtype_check(a_old, "float32")
+        if _numel(a_old) < n_act:
+            raise ValueError("a_old holds %d values for %d active particles" % (_numel(a_old), n_act))
+    if acc is None or tuple(acc.shape) != (n_act, 3):
+        raise ValueError("acc must have shape (%d, 3)" % n_act)
+    _dtype_check(acc, "float32")
+    if pot is not None:
+        _dtype_check(pot, "float32")
+        if _numel(pot) < n_act:
+            raise ValueError("pot holds %d values for %d active particles" % (_numel(pot), n_act))
+    if n_int is not None:
+        if str(n_int.dtype).replace("torch.", "") not in ("uint32", "int32"):
+            raise TypeError("n_int must be 32-bit integers, got %s" % n_int.dtype)
+        if _numel(n_int) < n_act:
+            raise ValueError("n_int holds %d values for %d active particles" % (_numel(n_int), n_act))
+
+
 class System:
     """A resident particle system (``tpm_sys``)."""
 
@@ -370,10 +397,6 @@ class System:
 
         fp = fp or ForceParams()
         n_act = self.n if active_ids is None else int(active_ids.shape[0])
-        if active_ids is not None and str(active_ids.dtype).replace("torch.", "") not in ("uint32", "int32"):
-            raise TypeError("active_ids must be 32-bit indices, got %s" % active_ids.dtype)
-        if a_old is not None:
-            _dtype_check(a_old, "float32")
         dev = torch.device("cuda", self.ctx.device)
         if acc is None:
             acc = torch.empty((n_act, 3), dtype=torch.float32, device=dev)
@@ -381,6 +404,7 @@ class System:
             pot = torch.empty(n_act, dtype=torch.float32, device=dev)
         if n_int is None and want_nint:
             n_int = torch.empty(n_act, dtype=torch.int32, device=dev)
+        _check_force_arrays(n_act, active_ids, a_old, acc, pot, n_int)
         cp = fp._c()
         _check(_lib.tpm_compute_forces(self.ctx._h, self.handle, _ptr(active_ids), n_act, _ptr(a_old), C.byref(cp),
                                        _ptr(acc), _ptr(pot), _ptr(n_int), _stream(stream, self.ctx.device)))
@@ -394,6 +418,7 @@ class System:
         acc, pot and n_int); at most ``NOALLOC_MAX_ACTIVE`` active particles."""
         fp = fp or ForceParams()
         n_act = int(active_ids.shape[0])
+        _check_force_arrays(n_act, active_ids, a_old, acc, pot, n_int)
         cp = fp._c()
         _check(_lib.tpm_compute_forces_noalloc(self.ctx._h, self.handle, _ptr(active_ids), n_act, _ptr(a_old),
                                                C.byref(cp), _ptr(acc), _ptr(pot), _ptr(n_int),

@@ -22,12 +22,14 @@ namespace {
 
 constexpr int64_t kMaxActive = TPM_NOALLOC_MAX_ACTIVE;
 constexpr size_t kIdsBytes = (size_t)kMaxActive * sizeof(uint32_t);
-constexpr size_t kFlagBytes = 256;
-constexpr size_t kSortTempBytes = size_t(2) << 20;  // CUB radix-sort temporary storage
-constexpr size_t kScratchBytes = 4 * kIdsBytes + kFlagBytes + kSortTempBytes;
+// CUB radix-sort temporary storage.  The sort runs on double buffers (keys /
+// values and their alternates, all in the scratch), so CUB needs only its
+// histograms and look-back state here, not copies of the keys.
+constexpr size_t kSortTempBytes = size_t(2) << 20;
+constexpr size_t kScratchBytes = 4 * kIdsBytes + kSortTempBytes;
 
-// The shared scratch: keys, values, sorted keys, sorted values, an error flag
-// and the sort's temporary storage.  Host code must not pass this symbol to a
+// The shared scratch: keys, values, alternate keys, alternate values and the
+// sort's temporary storage.  Host code must not pass this symbol to a
 // kernel -- on the host it only names a stand-in; its device address comes
 // from cudaGetSymbolAddress (see scratch_on_device).
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
@@ -59,24 +61,26 @@ int scratch_on_device(int device, unsigned char **out) {
 }
 
 // Sort keys of the active set (sorted position of each id) and its slots, in
-// the no-allocation scratch; an id out of range sets bit 0 of the status word
-// and is read as particle 0.
+// the no-allocation scratch; an id out of range sets bit 0 of the system's
+// status word (which tpm_sync_status reports) and is read as particle 0.
 __global__ void k_noalloc_active_keys(const uint32_t *__restrict__ ids, int64_t n_act,
                                       const uint32_t *__restrict__ rank, int64_t n, uint32_t *__restrict__ keys,
-                                      uint32_t *__restrict__ vals, int *__restrict__ bad) {
+                                      uint32_t *__restrict__ vals, int *__restrict__ err) {
     int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= n_act)
         return;
     uint32_t id = ids[k];
     if (id >= (uint64_t)n) {
-        atomicOr(bad, 1);
+        atomicOr(err, 1);
         id = 0;
     }
     keys[k] = rank[id];
     vals[k] = (uint32_t)k;
 }
 
-bool on_device(const void *p) {
+// True for NULL, managed memory, and device memory of `device` (memory of
+// another GPU would be dereferenced from the wrong device).
+bool on_device(const void *p, int device) {
     if (!p)
         return true;
     cudaPointerAttributes a{};
@@ -84,7 +88,9 @@ bool on_device(const void *p) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged)
+        return true;
+    return a.type == cudaMemoryTypeDevice && a.device == device;
 }
 
 }  // namespace
@@ -130,8 +136,10 @@ extern "C" int tpm_compute_forces_noalloc(tpm_ctx *h, tpm_sys sid, const uint32_
         return TPM_EINVAL;
     }
     TPM_CUDA(cudaSetDevice(c->device));
-    if (!on_device(active_ids) || !on_device(a_old) || !on_device(acc) || !on_device(pot) || !on_device(n_int)) {
-        set_error("all arrays must be device memory: host arrays would need staging buffers");
+    const int dv = c->device;
+    if (!on_device(active_ids, dv) || !on_device(a_old, dv) || !on_device(acc, dv) || !on_device(pot, dv) ||
+        !on_device(n_int, dv)) {
+        set_error("all arrays must be device memory of the context's GPU: host arrays would need staging buffers");
         return TPM_EINVAL;
     }
     unsigned char *base = nullptr;
@@ -139,33 +147,33 @@ extern "C" int tpm_compute_forces_noalloc(tpm_ctx *h, tpm_sys sid, const uint32_
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     uint32_t *keys = reinterpret_cast<uint32_t *>(base);
     uint32_t *vals = reinterpret_cast<uint32_t *>(base + kIdsBytes);
-    uint32_t *skeys = reinterpret_cast<uint32_t *>(base + 2 * kIdsBytes);
-    uint32_t *svals = reinterpret_cast<uint32_t *>(base + 3 * kIdsBytes);
-    int *bad = reinterpret_cast<int *>(base + 4 * kIdsBytes);
-    void *sort_tmp = base + 4 * kIdsBytes + kFlagBytes;
+    uint32_t *akeys = reinterpret_cast<uint32_t *>(base + 2 * kIdsBytes);
+    uint32_t *avals = reinterpret_cast<uint32_t *>(base + 3 * kIdsBytes);
+    void *sort_tmp = base + 4 * kIdsBytes;
 
     int bits = 1;
     while ((int64_t(1) << bits) < s->n)
         bits++;
+    // every buffer is written before it is read, so nothing in the shared
+    // scratch needs clearing; the result ends in either half of each pair
+    cub::DoubleBuffer<uint32_t> dk(keys, akeys), dvv(vals, avals);
     size_t need = 0;
-    TPM_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, need, keys, skeys, vals, svals, (int)n_active, 0, bits, st));
+    TPM_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, need, dk, dvv, (int)n_active, 0, bits, st));
     if (need > kSortTempBytes) {
         set_error("sort needs %zu bytes of temporary storage, the no-allocation scratch has %zu", need,
                   kSortTempBytes);
         return TPM_EINVAL;
     }
-    // the scratch keeps the previous call's contents: the error flag must start at zero
-    TPM_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
     k_noalloc_active_keys<<<(unsigned)((n_active + 255) / 256), 256, 0, st>>>(active_ids, n_active, s->rank, s->n,
-                                                                             keys, vals, bad);
+                                                                             keys, vals, s->err);
     count_launch();
     TPM_CUDA(cudaGetLastError());
-    TPM_CUDA(cub::DeviceRadixSort::SortPairs(sort_tmp, need, keys, skeys, vals, svals, (int)n_active, 0, bits, st));
+    TPM_CUDA(cub::DeviceRadixSort::SortPairs(sort_tmp, need, dk, dvv, (int)n_active, 0, bits, st));
     count_cub_call();
 
     WalkRequest r{};
-    r.sorted_idx = skeys;
-    r.slot = svals;
+    r.sorted_idx = dk.Current();
+    r.slot = dvv.Current();
     r.a_old = p->crit == TPM_CRIT_RELATIVE ? a_old : nullptr;
     r.n_act = n_active;
     r.acc = acc;

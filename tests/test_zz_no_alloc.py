@@ -57,6 +57,65 @@ def test_noalloc_matches_compute_forces_two_calls():
     ctx.close()
 
 
+def test_noalloc_at_the_maximum_size():
+    """Exactly TPM_NOALLOC_MAX_ACTIVE ids: the sort's temporary storage fits
+    the fixed array (the sort runs on double buffers), results as the plain
+    call's."""
+    import torch
+
+    import paper_1909_04667_gb300 as tpm
+
+    dev = torch.device("cuda", 0)
+    ctx = tpm.Context(0)
+    n = tpm.NOALLOC_MAX_ACTIVE + 4097
+    pos, mass = W.hernquist(n, 22)
+    s = ctx.build_tree(torch.from_numpy(pos).to(dev), torch.from_numpy(mass).to(dev),
+                       tpm.BuildParams(G=1.0, h=0.005, shift=tuple(W.root_shift(22)), leaf_bucket=8))
+    rng = np.random.default_rng(6)
+    ids = torch.from_numpy(rng.permutation(n)[:tpm.NOALLOC_MAX_ACTIVE].astype(np.int32)).to(dev)
+    fp = tpm.ForceParams(crit=tpm.CRIT_BH, theta=0.5)
+    ref_acc, ref_pot, ref_n = s.compute_forces(active_ids=ids, fp=fp)
+    acc = torch.full((len(ids), 3), float("nan"), device=dev)
+    pot = torch.full((len(ids),), float("nan"), device=dev)
+    n_int = torch.zeros(len(ids), dtype=torch.int32, device=dev)
+    s.compute_forces_noalloc(ids, acc, fp=fp, pot=pot, n_int=n_int)
+    s.sync_status()
+    assert close(acc.cpu().numpy(), ref_acc.cpu().numpy())
+    np.testing.assert_allclose(pot.cpu().numpy(), ref_pot.cpu().numpy(), rtol=P99_TOL)
+    np.testing.assert_array_equal(n_int.cpu().numpy(), ref_n.cpu().numpy())
+    s.release()
+    ctx.close()
+
+
+def test_noalloc_reports_an_out_of_range_id():
+    """An id >= n in device memory (built on the host, so nothing faults) is
+    read as particle 0 and reported by the next sync_status, as for the plain
+    call; the status word is cleared, and the next good call succeeds."""
+    import torch
+
+    import paper_1909_04667_gb300 as tpm
+
+    dev = torch.device("cuda", 0)
+    ctx = tpm.Context(0)
+    pos, mass = W.plummer(2000, 8)
+    s = ctx.build_tree(pos, mass, tpm.BuildParams())
+    ids_h = np.arange(0, 2000, 7, dtype=np.int32)
+    ids_h[5] = 2000  # one past the last particle
+    ids = torch.from_numpy(ids_h).to(dev)
+    acc = torch.empty((len(ids), 3), device=dev)
+    s.compute_forces_noalloc(ids, acc)
+    with pytest.raises(tpm.TreePMError, match="TPM_EINVAL.*out of range"):
+        s.sync_status()
+    ids_h[5] = 1999
+    ids = torch.from_numpy(ids_h).to(dev)
+    s.compute_forces_noalloc(ids, acc)
+    s.sync_status()
+    ref, _, _ = s.compute_forces(active_ids=ids)
+    assert close(acc.cpu().numpy(), ref.cpu().numpy())
+    s.release()
+    ctx.close()
+
+
 def test_noalloc_rejects_what_it_cannot_hold():
     import torch
 
@@ -73,5 +132,7 @@ def test_noalloc_rejects_what_it_cannot_hold():
     host_ids = np.arange(10, dtype=np.uint32)
     with pytest.raises(tpm.TreePMError, match="device memory"):
         s.compute_forces_noalloc(host_ids, torch.empty((10, 3), device=dev))
+    with pytest.raises(ValueError, match="acc must have shape"):
+        s.compute_forces_noalloc(torch.zeros(10, dtype=torch.int32, device=dev), torch.empty((9, 3), device=dev))
     s.release()
     ctx.close()
