@@ -20,6 +20,11 @@ LIB = os.path.join(PKG, "libtreepm.so")
 SOURCES = ["runtime.cu", "build.cu", "walk.cu", "pm.cu", "noalloc.cu", "batch.cu", "integrate.cu", "ewald.cu",
            "diagnostics.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# Per-file flags.  The walk flushes FP32 denormals to zero: its operands
+# (offsets, masses, r^-3 products) stay many orders of magnitude above the
+# denormal range, and without the flag each rsqrt and division carries a
+# denormal-handling path (measured 5% of the walk's time).
+FILE_FLAGS = {"walk.cu": ["-ftz=true"]}
 
 
 def _nvcc() -> str:
@@ -58,7 +63,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     for src in SOURCES:
         obj = os.path.join(OBJDIR, src.replace(".cu", ".o"))
         objs.append(obj)
-        cmds.append([nvcc, *_flags(extra_flags), "-c", os.path.join(CSRC, src), "-o", obj])
+        cmds.append([nvcc, *_flags(list(extra_flags) + FILE_FLAGS.get(src, [])), "-c", os.path.join(CSRC, src), "-o",
+                     obj])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -363,26 +363,75 @@ constexpr int kGroupWarps = 4;
 constexpr int kStackCap = 192;
 constexpr int kStackDepths[3] = {128, 192, 256};
 constexpr int kNodeFlush = 64;              // sweep once this many node entries are queued
-constexpr int kNodeCap = kNodeFlush + 32;   // one batch adds at most 32 (one per candidate)
+constexpr int kNodeCap = kNodeFlush + 32;   // one step adds at most 32 (one per lane)
 constexpr int kLeafFlush = 32;
-constexpr int kLeafCap = kLeafFlush + 64;
+constexpr int kLeafCap = kLeafFlush + 32;
+constexpr int kUndCap = 96;                 // nodes waiting for per-particle decisions
 constexpr uint32_t kLeafWrap = 0x80000000u, kLeafCount = 0x7fffffffu;
 enum { kSkip = 0, kAccept = 1, kOpen = 2, kMixed = 3, kNone = 4 };
 
-template <int STACK>
+template <int STACK, bool VARH, bool PERIODIC>
 struct GroupSharedT {
     static constexpr int kStack = STACK;
     static constexpr int kSafe = STACK - 64;  // above this, take one candidate at a time
     uint2 stack[STACK];  // (first child, lane mask)
     uint8_t scount[STACK];
-    float4 nsrc[kNodeCap];   // accepted node: centre of mass (group frame) + mass
-    float nsoft[kNodeCap];   // its largest spline support (per-particle softening only)
+    // accepted node e: centre of mass (group frame) and mass, stored by pairs
+    // of entries so that one 128-bit load feeds the two-wide FP32
+    // instructions: nxy[e / 2] = (x, x', y, y'), nzm[e / 2] = (z, z', m, m')
+    float4 nxy[kNodeCap / 2];
+    float4 nzm[kNodeCap / 2];
     uint32_t nmask[kNodeCap];
-    uint8_t nwrap[kNodeCap];
+    float nsoft[VARH ? kNodeCap : 1];      // its largest spline support (per-particle softening)
+    uint8_t nwrap[PERIODIC ? kNodeCap : 1];
     float4 lsrc[kLeafCap];   // opened leaf: centre (group frame) + first particle
     uint2 lmeta[kLeafCap];   // lane mask, wrap flag | particle count
-    uint2 cand[32];          // (node, lane mask)
+    uint2 und[kUndCap];      // node the group bounds left undecided, lane mask
+    // the group's particles by pairs: offset from the frame centre and
+    // criterion threshold, pxy[i] = (x, x', y, y'), pzt[i] = (z, z', t, t')
+    float4 pxy[16];
+    float4 pzt[16];
 };
+
+// Entry e of the node queue (paired layout).
+template <class SH>
+__device__ __forceinline__ float4 node_entry(const SH &sh, int e) {
+    const float *a = reinterpret_cast<const float *>(&sh.nxy[e >> 1]);
+    const float *b = reinterpret_cast<const float *>(&sh.nzm[e >> 1]);
+    const int o = e & 1;
+    return make_float4(a[o], a[2 + o], b[o], b[2 + o]);
+}
+
+template <class SH>
+__device__ __forceinline__ void put_node_entry(SH &sh, int e, float4 v) {
+    float *a = reinterpret_cast<float *>(&sh.nxy[e >> 1]);
+    float *b = reinterpret_cast<float *>(&sh.nzm[e >> 1]);
+    const int o = e & 1;
+    a[o] = v.x;
+    a[2 + o] = v.y;
+    b[o] = v.z;
+    b[2 + o] = v.w;
+}
+
+template <class SH>
+__device__ __forceinline__ void put_part_entry(SH &sh, int p, float4 v) {
+    float *a = reinterpret_cast<float *>(&sh.pxy[p >> 1]);
+    float *b = reinterpret_cast<float *>(&sh.pzt[p >> 1]);
+    const int o = p & 1;
+    a[o] = v.x;
+    a[2 + o] = v.y;
+    b[o] = v.z;
+    b[2 + o] = v.w;
+}
+
+// Particle p of the group (paired layout): offset and criterion threshold.
+template <class SH>
+__device__ __forceinline__ float4 part_entry(const SH &sh, int p) {
+    const float *a = reinterpret_cast<const float *>(&sh.pxy[p >> 1]);
+    const float *b = reinterpret_cast<const float *>(&sh.pzt[p >> 1]);
+    const int o = p & 1;
+    return make_float4(a[o], a[2 + o], b[o], b[2 + o]);
+}
 
 // Conservative decision for all particles inside [lo, hi] (group frame).
 template <bool PERIODIC, bool RELATIVE, bool TREEPM, bool VARH>
@@ -482,7 +531,7 @@ __device__ __forceinline__ void sweep_full(const SH &sh, int nf, float xox, floa
                                            const WalkConsts &k, float &ax, float &ay, float &az, float &ph) {
     if (TREEPM || PERIODIC) {
         for (int e = 0; e < nf; e++) {
-            const float4 A = sh.nsrc[e];
+            const float4 A = node_entry(sh, e);
             float rx = A.x - xox, ry = A.y - xoy, rz = A.z - xoz;
             if (PERIODIC && sh.nwrap[e]) {
                 rx = wrap_min_image(rx, k);
@@ -500,23 +549,35 @@ __device__ __forceinline__ void sweep_full(const SH &sh, int nf, float xox, floa
         return;
     }
     if (!VARH) {
+        // pairs of entries through the two-wide FP32 instructions, each
+        // element rounded as the scalar instruction would round it; the two
+        // halves of each sum are added at the end
         float rmin = __int_as_float(0x7f800000);
+        const float2 nx = make_float2(-xox, -xox), ny = make_float2(-xoy, -xoy), nz = make_float2(-xoz, -xoz);
+        float2 sx = make_float2(0.f, 0.f), sy = sx, sz = sx, sp = sx;
         int e = 0;
-        for (; e + 3 < nf; e += 4) {
-            float4 A[4];
-#pragma unroll
-            for (int u = 0; u < 4; u++)
-                A[u] = sh.nsrc[e + u];
-#pragma unroll
-            for (int u = 0; u < 4; u++) {
-                const float rx = A[u].x - xox, ry = A[u].y - xoy, rz = A[u].z - xoz;
-                const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-                rmin = fminf(rmin, r2);
-                newton_term(rx, ry, rz, fmaxf(r2, k.h2), A[u].w, ax, ay, az, ph);
-            }
+#pragma unroll 2
+        for (; e + 1 < nf; e += 2) {
+            const float4 XY = sh.nxy[e >> 1], ZM = sh.nzm[e >> 1];
+            const float2 rx = __fadd2_rn(make_float2(XY.x, XY.y), nx);
+            const float2 ry = __fadd2_rn(make_float2(XY.z, XY.w), ny);
+            const float2 rz = __fadd2_rn(make_float2(ZM.x, ZM.y), nz);
+            const float2 r2 = __ffma2_rn(rx, rx, __ffma2_rn(ry, ry, __fmul2_rn(rz, rz)));
+            rmin = fminf(rmin, fminf(r2.x, r2.y));
+            const float2 ri = make_float2(rsqrtf(fmaxf(r2.x, k.h2)), rsqrtf(fmaxf(r2.y, k.h2)));
+            const float2 mr = __fmul2_rn(make_float2(ZM.z, ZM.w), ri);
+            const float2 mr3 = __fmul2_rn(__fmul2_rn(mr, ri), ri);
+            sx = __ffma2_rn(mr3, rx, sx);
+            sy = __ffma2_rn(mr3, ry, sy);
+            sz = __ffma2_rn(mr3, rz, sz);
+            sp = __fadd2_rn(sp, mr);
         }
+        ax += sx.x + sx.y;
+        ay += sy.x + sy.y;
+        az += sz.x + sz.y;
+        ph -= sp.x + sp.y;
         for (; e < nf; e++) {
-            const float4 A = sh.nsrc[e];
+            const float4 A = node_entry(sh, e);
             const float rx = A.x - xox, ry = A.y - xoy, rz = A.z - xoz;
             const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
             rmin = fminf(rmin, r2);
@@ -524,7 +585,7 @@ __device__ __forceinline__ void sweep_full(const SH &sh, int nf, float xox, floa
         }
         if (__any_sync(0xffffffffu, rmin < k.h2)) {
             for (int q = 0; q < nf; q++) {
-                const float4 A = sh.nsrc[q];
+                const float4 A = node_entry(sh, q);
                 const float rx = A.x - xox, ry = A.y - xoy, rz = A.z - xoz;
                 const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
                 if (r2 < k.h2) {
@@ -541,7 +602,7 @@ __device__ __forceinline__ void sweep_full(const SH &sh, int nf, float xox, floa
         float4 A[4];
 #pragma unroll
         for (int u = 0; u < 4; u++)
-            A[u] = sh.nsrc[e + u];
+            A[u] = node_entry(sh, e + u);
 #pragma unroll
         for (int u = 0; u < 4; u++) {
             const float rx = A[u].x - xox, ry = A[u].y - xoy, rz = A[u].z - xoz;
@@ -557,7 +618,7 @@ __device__ __forceinline__ void sweep_full(const SH &sh, int nf, float xox, floa
         }
     }
     for (; e < nf; e++) {
-        const float4 A = sh.nsrc[e];
+        const float4 A = node_entry(sh, e);
         const float rx = A.x - xox, ry = A.y - xoy, rz = A.z - xoz;
         const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
         float h2 = k.h2;
@@ -571,7 +632,7 @@ __device__ __forceinline__ void sweep_full(const SH &sh, int nf, float xox, floa
     }
     if (__any_sync(0xffffffffu, soft)) {
         for (int q = 0; q < nf; q++) {
-            const float4 A = sh.nsrc[q];
+            const float4 A = node_entry(sh, q);
             const float rx = A.x - xox, ry = A.y - xoy, rz = A.z - xoz;
             const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
             if (VARH) {
@@ -596,7 +657,7 @@ __device__ __forceinline__ void sweep_partial(const SH &sh, int np, unsigned lan
     const int e0 = kNodeCap - np;
     if (TREEPM || PERIODIC) {
         for (int e = e0; e < kNodeCap; e++) {
-            const float4 E = sh.nsrc[e];
+            const float4 E = node_entry(sh, e);
             const bool mine = (sh.nmask[e] & lanebit) != 0u;
             float rx = E.x - xox, ry = E.y - xoy, rz = E.z - xoz;
             if (PERIODIC && sh.nwrap[e]) {
@@ -618,19 +679,45 @@ __device__ __forceinline__ void sweep_partial(const SH &sh, int np, unsigned lan
     }
     if (!VARH) {
         float rmin = __int_as_float(0x7f800000);
-#pragma unroll 2
-        for (int e = e0; e < kNodeCap; e++) {
-            const float4 E = sh.nsrc[e];
+        int e = e0;
+        if (e & 1) {  // an odd first entry, then aligned pairs (kNodeCap is even)
+            const float4 E = node_entry(sh, e);
             const bool mine = (sh.nmask[e] & lanebit) != 0u;
             const float rx = E.x - xox, ry = E.y - xoy, rz = E.z - xoz;
             const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
             rmin = fminf(rmin, r2);
             cnt += mine ? 1u : 0u;
             newton_term(rx, ry, rz, fmaxf(r2, k.h2), mine ? E.w : 0.0f, ax, ay, az, ph);
+            e++;
         }
+        const float2 nx = make_float2(-xox, -xox), ny = make_float2(-xoy, -xoy), nz = make_float2(-xoz, -xoz);
+        float2 sx = make_float2(0.f, 0.f), sy = sx, sz = sx, sp = sx;
+#pragma unroll 2
+        for (; e < kNodeCap; e += 2) {
+            const float4 XY = sh.nxy[e >> 1], ZM = sh.nzm[e >> 1];
+            const uint2 Mk = *reinterpret_cast<const uint2 *>(&sh.nmask[e]);
+            const bool m0 = (Mk.x & lanebit) != 0u, m1 = (Mk.y & lanebit) != 0u;
+            const float2 rx = __fadd2_rn(make_float2(XY.x, XY.y), nx);
+            const float2 ry = __fadd2_rn(make_float2(XY.z, XY.w), ny);
+            const float2 rz = __fadd2_rn(make_float2(ZM.x, ZM.y), nz);
+            const float2 r2 = __ffma2_rn(rx, rx, __ffma2_rn(ry, ry, __fmul2_rn(rz, rz)));
+            rmin = fminf(rmin, fminf(r2.x, r2.y));
+            cnt += (m0 ? 1u : 0u) + (m1 ? 1u : 0u);
+            const float2 ri = make_float2(rsqrtf(fmaxf(r2.x, k.h2)), rsqrtf(fmaxf(r2.y, k.h2)));
+            const float2 mr = __fmul2_rn(make_float2(m0 ? ZM.z : 0.0f, m1 ? ZM.w : 0.0f), ri);
+            const float2 mr3 = __fmul2_rn(__fmul2_rn(mr, ri), ri);
+            sx = __ffma2_rn(mr3, rx, sx);
+            sy = __ffma2_rn(mr3, ry, sy);
+            sz = __ffma2_rn(mr3, rz, sz);
+            sp = __fadd2_rn(sp, mr);
+        }
+        ax += sx.x + sx.y;
+        ay += sy.x + sy.y;
+        az += sz.x + sz.y;
+        ph -= sp.x + sp.y;
         if (__any_sync(0xffffffffu, rmin < k.h2)) {
             for (int e = e0; e < kNodeCap; e++) {
-                const float4 E = sh.nsrc[e];
+                const float4 E = node_entry(sh, e);
                 const float rx = E.x - xox, ry = E.y - xoy, rz = E.z - xoz;
                 const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
                 if ((sh.nmask[e] & lanebit) && r2 < k.h2) {
@@ -644,7 +731,7 @@ __device__ __forceinline__ void sweep_partial(const SH &sh, int np, unsigned lan
     bool soft = false;
 #pragma unroll 2
     for (int e = e0; e < kNodeCap; e++) {
-        const float4 E = sh.nsrc[e];
+        const float4 E = node_entry(sh, e);
         const bool mine = (sh.nmask[e] & lanebit) != 0u;
         const float rx = E.x - xox, ry = E.y - xoy, rz = E.z - xoz;
         const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
@@ -661,7 +748,7 @@ __device__ __forceinline__ void sweep_partial(const SH &sh, int np, unsigned lan
     }
     if (__any_sync(0xffffffffu, soft)) {
         for (int e = e0; e < kNodeCap; e++) {
-            const float4 E = sh.nsrc[e];
+            const float4 E = node_entry(sh, e);
             const float rx = E.x - xox, ry = E.y - xoy, rz = E.z - xoz;
             const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
             if (!(sh.nmask[e] & lanebit))
@@ -677,13 +764,65 @@ __device__ __forceinline__ void sweep_partial(const SH &sh, int np, unsigned lan
     }
 }
 
-// Sweeps the queued opened leaves, particle by particle.
+// Sweeps the queued opened leaves, particle by particle.  With open
+// boundaries and no split every pair first gets the Newtonian term at
+// max(r, h) (no branch: the pairs of a leaf are mostly for a few lanes, and
+// many lie inside the softening length); a leaf in which some lane met a
+// particle closer than its softening length is swept a second time, taking
+// those pairs' h-terms out again and adding their spline terms.
 template <bool PERIODIC, bool TREEPM, bool VARH, class SH>
 __device__ __forceinline__ void sweep_leaves(const SH &sh, int nl, unsigned lanebit, uint32_t self,
                                              float xox, float xoy, float xoz, float hi,
                                              const float4 *__restrict__ spart, const float *__restrict__ psoft,
                                              const WalkConsts &k, float &ax, float &ay, float &az, float &ph,
                                              uint32_t &cnt) {
+    if (!TREEPM && !PERIODIC) {
+        for (int e = 0; e < nl; e++) {
+            const float4 E = sh.lsrc[e];
+            const uint2 Mt = sh.lmeta[e];
+            const bool mine = (Mt.x & lanebit) != 0u;
+            // subtract the small particle-to-leaf-centre vector first so that
+            // close pairs keep their precision
+            const float px = xox - E.x, py = xoy - E.y, pz = xoz - E.z;
+            const int j0 = __float_as_int(E.w);
+            const int j1 = j0 + (int)(Mt.y & kLeafCount);
+            bool close = false;
+            for (int jj = j0; jj < j1; jj++) {
+                const float4 P = __ldg(&spart[jj]);
+                const float qx = P.x - px, qy = P.y - py, qz = P.z - pz;
+                const float q2 = fmaf(qx, qx, fmaf(qy, qy, qz * qz));
+                float h2 = k.h2;
+                if (VARH) {
+                    const float he = fmaxf(hi, __ldg(&psoft[jj]));
+                    h2 = he * he;
+                }
+                const bool use = mine && (uint32_t)jj != self;
+                close |= use && q2 < h2;
+                cnt += use ? 1u : 0u;
+                newton_term(qx, qy, qz, fmaxf(q2, h2), use ? P.w : 0.0f, ax, ay, az, ph);
+            }
+            if (__any_sync(0xffffffffu, close)) {
+                for (int jj = j0; jj < j1; jj++) {
+                    const float4 P = __ldg(&spart[jj]);
+                    const float qx = P.x - px, qy = P.y - py, qz = P.z - pz;
+                    const float q2 = fmaf(qx, qx, fmaf(qy, qy, qz * qz));
+                    float he = 0.0f, h2 = k.h2;
+                    if (VARH) {
+                        he = fmaxf(hi, __ldg(&psoft[jj]));
+                        h2 = he * he;
+                    }
+                    if (mine && (uint32_t)jj != self && q2 < h2) {
+                        newton_term(qx, qy, qz, h2, -P.w, ax, ay, az, ph);
+                        if (VARH)
+                            pair_term_h<false>(qx, qy, qz, q2, P.w, he, k, ax, ay, az, ph);
+                        else
+                            pair_term<false>(qx, qy, qz, q2, P.w, k, ax, ay, az, ph);
+                    }
+                }
+            }
+        }
+        return;
+    }
     for (int e = 0; e < nl; e++) {
         const float4 E = sh.lsrc[e];
         const uint2 Mt = sh.lmeta[e];
@@ -736,6 +875,16 @@ struct TreeView {
 
 // Walks the tree for the group of gcount <= 32 active particles at positions
 // [g0, g0 + gcount) of the sorted active list (one per lane).
+//
+// Candidates come from the stack 32 at a time and are classified one per
+// lane with the group bounds.  Nodes the bounds leave undecided wait in a
+// queue; once 32 wait (or the stack runs dry) they are decided particle by
+// particle with the loop transposed: each lane holds one waiting node and
+// runs through the group's particles (read from shared memory), so that one
+// pass of 32 iterations decides 32 nodes for all 32 particles.  Each
+// particle's decision is the per-particle walk's (the same FP32 arithmetic
+// as the lane walk); lanes that accept a node get its monopole through the
+// node queue, lanes that open it get its children or its leaf.
 template <bool PERIODIC, bool RELATIVE, bool TREEPM, bool VARH, class SH>
 __device__ __forceinline__ void group_walk(const TreeView &T, const WalkConsts &k, SH &sh,
                                            const uint32_t *__restrict__ sidx, const uint32_t *__restrict__ slot,
@@ -813,81 +962,214 @@ __device__ __forceinline__ void group_walk(const TreeView &T, const WalkConsts &
 
     float ax = 0.f, ay = 0.f, az = 0.f, ph = 0.f;
     uint32_t cnt = 0;
+    put_part_entry(sh, lane, make_float4(xox, xoy, xoz, thr));  // read by the transposed decisions
     if (lane == 0) {
         sh.stack[0] = make_uint2(0u, valid_mask);  // the root, breadth-first index 0
         sh.scount[0] = 1;
     }
-    int sn = 1, nf = 0, np = 0, nl = 0;
+    int sn = 1, nf = 0, np = 0, nl = 0, nu = 0;
     __syncwarp();
-    while (sn > 0) {
-        // ---- take up to 32 candidates from the top child ranges
-        const int cap = sn > SH::kSafe ? 1 : 32;
-        const int idx = sn - 1 - lane;
-        uint2 R = make_uint2(0u, 0u);
-        int c = 0;
-        if (idx >= 0) {
-            R = sh.stack[idx];
-            c = sh.scount[idx];
-        }
-        int incl = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(FULL, incl, o);
-            if (lane >= o)
-                incl += v;
-        }
-        const int excl = incl - c;
-        const bool take = idx >= 0 && c > 0 && excl < cap;
-        const bool whole = take && incl <= cap;
-        const int ntake = take ? min(c, cap - excl) : 0;
-        for (int t = 0; t < ntake; t++)
-            sh.cand[excl + t] = make_uint2(R.x + (uint32_t)t, R.y);
-        const int nwhole = __popc(__ballot_sync(FULL, whole));
-        const int ncand = min(__shfl_sync(FULL, incl, 31), cap);
-        if (take && !whole) {  // the partly taken range stays on top
-            sh.stack[idx].x = R.x + (uint32_t)ntake;
-            sh.scount[idx] = (uint8_t)(c - ntake);
-        }
-        sn -= nwhole;
-        __syncwarp();
-
-        // ---- one candidate per lane: decide for the whole group
+    for (;;) {
+        // once the stack and the undecided queue are empty, the queued
+        // monopoles and leaves are swept a last time and the walk ends (one
+        // copy of each sweep serves both)
+        const bool done = sn == 0 && nu == 0;
+        if (!done) {
+        // nodes waiting for per-particle decisions go first once a full batch
+        // waits (and the stack has room for what they may open), when the
+        // stack is empty, or when the queue could not take another batch
+        const int room = SH::kStack - 53 - sn;
+        const bool resolve = nu > 0 && (sn == 0 || (nu >= 32 && room >= 32) || nu > kUndCap - 33);
         int cls = kNone;
-        uint32_t nmask = 0;
+        uint32_t nmask = 0;  // lanes that need the node (resolution: lanes that open it)
+        uint32_t amask = 0;  // resolution: lanes that accept the node
         float4 C = make_float4(0.f, 0.f, 0.f, 0.f), O = C;
         int4 Lk = make_int4(0, 0, 0, 0);
         float dcx = 0.f, dcy = 0.f, dcz = 0.f;
         float hsig = 0.0f;  // the node's largest softening, negative when mixed
-        if (lane < ncand) {
-            const uint2 cd = sh.cand[lane];
-            nmask = cd.y;
-            C = __ldg(&bcen[cd.x]);
-            O = __ldg(&bcom[cd.x]);
-            Lk = __ldg(&blink[cd.x]);
-            if (VARH)
-                hsig = __ldg(&T.bsoft[cd.x]);
-            cls = classify_group<PERIODIC, RELATIVE, TREEPM, VARH>(C, O, gcx, gcy, gcz, lox, loy, loz, hix, hiy, hiz,
-                                                                   tmin, tmax, wide, hsig, hmin_g, k, dcx, dcy, dcz);
+        uint32_t node = 0;
+        if (resolve) {
+            // ---- one waiting node per lane, decided for every particle of the group
+            const int nr = min(min(nu, 32), max(room, 1));
+            uint2 U = make_uint2(0u, 0u);
+            if (lane < nr) {
+                U = sh.und[nu - nr + lane];
+                C = __ldg(&bcen[U.x]);
+                O = __ldg(&bcom[U.x]);
+                Lk = __ldg(&blink[U.x]);
+                if (VARH)
+                    hsig = __ldg(&T.bsoft[U.x]);
+            }
+            nu -= nr;
+            const float dx = C.x - gcx, dy = C.y - gcy, dz = C.z - gcz;  // exact
+            const float L = C.w;
+            const float q = RELATIVE ? O.w * L * L : L * L;
+            const float gl = 0.6f * L;
+            unsigned om = 0u, am = 0u;
+            if (!PERIODIC && !TREEPM && !VARH) {
+                // particle pairs through the two-wide FP32 instructions; each
+                // element is rounded as in the scalar form, so the decisions
+                // are the same bits
+                const float2 ndx = make_float2(-dx, -dx), ndy = make_float2(-dy, -dy), ndz = make_float2(-dz, -dz);
+                const float2 ox = make_float2(O.x, O.x), oy = make_float2(O.y, O.y), oz = make_float2(O.z, O.z);
+                const float2 m1 = make_float2(-1.0f, -1.0f);
+                const bool guard_on = k.box_guard != 0;
+                unsigned uy = U.y;  // lane bits still to decide, particle pair i in bits 0-1
+#pragma unroll 2
+                for (int i = 0; i < 16; i++, uy >>= 2) {
+                    const float4 XY = sh.pxy[i], ZT = sh.pzt[i];
+                    const float2 px = __fadd2_rn(make_float2(XY.x, XY.y), ndx);
+                    const float2 py = __fadd2_rn(make_float2(XY.z, XY.w), ndy);
+                    const float2 pz = __fadd2_rn(make_float2(ZT.x, ZT.y), ndz);
+                    const float2 rx = __ffma2_rn(px, m1, ox), ry = __ffma2_rn(py, m1, oy), rz = __ffma2_rn(pz, m1, oz);
+                    const float2 r2 = __ffma2_rn(rx, rx, __ffma2_rn(ry, ry, __fmul2_rn(rz, rz)));
+                    float2 t = __fmul2_rn(make_float2(ZT.z, ZT.w), r2);
+                    if (RELATIVE)
+                        t = __fmul2_rn(t, r2);
+                    const bool g0 = guard_on && fmaxf(fabsf(px.x), fmaxf(fabsf(py.x), fabsf(pz.x))) <= gl;
+                    const bool g1 = guard_on && fmaxf(fabsf(px.y), fmaxf(fabsf(py.y), fabsf(pz.y))) <= gl;
+                    const bool o0 = g0 || q > t.x, o1 = g1 || q > t.y;
+                    const unsigned b0 = 1u << (2 * i), b1 = 2u << (2 * i);
+                    if (uy & 1u)
+                        o0 ? (om |= b0) : (am |= b0);
+                    if (uy & 2u)
+                        o1 ? (om |= b1) : (am |= b1);
+                }
+            } else {
+            const unsigned umask = __reduce_or_sync(FULL, U.y);
+            for (unsigned m = umask; m; m &= m - 1u) {
+                const int p = __ffs(m) - 1;
+                const float4 P = part_entry(sh, p);
+                const bool act = (U.y >> p) & 1u;
+                float px = P.x - dx, py = P.y - dy, pz = P.z - dz;
+                if (PERIODIC) {
+                    px = wrap_min_image(px, k);
+                    py = wrap_min_image(py, k);
+                    pz = wrap_min_image(pz, k);
+                }
+                float rx = O.x - px, ry = O.y - py, rz = O.z - pz;
+                if (PERIODIC && (EWALD || L > k.bigL)) {
+                    rx = wrap_min_image(rx, k);
+                    ry = wrap_min_image(ry, k);
+                    rz = wrap_min_image(rz, k);
+                }
+                const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+                bool far = false;
+                if (TREEPM) {
+                    const float ex = fmaxf(fabsf(px) - 0.5f * L, 0.0f), ey = fmaxf(fabsf(py) - 0.5f * L, 0.0f),
+                                ez = fmaxf(fabsf(pz) - 0.5f * L, 0.0f);
+                    far = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) > k.rcut2;
+                }
+                const bool guard = k.box_guard && fabsf(px) <= gl && fabsf(py) <= gl && fabsf(pz) <= gl;
+                bool crit = RELATIVE ? (q > P.w * r2 * r2) : (q > P.w * r2);
+                if (VARH) {  // Sec. 3.2: a node of mixed softenings is opened inside its largest one
+                    const float hp = __shfl_sync(FULL, hi, p);
+                    crit = crit || (hsig < 0.0f && hp < -hsig && r2 < hsig * hsig);
+                }
+                const unsigned b = 1u << p;
+                if (act && !far)
+                    (guard || crit) ? (om |= b) : (am |= b);
+            }
+            }
+            node = U.x;
+            nmask = om;
+            amask = am;
+            dcx = dx;
+            dcy = dy;
+            dcz = dz;
+            if (PERIODIC) {
+                dcx = wrap_min_image(dcx, k);
+                dcy = wrap_min_image(dcy, k);
+                dcz = wrap_min_image(dcz, k);
+            }
+            cls = (lane < nr) ? kMixed : kNone;
+        } else {
+            // ---- take up to 32 candidates from the top child ranges
+            const int cap = sn > SH::kSafe ? 1 : 32;
+            const int idx = sn - 1 - lane;
+            uint2 R = make_uint2(0u, 0u);
+            int c = 0;
+            if (idx >= 0) {
+                R = sh.stack[idx];
+                c = sh.scount[idx];
+            }
+            int incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o)
+                    incl += v;
+            }
+            const int excl = incl - c;
+            const bool take = idx >= 0 && c > 0 && excl < cap;
+            const bool whole = take && incl <= cap;
+            const int ntake = take ? min(c, cap - excl) : 0;
+            const int nwhole = __popc(__ballot_sync(FULL, whole));
+            const int ncand = min(__shfl_sync(FULL, incl, 31), cap);
+            // candidate `lane` comes from the range r whose prefix sums
+            // bracket it (binary search over the nondecreasing incl)
+            int r = 0;
+#pragma unroll
+            for (int b = 16; b > 0; b >>= 1)
+                if (__shfl_sync(FULL, incl, r + b - 1) <= lane)
+                    r += b;
+            const uint32_t cnode = __shfl_sync(FULL, R.x, r) + (uint32_t)(lane - __shfl_sync(FULL, excl, r));
+            const uint32_t cmask = __shfl_sync(FULL, R.y, r);
+            if (take && !whole) {  // the partly taken range stays on top
+                sh.stack[idx].x = R.x + (uint32_t)ntake;
+                sh.scount[idx] = (uint8_t)(c - ntake);
+            }
+            sn -= nwhole;
+            __syncwarp();
+
+            // ---- one candidate per lane: decide for the whole group
+            if (lane < ncand) {
+                node = cnode;
+                nmask = cmask;
+                C = __ldg(&bcen[cnode]);
+                O = __ldg(&bcom[cnode]);
+                Lk = __ldg(&blink[cnode]);
+                if (VARH)
+                    hsig = __ldg(&T.bsoft[cnode]);
+                cls = classify_group<PERIODIC, RELATIVE, TREEPM, VARH>(C, O, gcx, gcy, gcz, lox, loy, loz, hix, hiy,
+                                                                       hiz, tmin, tmax, wide, hsig, hmin_g, k, dcx,
+                                                                       dcy, dcz);
+            }
+            // nodes the bounds cannot decide wait for the per-particle decisions
+            const unsigned bm = __ballot_sync(FULL, cls == kMixed);
+            if (cls == kMixed)
+                sh.und[nu + __popc(bm & lt_mask)] = make_uint2(node, nmask);
+            nu += __popc(bm);
+            if (cls == kAccept) {
+                amask = nmask;
+                nmask = 0u;
+            } else if (cls != kOpen) {
+                nmask = 0u;
+            }
         }
         __syncwarp();
+        // ---- queue what the lanes accept and open: amask = lanes that take the
+        // node's monopole, nmask = lanes that open it
         const bool is_leaf = Lk.y == 0;
         // pair vectors are wrapped per lane when the group-centred image may
         // not be the particle's nearest one, and always for the Ewald table
         const bool wrapf = PERIODIC && (EWALD || wide || C.w > k.bigL);
-        const bool e_acc = cls == kAccept, e_leaf = cls == kOpen && is_leaf, e_push = cls == kOpen && !is_leaf;
-        const bool e_full = e_acc && nmask == valid_mask;
+        const bool e_acc = amask != 0u;
+        const bool e_full = e_acc && amask == valid_mask;
         const unsigned bf = __ballot_sync(FULL, e_full);
         const unsigned bq = __ballot_sync(FULL, e_acc && !e_full);
         if (e_acc) {
             const int at = e_full ? nf + __popc(bf & lt_mask) : kNodeCap - 1 - np - __popc(bq & lt_mask);
-            sh.nsrc[at] = make_float4(dcx + O.x, dcy + O.y, dcz + O.z, O.w);
-            sh.nmask[at] = nmask;
-            sh.nwrap[at] = wrapf ? 1 : 0;
+            put_node_entry(sh, at, make_float4(dcx + O.x, dcy + O.y, dcz + O.z, O.w));
+            sh.nmask[at] = amask;
+            if (PERIODIC)
+                sh.nwrap[at] = wrapf ? 1 : 0;
             if (VARH)
                 sh.nsoft[at] = fabsf(hsig);
         }
         nf += __popc(bf);
         np += __popc(bq);
+        const bool e_leaf = nmask != 0u && is_leaf, e_push = nmask != 0u && !is_leaf;
         const unsigned bl = __ballot_sync(FULL, e_leaf);
         if (e_leaf) {
             const int at = nl + __popc(bl & lt_mask);
@@ -906,109 +1188,23 @@ __device__ __forceinline__ void group_walk(const TreeView &T, const WalkConsts &
             }
         }
         sn = min(sn + __popc(bp), SH::kStack);
-
-        // ---- nodes the bounds could not decide: per-particle decisions, as in
-        // the lane walk.  A lane that accepts the node adds its monopole at
-        // once, with the r^2 its criterion used; only opened nodes go on.  The
-        // node's record comes from the lane that classified it; its links are
-        // packed as (first child, child count) for an internal node and
-        // (first particle, particle count | leaf bit) for a leaf.
-        const int lk0 = is_leaf ? Lk.z : Lk.x;
-        const int lk1 = is_leaf ? (int)((uint32_t)Lk.w | 0x80000000u) : Lk.y;
-        unsigned mixed = __ballot_sync(FULL, cls == kMixed);
-        while (mixed) {
-            const int t = __ffs(mixed) - 1;
-            mixed &= mixed - 1;
-            const uint32_t mm = __shfl_sync(FULL, nmask, t);
-            const float MCx = __shfl_sync(FULL, C.x, t), MCy = __shfl_sync(FULL, C.y, t),
-                        MCz = __shfl_sync(FULL, C.z, t), L = __shfl_sync(FULL, C.w, t);
-            const float MOx = __shfl_sync(FULL, O.x, t), MOy = __shfl_sync(FULL, O.y, t),
-                        MOz = __shfl_sync(FULL, O.z, t), MOm = __shfl_sync(FULL, O.w, t);
-            const int l0 = __shfl_sync(FULL, lk0, t), l1 = __shfl_sync(FULL, lk1, t);
-            const float hs = VARH ? __shfl_sync(FULL, hsig, t) : 0.0f;
-            const bool act = (mm & lanebit) != 0u;
-            const float dx = MCx - gcx, dy = MCy - gcy, dz = MCz - gcz;  // exact
-            float px = xox - dx, py = xoy - dy, pz = xoz - dz;
-            if (PERIODIC) {
-                px = wrap_min_image(px, k);
-                py = wrap_min_image(py, k);
-                pz = wrap_min_image(pz, k);
-            }
-            float rx = MOx - px, ry = MOy - py, rz = MOz - pz;
-            if (PERIODIC && (EWALD || L > k.bigL)) {
-                rx = wrap_min_image(rx, k);
-                ry = wrap_min_image(ry, k);
-                rz = wrap_min_image(rz, k);
-            }
-            const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-            bool far = false;
-            if (TREEPM) {
-                const float ex = fmaxf(fabsf(px) - 0.5f * L, 0.0f), ey = fmaxf(fabsf(py) - 0.5f * L, 0.0f),
-                            ez = fmaxf(fabsf(pz) - 0.5f * L, 0.0f);
-                far = fmaf(ex, ex, fmaf(ey, ey, ez * ez)) > k.rcut2;
-            }
-            const float gl = 0.6f * L;
-            const bool guard = k.box_guard && fabsf(px) <= gl && fabsf(py) <= gl && fabsf(pz) <= gl;
-            bool crit = RELATIVE ? (MOm * L * L > thr * r2 * r2) : (L * L > thr * r2);
-            if (VARH)  // Sec. 3.2: a node of mixed softenings is opened inside its largest one
-                crit = crit || (hs < 0.0f && hi < -hs && r2 < hs * hs);
-            const bool open = act && !far && (guard || crit);
-            if (act && !far && !open) {
-                if (VARH)
-                    pair_term_h<TREEPM>(rx, ry, rz, r2, MOm, fmaxf(hi, fabsf(hs)), k, ax, ay, az, ph);
-                else
-                    pair_term<TREEPM>(rx, ry, rz, r2, MOm, k, ax, ay, az, ph);
-                if (EWALD)
-                    ewald_term(rx, ry, rz, MOm, k, ax, ay, az, ph);
-                cnt++;
-            }
-            const unsigned om = __ballot_sync(FULL, open);
-            if (om) {
-                if (l1 >= 0) {
-                    if (lane == 0) {
-                        if (sn < SH::kStack) {
-                            sh.stack[sn] = make_uint2((uint32_t)l0, om);
-                            sh.scount[sn] = (uint8_t)l1;
-                        } else {
-                            atomicOr(err, 2);
-                        }
-                    }
-                    sn = min(sn + 1, SH::kStack);
-                } else {
-                    float wx = dx, wy = dy, wz = dz;  // node centre, group-centred nearest image
-                    if (PERIODIC) {
-                        wx = wrap_min_image(wx, k);
-                        wy = wrap_min_image(wy, k);
-                        wz = wrap_min_image(wz, k);
-                    }
-                    const bool wflag = PERIODIC && (EWALD || wide || L > k.bigL);
-                    if (lane == 0) {
-                        sh.lsrc[nl] = make_float4(wx, wy, wz, __int_as_float(l0));
-                        sh.lmeta[nl] = make_uint2(om, (wflag ? kLeafWrap : 0u) | ((uint32_t)l1 & kLeafCount));
-                    }
-                    nl++;
-                }
-            }
-        }
         __syncwarp();
-        if (nf + np >= kNodeFlush) {
+        }
+        if (done || nf + np >= kNodeFlush) {
             sweep_full<PERIODIC, TREEPM, VARH>(sh, nf, xox, xoy, xoz, hi, k, ax, ay, az, ph);
             sweep_partial<PERIODIC, TREEPM, VARH>(sh, np, lanebit, xox, xoy, xoz, hi, k, ax, ay, az, ph, cnt);
             cnt += valid ? (uint32_t)nf : 0u;
             nf = np = 0;
         }
-        if (nl >= kLeafFlush) {
+        if (done || nl >= kLeafFlush) {
             sweep_leaves<PERIODIC, TREEPM, VARH>(sh, nl, lanebit, s, xox, xoy, xoz, hi, spart, T.psoft, k, ax, ay, az,
                                                  ph, cnt);
             nl = 0;
         }
+        if (done)
+            break;
         __syncwarp();
     }
-    sweep_full<PERIODIC, TREEPM, VARH>(sh, nf, xox, xoy, xoz, hi, k, ax, ay, az, ph);
-    sweep_partial<PERIODIC, TREEPM, VARH>(sh, np, lanebit, xox, xoy, xoz, hi, k, ax, ay, az, ph, cnt);
-    cnt += (uint32_t)nf;
-    sweep_leaves<PERIODIC, TREEPM, VARH>(sh, nl, lanebit, s, xox, xoy, xoz, hi, spart, T.psoft, k, ax, ay, az, ph,
-                                         cnt);
     if (!valid)
         return;
     if (EWALD)  // the particle's own images and the background
@@ -1032,13 +1228,15 @@ __device__ __forceinline__ void group_walk(const TreeView &T, const WalkConsts &
 }
 
 
-// One warp per group of `gsize` consecutive active particles.
+// One warp per group of `gsize` consecutive active particles.  Seven blocks
+// of four warps per SM: the register cap (72) that keeps the paired FP32
+// sweeps and decisions free of spills (measured against caps of 64 and none).
 template <bool PERIODIC, bool RELATIVE, bool TREEPM, bool VARH>
-__global__ void __launch_bounds__(kGroupWarps * 32)
+__global__ void __launch_bounds__(kGroupWarps * 32, 7)
     k_walk_group(TreeView T, const uint32_t *__restrict__ sidx, const uint32_t *__restrict__ slot,
                  const float *__restrict__ a_old, int64_t n_act, int gsize, WalkConsts k, float *__restrict__ acc,
                  float *__restrict__ pot, uint32_t *__restrict__ nint, int accumulate, int *__restrict__ err) {
-    using SH = GroupSharedT<kStackCap>;
+    using SH = GroupSharedT<kStackCap, VARH, PERIODIC>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SH &sh = reinterpret_cast<SH *>(smem_raw)[threadIdx.x >> 5];
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1067,7 +1265,7 @@ __global__ void __launch_bounds__(kGroupWarps * 32)
                  const unsigned *__restrict__ n_groups, unsigned *__restrict__ next, const uint32_t *__restrict__ sidx,
                  const uint32_t *__restrict__ slot, const float *__restrict__ a_old, float *__restrict__ acc,
                  float *__restrict__ pot, uint32_t *__restrict__ nint, int *__restrict__ err) {
-    using SH = GroupSharedT<STACK>;
+    using SH = GroupSharedT<STACK, false, PERIODIC>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SH &sh = reinterpret_cast<SH *>(smem_raw)[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
@@ -1105,7 +1303,7 @@ void launch(const System *s, const WalkRequest &r, const WalkConsts &k, bool lan
         count_launch();
     } else {
         const int64_t blocks = (warps + kGroupWarps - 1) / kGroupWarps;
-        const size_t smem = kGroupWarps * sizeof(GroupSharedT<kStackCap>);
+        const size_t smem = kGroupWarps * sizeof(GroupSharedT<kStackCap, V, P>);
         TreeView tv{s->bcen, s->bcom, s->blink, s->spart, s->psoft, s->bsoft, s->key,
                     s->perm, s->pos,  s->x0[0], s->x0[1],  s->x0[2], s->L0};
         k_walk_group<P, R, T, V><<<(unsigned)blocks, kGroupWarps * 32, smem, st>>>(
@@ -1177,7 +1375,7 @@ template <int STACK>
 int launch_walk_batch_at(Ctx *c, const void *reqs, const uint4 *groups, const unsigned *n_groups, unsigned *next,
                          const uint32_t *sidx, const uint32_t *slot, const float *a_old, float *acc, float *pot,
                          uint32_t *nint, int *err, cudaStream_t st) {
-    const size_t smem = kGroupWarps * sizeof(GroupSharedT<STACK>);
+    const size_t smem = kGroupWarps * sizeof(GroupSharedT<STACK, false, false>);
     static int blocks_per_sm = 0;  // resident blocks of this variant (one persistent wave)
     if (!blocks_per_sm) {
         int b = 0;
