@@ -215,7 +215,7 @@ int tpm_compute_forces(tpm_ctx *ctx, tpm_sys s, const uint32_t *active_ids, int6
  * pay for (or risk failing) an allocation at every step.  The per-call
  * scratch of tpm_compute_forces (the active set sorted into key order and
  * the sort's temporary storage) lives instead in one fixed-size device array
- * inside the library, about 6 MiB, which every GPU that loads the library
+ * inside the library, about 8 MiB, which every GPU that loads the library
  * holds until the process exits.
  *   Same arguments and results as tpm_compute_forces, except:
  *   - active_ids is required and n_active must lie in [1, TPM_NOALLOC_MAX_ACTIVE];

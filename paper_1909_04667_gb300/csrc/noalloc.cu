@@ -26,10 +26,12 @@ constexpr size_t kIdsBytes = (size_t)kMaxActive * sizeof(uint32_t);
 // values and their alternates, all in the scratch), so CUB needs only its
 // histograms and look-back state here, not copies of the keys.
 constexpr size_t kSortTempBytes = size_t(2) << 20;
-constexpr size_t kScratchBytes = 4 * kIdsBytes + kSortTempBytes;
+constexpr size_t kRunsBytes = (size_t)kMaxActive * sizeof(uint2);  // runs of spread-out walk groups
+constexpr size_t kScratchBytes = 4 * kIdsBytes + kSortTempBytes + kRunsBytes + 256;
 
-// The shared scratch: keys, values, alternate keys, alternate values and the
-// sort's temporary storage.  Host code must not pass this symbol to a
+// The shared scratch: keys, values, alternate keys, alternate values, the
+// sort's temporary storage, the walk's run list and its count.  Host code
+// must not pass this symbol to a
 // kernel -- on the host it only names a stand-in; its device address comes
 // from cudaGetSymbolAddress (see scratch_on_device).
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
@@ -150,6 +152,8 @@ extern "C" int tpm_compute_forces_noalloc(tpm_ctx *h, tpm_sys sid, const uint32_
     uint32_t *akeys = reinterpret_cast<uint32_t *>(base + 2 * kIdsBytes);
     uint32_t *avals = reinterpret_cast<uint32_t *>(base + 3 * kIdsBytes);
     void *sort_tmp = base + 4 * kIdsBytes;
+    uint2 *runs = reinterpret_cast<uint2 *>(base + 4 * kIdsBytes + kSortTempBytes);
+    unsigned *nruns = reinterpret_cast<unsigned *>(base + 4 * kIdsBytes + kSortTempBytes + kRunsBytes);
 
     int bits = 1;
     while ((int64_t(1) << bits) < s->n)
@@ -180,6 +184,8 @@ extern "C" int tpm_compute_forces_noalloc(tpm_ctx *h, tpm_sys sid, const uint32_
     r.pot = pot;
     r.nint = n_int;
     r.no_alloc = 1;
+    r.runs = runs;    // the walk clears the count
+    r.nruns = nruns;
     if (p->treepm) {
         TPM_CHECK(pm_interp_device(c, s, r, st));
         r.accumulate = 1;

@@ -573,6 +573,10 @@ int tpm_compute_forces(tpm_ctx *h, tpm_sys sid, const uint32_t *active_ids, int6
         r.sorted_idx = sk;
         r.slot = sv;
     }
+    if (!s->bp.periodic) {  // runs of spread-out chunks
+        TPM_CHECK(tmp.get(&r.runs, n_active, st));
+        TPM_CHECK(tmp.get(&r.nruns, 1, st));
+    }
     if (p->treepm) {
         TPM_CHECK(pm_interp_device(c, s, r, st));
         r.accumulate = 1;

@@ -200,6 +200,11 @@ struct WalkRequest {
     uint32_t *nint;              // nullable
     int accumulate;              // 1: add to acc / pot instead of overwriting
     int no_alloc = 0;            // 1: the call must not allocate device memory
+    // open boundaries: room for n_act runs of spread-out chunks and their
+    // count, for the lane walk (which hands them to the group walk; cleared by
+    // walk_device)
+    uint2 *runs = nullptr;
+    unsigned *nruns = nullptr;
 };
 
 int walk_device(Ctx *c, const System *s, const tpm_force_params *p, const WalkRequest &r, cudaStream_t st);

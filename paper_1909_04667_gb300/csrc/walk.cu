@@ -22,6 +22,7 @@
 // particles as FP32 offsets from their node centre, so every pair vector is
 // a sum of small, accurately rounded terms and the pair arithmetic runs in
 // FP32 with FP32 accumulation.
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 
@@ -182,6 +183,78 @@ __device__ __forceinline__ void ewald_term(float rx, float ry, float rz, float m
     ph = fmaf(m * k.eps, v[3], ph);
 }
 
+// ----------------------------------------------------------------------
+// Walk frames of spread-out chunks.
+//
+// A group's frame is the smallest key cell holding its first and last
+// particle, and each particle's offset from the frame centre is rounded to
+// FP32 once (an error up to 2^-25 of the cell's side).  Particles that are
+// consecutive in key order are normally close, but a chunk can reach from a
+// dense region to a far particle (an outlier, or a jump of the space-filling
+// curve across a coarse cell boundary); its frame is then far coarser than
+// the separations of its dense members and their close pairs lose precision.
+// Such a chunk is cut into runs: wherever the frame is more than
+// 2^kFrameSpan times coarser than the finest cell some member shares with a
+// key-order neighbour, the chunk splits at the pairs of consecutive
+// particles that share only the frame's cell, and the pieces are examined
+// again.  The warp then walks the runs one after the other, each in its own
+// frame (the lane walk lists them for a small group-walk launch after it);
+// every decision stays the per-particle walk's.
+constexpr int kFrameSpan = 8;
+
+__device__ __forceinline__ int common_level(uint64_t a, uint64_t b) {
+    const uint64_t x = a ^ b;
+    return x ? min((__clzll(x) - 1) / 3, kMaxLevel) : kMaxLevel;
+}
+
+// Bit i of the result: a run ends after particle i of the chunk [g0, g0 +
+// gcount) of the sorted active list (0: the chunk keeps one frame).
+__device__ __forceinline__ unsigned chunk_cuts(const uint64_t *__restrict__ key, const uint32_t *__restrict__ sidx,
+                                               int64_t g0, int gcount) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const bool valid = lane < gcount;
+    const int64_t gi = valid ? g0 + lane : g0;
+    const uint64_t kk = key[sidx ? sidx[gi] : (uint32_t)gi];
+    const uint64_t kn = __shfl_down_sync(FULL, kk, 1);
+    const bool pair = lane + 1 < gcount;  // (lane, lane + 1) are consecutive members
+    const int lv = pair ? common_level(kk, kn) : 0;
+    unsigned cut = 0u;
+    for (int it = 0; it <= kMaxLevel; it++) {
+        const bool inrun = pair && !((cut >> lane) & 1u);
+        const int prev = __shfl_up_sync(FULL, inrun ? lv : -1, 1);
+        // finest level this particle shares with an in-run neighbour, and
+        // the run's frame level (the coarsest level shared inside the run)
+        const int lam = max(inrun ? lv : -1, lane > 0 ? prev : -1);
+        const unsigned run = valid ? (unsigned)__popc(cut & ((1u << lane) - 1u)) : 64u + (unsigned)lane;
+        const unsigned seg = __match_any_sync(FULL, run);
+        const unsigned frame = __reduce_min_sync(seg, inrun ? (unsigned)lv : 99u);
+        const unsigned finest = __reduce_max_sync(seg, (unsigned)(lam + 1));
+        const bool split = valid && inrun && (unsigned)lv == frame && finest > frame + 1u + (unsigned)kFrameSpan;
+        const unsigned add = __ballot_sync(FULL, split);
+        if (!add)
+            break;
+        cut |= add;
+    }
+    return cut;
+}
+
+// Appends the runs of a cut chunk to the run list (start, count).
+__device__ __forceinline__ void append_runs(unsigned cut, int64_t g0, int gcount, uint2 *__restrict__ runs,
+                                            unsigned *__restrict__ nruns) {
+    const int lane = threadIdx.x & 31;
+    const unsigned starts = (1u | (cut << 1)) & (gcount >= 32 ? 0xffffffffu : ((1u << gcount) - 1u));
+    unsigned base = 0;
+    if (lane == 0)
+        base = atomicAdd(nruns, (unsigned)__popc(starts));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if ((starts >> lane) & 1u) {
+        const unsigned long long above = (unsigned long long)starts & ~((2ull << lane) - 1ull);
+        const int next = above ? __ffsll((long long)above) - 1 : gcount;
+        runs[base + __popc(starts & ((1u << lane) - 1u))] = make_uint2((uint32_t)(g0 + lane), (uint32_t)(next - lane));
+    }
+}
+
 template <bool PERIODIC, bool RELATIVE, bool TREEPM, bool VARH>
 __global__ void __launch_bounds__(kWalkThreads)
     k_walk(const float4 *__restrict__ ncen, const float4 *__restrict__ ncom, const int4 *__restrict__ nlink,
@@ -189,12 +262,21 @@ __global__ void __launch_bounds__(kWalkThreads)
            const double *__restrict__ pos, double x0, double y0, double z0, double L0, int nnodes,
            const float *__restrict__ psoft, const float *__restrict__ nsoft, const uint32_t *__restrict__ sidx,
            const uint32_t *__restrict__ slot, const float *__restrict__ a_old, int64_t n_act, WalkConsts k,
-           float *__restrict__ acc, float *__restrict__ pot, uint32_t *__restrict__ nint, int accumulate) {
+           float *__restrict__ acc, float *__restrict__ pot, uint32_t *__restrict__ nint, int accumulate,
+           uint2 *__restrict__ runs, unsigned *__restrict__ nruns) {
     constexpr bool EWALD = PERIODIC && !TREEPM;  // periodic tree without the mesh
     const int lane = threadIdx.x & 31;
     const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane);
     if (g0 >= n_act)
         return;  // the whole warp leaves together
+    if (!PERIODIC) {  // spread-out chunks are walked in runs by the group walk
+        const int gcount = (int)min((int64_t)32, n_act - g0);
+        const unsigned cut = chunk_cuts(key, sidx, g0, gcount);
+        if (cut) {
+            append_runs(cut, g0, gcount, runs, nruns);
+            return;
+        }
+    }
     const int64_t gi = g0 + lane;
     const bool valid = gi < n_act;
     const int64_t glast = min(g0 + 31, n_act - 1);
@@ -918,14 +1000,13 @@ __device__ __forceinline__ void group_walk(const TreeView &T, const WalkConsts &
     const int glevel = kx ? min((__clzll(kx) - 1) / 3, kMaxLevel) : kMaxLevel;
     const uint64_t gpre = kf >> (3 * (kMaxLevel - glevel));
     const double ghalf = ldexp(L0, -(glevel + 1));
-    const double gcx_d = (double)(2 * (uint64_t)compact3w(gpre) + 1) * ghalf;
-    const double gcy_d = (double)(2 * (uint64_t)compact3w(gpre >> 1) + 1) * ghalf;
-    const double gcz_d = (double)(2 * (uint64_t)compact3w(gpre >> 2) + 1) * ghalf;
-    const float gcx = (float)gcx_d, gcy = (float)gcy_d, gcz = (float)gcz_d;
+    double gcx_d = (double)(2 * (uint64_t)compact3w(gpre) + 1) * ghalf;
+    double gcy_d = (double)(2 * (uint64_t)compact3w(gpre >> 1) + 1) * ghalf;
+    double gcz_d = (double)(2 * (uint64_t)compact3w(gpre >> 2) + 1) * ghalf;
     const uint32_t j = perm[s];
-    const float xox = (float)(pos[3 * j] - (x0 + gcx_d));
-    const float xoy = (float)(pos[3 * j + 1] - (y0 + gcy_d));
-    const float xoz = (float)(pos[3 * j + 2] - (z0 + gcz_d));
+    const double dxo = pos[3 * j] - (x0 + gcx_d), dyo = pos[3 * j + 1] - (y0 + gcy_d),
+                 dzo = pos[3 * j + 2] - (z0 + gcz_d);
+    float xox = (float)dxo, xoy = (float)dyo, xoz = (float)dzo;
     float thr = k.thr_const;
     if (RELATIVE)
         thr = valid ? k.alpha_over_G * fabsf(a_old[out]) : 0.0f;
@@ -937,18 +1018,44 @@ __device__ __forceinline__ void group_walk(const TreeView &T, const WalkConsts &
 
     // group bounding box and criterion thresholds over the valid lanes
     const float inf = __int_as_float(0x7f800000);
-    float lox = valid ? xox : inf, loy = valid ? xoy : inf, loz = valid ? xoz : inf;
-    float hix = valid ? xox : -inf, hiy = valid ? xoy : -inf, hiz = valid ? xoz : -inf;
-    float tmin = valid ? thr : inf, tmax = valid ? thr : 0.0f;
+    float lox, loy, loz, hix, hiy, hiz;
+    auto bounding_box = [&]() {
+        lox = valid ? xox : inf, loy = valid ? xoy : inf, loz = valid ? xoz : inf;
+        hix = valid ? xox : -inf, hiy = valid ? xoy : -inf, hiz = valid ? xoz : -inf;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        lox = fminf(lox, __shfl_xor_sync(FULL, lox, o));
-        loy = fminf(loy, __shfl_xor_sync(FULL, loy, o));
-        loz = fminf(loz, __shfl_xor_sync(FULL, loz, o));
-        hix = fmaxf(hix, __shfl_xor_sync(FULL, hix, o));
-        hiy = fmaxf(hiy, __shfl_xor_sync(FULL, hiy, o));
-        hiz = fmaxf(hiz, __shfl_xor_sync(FULL, hiz, o));
-        if (RELATIVE) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lox = fminf(lox, __shfl_xor_sync(FULL, lox, o));
+            loy = fminf(loy, __shfl_xor_sync(FULL, loy, o));
+            loz = fminf(loz, __shfl_xor_sync(FULL, loz, o));
+            hix = fmaxf(hix, __shfl_xor_sync(FULL, hix, o));
+            hiy = fmaxf(hiy, __shfl_xor_sync(FULL, hiy, o));
+            hiz = fmaxf(hiz, __shfl_xor_sync(FULL, hiz, o));
+        }
+    };
+    bounding_box();
+    if (!PERIODIC) {
+        // Open boundaries: move the frame centre to the middle of the group's
+        // bounding box, on the grid of the node centres (2^-22 L0, so that
+        // node-to-frame offsets stay exact in FP32), and take the offsets
+        // again in FP64.  The key cell can be far larger than the group (a
+        // group across a coarse cell boundary, or inside a depth-capped cell
+        // much wider than its particles' separations).
+        const float q = (float)ldexp(L0, -22), iq = (float)ldexp(1.0 / L0, 22);  // powers of two
+        const float sx = q * rintf(0.5f * (lox + hix) * iq), sy = q * rintf(0.5f * (loy + hiy) * iq),
+                    sz = q * rintf(0.5f * (loz + hiz) * iq);
+        gcx_d += (double)sx;
+        gcy_d += (double)sy;
+        gcz_d += (double)sz;
+        xox = (float)(dxo - (double)sx);
+        xoy = (float)(dyo - (double)sy);
+        xoz = (float)(dzo - (double)sz);
+        bounding_box();
+    }
+    const float gcx = (float)gcx_d, gcy = (float)gcy_d, gcz = (float)gcz_d;
+    float tmin = valid ? thr : inf, tmax = valid ? thr : 0.0f;
+    if (RELATIVE) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
             tmin = fminf(tmin, __shfl_xor_sync(FULL, tmin, o));
             tmax = fmaxf(tmax, __shfl_xor_sync(FULL, tmax, o));
         }
@@ -1228,6 +1335,28 @@ __device__ __forceinline__ void group_walk(const TreeView &T, const WalkConsts &
 }
 
 
+// Walks a chunk of consecutive active particles: in one frame, or, when it
+// is spread out (chunk_cuts), run by run, each run in its own frame.
+template <bool PERIODIC, bool RELATIVE, bool TREEPM, bool VARH, class SH>
+__device__ __forceinline__ void walk_runs_of_chunk(const TreeView &T, const WalkConsts &k, SH &sh,
+                                                   const uint32_t *__restrict__ sidx, const uint32_t *__restrict__ slot,
+                                                   int64_t g0, int gcount, const float *__restrict__ a_old,
+                                                   float *__restrict__ acc, float *__restrict__ pot,
+                                                   uint32_t *__restrict__ nint, int accumulate, int *__restrict__ err) {
+    unsigned cut = PERIODIC ? 0u : chunk_cuts(T.key, sidx, g0, gcount);  // a periodic box bounds every frame
+    int start = 0;
+    for (;;) {
+        const int end = cut ? __ffs(cut) : gcount;
+        group_walk<PERIODIC, RELATIVE, TREEPM, VARH>(T, k, sh, sidx, slot, g0 + start, end - start, a_old, acc, pot,
+                                                     nint, accumulate, err);
+        if (!cut)
+            break;
+        cut &= cut - 1u;
+        start = end;
+        __syncwarp();
+    }
+}
+
 // One warp per group of `gsize` consecutive active particles.  Seven blocks
 // of four warps per SM: the register cap (72) that keeps the paired FP32
 // sweeps and decisions free of spills (measured against caps of 64 and none).
@@ -1244,8 +1373,28 @@ __global__ void __launch_bounds__(kGroupWarps * 32, 7)
     if (g0 >= n_act)
         return;  // whole warp
     const int gcount = (int)min((int64_t)gsize, n_act - g0);
-    group_walk<PERIODIC, RELATIVE, TREEPM, VARH>(T, k, sh, sidx, slot, g0, gcount, a_old, acc, pot, nint, accumulate,
-                                                 err);
+    walk_runs_of_chunk<PERIODIC, RELATIVE, TREEPM, VARH>(T, k, sh, sidx, slot, g0, gcount, a_old, acc, pot, nint,
+                                                         accumulate, err);
+}
+
+// The runs of cut chunks, one warp per run.
+template <bool PERIODIC, bool RELATIVE, bool TREEPM, bool VARH>
+__global__ void __launch_bounds__(kGroupWarps * 32)
+    k_walk_runs(TreeView T, const uint32_t *__restrict__ sidx, const uint32_t *__restrict__ slot,
+                const float *__restrict__ a_old, const uint2 *__restrict__ runs, const unsigned *__restrict__ nruns,
+                WalkConsts k, float *__restrict__ acc, float *__restrict__ pot, uint32_t *__restrict__ nint,
+                int accumulate, int *__restrict__ err) {
+    using SH = GroupSharedT<kStackCap, VARH, PERIODIC>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SH &sh = reinterpret_cast<SH *>(smem_raw)[threadIdx.x >> 5];
+    const unsigned total = *nruns;
+    const unsigned nw = gridDim.x * (blockDim.x >> 5);
+    for (unsigned w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < total; w += nw) {
+        const uint2 R = runs[w];
+        group_walk<PERIODIC, RELATIVE, TREEPM, VARH>(T, k, sh, sidx, slot, R.x, (int)R.y, a_old, acc, pot, nint,
+                                                     accumulate, err);
+        __syncwarp();
+    }
 }
 
 // One request of a batch: which tree, with which constants and criterion.
@@ -1260,7 +1409,7 @@ struct BatchReq {
 // belong to different requests and different trees.  Compiled per candidate
 // stack capacity (the plan's autotuner chooses one).
 template <bool PERIODIC, bool TREEPM, int STACK>
-__global__ void __launch_bounds__(kGroupWarps * 32)
+__global__ void __launch_bounds__(kGroupWarps * 32, 7)
     k_walk_batch(const BatchReq *__restrict__ reqs, const uint4 *__restrict__ groups,
                  const unsigned *__restrict__ n_groups, unsigned *__restrict__ next, const uint32_t *__restrict__ sidx,
                  const uint32_t *__restrict__ slot, const float *__restrict__ a_old, float *__restrict__ acc,
@@ -1268,6 +1417,10 @@ __global__ void __launch_bounds__(kGroupWarps * 32)
     using SH = GroupSharedT<STACK, false, PERIODIC>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SH &sh = reinterpret_cast<SH *>(smem_raw)[threadIdx.x >> 5];
+    // the current group's request record, read from shared memory where the
+    // walk needs a field (copies in registers would crowd out the walk's own)
+    __shared__ __align__(16) BatchReq breq[kGroupWarps];
+    BatchReq &R = breq[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const unsigned total = *n_groups;
     for (;;) {
@@ -1278,36 +1431,50 @@ __global__ void __launch_bounds__(kGroupWarps * 32)
         if (g >= total)
             break;
         const uint4 G = groups[g];
-        const BatchReq &R = reqs[G.z];
-        const TreeView T = R.T;
-        const WalkConsts k = R.k;
+        {
+            static_assert(sizeof(BatchReq) % 4 == 0, "request records copy as words");
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(&reqs[G.z]);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(&R);
+            for (int w = lane; w < (int)(sizeof(BatchReq) / 4); w += 32)
+                dst[w] = src[w];
+            __syncwarp();
+        }
         if (R.relative)
-            group_walk<PERIODIC, true, TREEPM, false>(T, k, sh, sidx, slot, G.x, (int)G.y, a_old, acc, pot, nint, 0,
-                                                      err);
+            walk_runs_of_chunk<PERIODIC, true, TREEPM, false>(R.T, R.k, sh, sidx, slot, G.x, (int)G.y, a_old, acc,
+                                                              pot, nint, 0, err);
         else
-            group_walk<PERIODIC, false, TREEPM, false>(T, k, sh, sidx, slot, G.x, (int)G.y, a_old, acc, pot, nint, 0,
-                                                       err);
+            walk_runs_of_chunk<PERIODIC, false, TREEPM, false>(R.T, R.k, sh, sidx, slot, G.x, (int)G.y, a_old, acc,
+                                                               pot, nint, 0, err);
         __syncwarp();
     }
 }
 
 template <bool P, bool R, bool T, bool V>
-void launch(const System *s, const WalkRequest &r, const WalkConsts &k, bool lanes, int *err, cudaStream_t st) {
+void launch(const System *s, const WalkRequest &r, const WalkConsts &k, bool lanes, int *err, int num_sms,
+            cudaStream_t st) {
     const int64_t warps = (r.n_act + 31) / 32;
     if (lanes) {
         const int64_t blocks = (warps * 32 + kWalkThreads - 1) / kWalkThreads;
         k_walk<P, R, T, V><<<(unsigned)blocks, kWalkThreads, 0, st>>>(
             s->ncen, s->ncom, s->nlink, s->spart, s->key, s->perm, s->pos, s->x0[0], s->x0[1], s->x0[2], s->L0,
             (int)s->nnodes, s->psoft, s->nsoft, r.sorted_idx, r.slot, r.a_old, r.n_act, k, r.acc, r.pot, r.nint,
-            r.accumulate);
+            r.accumulate, r.runs, r.nruns);
         count_launch();
-    } else {
+    }
+    const size_t smem = kGroupWarps * sizeof(GroupSharedT<kStackCap, V, P>);
+    TreeView tv{s->bcen, s->bcom, s->blink, s->spart, s->psoft, s->bsoft, s->key,
+                s->perm, s->pos,  s->x0[0], s->x0[1],  s->x0[2], s->L0};
+    if (!lanes) {
         const int64_t blocks = (warps + kGroupWarps - 1) / kGroupWarps;
-        const size_t smem = kGroupWarps * sizeof(GroupSharedT<kStackCap, V, P>);
-        TreeView tv{s->bcen, s->bcom, s->blink, s->spart, s->psoft, s->bsoft, s->key,
-                    s->perm, s->pos,  s->x0[0], s->x0[1],  s->x0[2], s->L0};
         k_walk_group<P, R, T, V><<<(unsigned)blocks, kGroupWarps * 32, smem, st>>>(
             tv, r.sorted_idx, r.slot, r.a_old, r.n_act, 32, k, r.acc, r.pot, r.nint, r.accumulate, err);
+        count_launch();
+    } else if constexpr (!P) {
+        // the lane walk hands spread-out chunks to the group walk: their runs
+        // (rare: usually none, and the launch returns at once)
+        const int64_t blocks = std::min<int64_t>(warps, 2 * (int64_t)num_sms);
+        k_walk_runs<P, R, T, V><<<(unsigned)blocks, kGroupWarps * 32, smem, st>>>(
+            tv, r.sorted_idx, r.slot, r.a_old, r.runs, r.nruns, k, r.acc, r.pot, r.nint, r.accumulate, err);
         count_launch();
     }
 }
@@ -1425,27 +1592,34 @@ int walk_device(Ctx *c, const System *s, const tpm_force_params *p, const WalkRe
     const int ov = walk_override();
     const bool lanes = ov == 1 || (ov == 0 && per);
     int *err = s->err;
+    if (!per && lanes) {  // the lane walk's list of cut chunks' runs: n_act entries at most
+        if (!r.runs || !r.nruns) {
+            set_error("internal: open-boundary lane walk without a run list");
+            return TPM_EINVAL;
+        }
+        TPM_CUDA(cudaMemsetAsync(r.nruns, 0, sizeof(unsigned), st));
+    }
     const bool varh = s->psoft != nullptr;  // per-particle softening (open boundaries only)
     if (varh && per) {
         set_error("per-particle softening is available with open boundaries");
         return TPM_EINVAL;
     }
     if (!per && !tpm)
-        rel ? (varh ? launch<false, true, false, true>(s, r, k, lanes, err, st)
-                    : launch<false, true, false, false>(s, r, k, lanes, err, st))
-            : (varh ? launch<false, false, false, true>(s, r, k, lanes, err, st)
-                    : launch<false, false, false, false>(s, r, k, lanes, err, st));
+        rel ? (varh ? launch<false, true, false, true>(s, r, k, lanes, err, c->num_sms, st)
+                    : launch<false, true, false, false>(s, r, k, lanes, err, c->num_sms, st))
+            : (varh ? launch<false, false, false, true>(s, r, k, lanes, err, c->num_sms, st)
+                    : launch<false, false, false, false>(s, r, k, lanes, err, c->num_sms, st));
     else if (!per && tpm)
-        rel ? (varh ? launch<false, true, true, true>(s, r, k, lanes, err, st)
-                    : launch<false, true, true, false>(s, r, k, lanes, err, st))
-            : (varh ? launch<false, false, true, true>(s, r, k, lanes, err, st)
-                    : launch<false, false, true, false>(s, r, k, lanes, err, st));
+        rel ? (varh ? launch<false, true, true, true>(s, r, k, lanes, err, c->num_sms, st)
+                    : launch<false, true, true, false>(s, r, k, lanes, err, c->num_sms, st))
+            : (varh ? launch<false, false, true, true>(s, r, k, lanes, err, c->num_sms, st)
+                    : launch<false, false, true, false>(s, r, k, lanes, err, c->num_sms, st));
     else if (tpm)
-        rel ? launch<true, true, true, false>(s, r, k, lanes, err, st)
-            : launch<true, false, true, false>(s, r, k, lanes, err, st);
+        rel ? launch<true, true, true, false>(s, r, k, lanes, err, c->num_sms, st)
+            : launch<true, false, true, false>(s, r, k, lanes, err, c->num_sms, st);
     else
-        rel ? launch<true, true, false, false>(s, r, k, lanes, err, st)
-            : launch<true, false, false, false>(s, r, k, lanes, err, st);
+        rel ? launch<true, true, false, false>(s, r, k, lanes, err, c->num_sms, st)
+            : launch<true, false, false, false>(s, r, k, lanes, err, c->num_sms, st);
     TPM_CUDA(cudaGetLastError());
     return TPM_OK;
 }

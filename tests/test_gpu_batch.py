@@ -21,6 +21,20 @@ def rel(a, b):
     return np.linalg.norm(a - b, axis=1) / np.maximum(np.linalg.norm(b, axis=1), 1e-300)
 
 
+def oracle_check(acc, nint, a_o, n_o, p99=P99_TOL, mx=MAX_TOL):
+    """The batched walk against the oracle's per-particle walk: interaction
+    counts equal except for FP32 margin flips (0.5%, or one particle in a
+    small request), forces within the FP32 tolerance where counts agree and
+    within the method's 5e-3 where a decision flipped."""
+    same = nint == n_o
+    assert np.mean(~same) <= 0.005 or (~same).sum() <= 1, "%d counts differ" % (~same).sum()
+    e = rel(acc.astype(np.float64), a_o)
+    if same.any():
+        assert np.percentile(e[same], 99) <= p99 and e[same].max() <= mx, (np.percentile(e[same], 99), e[same].max())
+    if (~same).any():
+        assert e[~same].max() <= 5e-3
+
+
 @pytest.fixture(scope="module")
 def env():
     import torch
@@ -170,4 +184,78 @@ def test_autotune_and_errors(env):
     plan.compute_forces_batch([r[0] for r in reqs], off, [r[2] for r in reqs], bad, acc, a_old=a_old)
     with pytest.raises(tpm.TreePMError, match="out of range"):
         plan.sync_status()
+    plan.close()
+
+
+@pytest.fixture(scope="module")
+def oracle_env(oracle_mod):
+    """Three systems (a Plummer sphere, a Hernquist halo, two clusters with
+    isolated particles between them) with their oracle trees, |a_old| from a
+    geometric GPU pass, and uneven requests on all three."""
+    import torch
+
+    import paper_1909_04667_gb300 as tpm
+
+    dev = torch.device("cuda", 0)
+    ctx = tpm.Context(0)
+    specs = [(W.plummer(12000, 15), 0.01, 15), (W.hernquist(30000, 16), 0.005, 16),
+             (W.clusters_with_outliers(4096, 78), 0.01, 78)]
+    systems, trees, aold = [], [], {}
+    for (pos, mass), h, seed in specs:
+        shift = tuple(W.root_shift(seed))
+        s = ctx.build_tree(torch.from_numpy(pos).to(dev), torch.from_numpy(mass).to(dev),
+                           tpm.BuildParams(G=1.0, h=h, shift=shift, leaf_bucket=8))
+        a, _, _ = s.compute_forces(fp=tpm.ForceParams(theta=0.5))
+        aold[s.handle] = torch.linalg.vector_norm(a, dim=1).contiguous()
+        systems.append((s, h))
+        trees.append(oracle_mod.Tree(pos, mass, bucket=8, shift=shift))
+    rng = np.random.default_rng(17)
+    reqs = []
+    for r in range(8):
+        k = r % 3
+        s, h = systems[k]
+        size = s.n if (k == 2 and r < 3) else int(rng.integers(1, 3000))
+        ids = rng.choice(s.n, size, replace=False).astype(np.int32)
+        fp = tpm.ForceParams(theta=0.6) if r % 2 else tpm.ForceParams(crit=tpm.CRIT_RELATIVE, alpha=0.002)
+        reqs.append((k, ids, fp))
+    # the oracle walk of every request
+    ref = []
+    for k, ids, fp in reqs:
+        s, h = systems[k]
+        ao = aold[s.handle][torch.from_numpy(ids.astype(np.int64)).to(dev)].cpu().numpy()
+        if fp.crit == tpm.CRIT_RELATIVE:
+            a_o, _, n_o = trees[k].walk(ids, 1.0, h, crit="relative", alpha=fp.alpha, a_old=ao)
+        else:
+            a_o, _, n_o = trees[k].walk(ids, 1.0, h, theta=fp.theta)
+        ref.append((a_o, n_o))
+    yield tpm, torch, dev, ctx, systems, reqs, aold, ref
+    ctx.close()
+
+
+@pytest.mark.parametrize("group", [8, 16, 32])
+@pytest.mark.parametrize("depth", [128, 192, 256])
+def test_batch_matches_oracle_walk(oracle_env, group, depth):
+    """Every group size and stack depth of the persistent batched walk against
+    the oracle's per-particle walk directly (not through the plain call)."""
+    tpm, torch, dev, ctx, systems, reqs, aold, ref = oracle_env
+    ids = np.concatenate([r[1] for r in reqs])
+    off = np.concatenate([[0], np.cumsum([len(r[1]) for r in reqs])])
+    a_old = torch.cat([aold[systems[k][0].handle][torch.from_numpy(i.astype(np.int64)).to(dev)]
+                       for k, i, _ in reqs])
+    plan = ctx.create_plan(int(off[-1]), len(reqs))
+    plan.group_size = group
+    plan.stack_depth = depth
+    acc = torch.empty((len(ids), 3), device=dev)
+    nint = torch.empty(len(ids), dtype=torch.int32, device=dev)
+    plan.compute_forces_batch([systems[k][0] for k, _, _ in reqs], off, [r[2] for r in reqs],
+                              torch.from_numpy(ids).to(dev), acc, a_old=a_old, n_int=nint)
+    plan.sync_status()
+    acc, nint = acc.cpu().numpy(), nint.cpu().numpy()
+    for r, (a_o, n_o) in enumerate(ref):
+        sl = slice(off[r], off[r + 1])
+        try:
+            oracle_check(acc[sl], nint[sl], a_o, n_o)
+        except AssertionError as e:
+            raise AssertionError("request %d (system %d, %d ids, crit %d): %s" % (r, reqs[r][0], len(reqs[r][1]),
+                                                                                   reqs[r][2].crit, e))
     plan.close()

@@ -22,6 +22,7 @@ pytestmark = pytest.mark.gpu
 
 P99_TOL = 2e-5
 MAX_TOL = 2e-4
+ROOT_DIR = __import__("os").path.dirname(__import__("os").path.dirname(__import__("os").path.abspath(__file__)))
 
 
 @pytest.fixture(scope="module")
@@ -147,10 +148,10 @@ def test_depth_cap_with_far_outlier(oracle_mod, tpm, ctx, torch_dev):
     level-21 cell (the depth cap) is 8 wide and holds a large share of the
     Plummer core: leaves of ~500 particles, far beyond the bucket of 8, and a
     walk that is nearly a direct sum.  The tree equals the oracle's bit for
-    bit and every interaction count agrees.  The forces agree for every
-    particle except the 31 that share the outlier's 32-particle walk group:
-    their offsets are rounded to FP32 in that group's 2^24-wide frame (a
-    limit of the group frame, measured at up to 1.75 relative error there)."""
+    bit, every interaction count agrees, and every particle's force is within
+    the FP32 tolerance -- including the 31 that share the outlier's
+    32-particle chunk, whose walk is cut into runs with frames of their own
+    (the chunk's frame would be the whole 2^24-wide root)."""
     n = 4096
     pos, mass = W.plummer(n, 77)
     pos[-1] = [1.0e7, 0.0, 0.0]
@@ -164,17 +165,66 @@ def test_depth_cap_with_far_outlier(oracle_mod, tpm, ctx, torch_dev):
     for k in ("key", "perm", "level", "prefix", "first", "count", "skip", "mass", "com"):
         np.testing.assert_array_equal(ex[k], rx[k], err_msg=k)
     assert ex["count"][ex["level"] == 21].max() > 400
-    # walk groups are 32 consecutive particles in key order (all active)
-    chunk = np.empty(n, np.int64)
-    chunk[ex["perm"].astype(np.int64)] = np.arange(n) // 32
-    ok = chunk != chunk[n - 1]
     acc, pot, nint = s.compute_forces(fp=tpm.ForceParams(crit=tpm.CRIT_BH, theta=0.5))
     s.sync_status()
     s.release()
     a_o, p_o, n_o = ref.walk(np.arange(n), 1.0, 0.01, theta=0.5)
     nint = nint.cpu().numpy()
     np.testing.assert_array_equal(nint, n_o)
-    compare_forces(acc.cpu().numpy().astype(np.float64)[ok], a_o[ok], nint[ok], n_o[ok])
+    compare_forces(acc.cpu().numpy().astype(np.float64), a_o, nint, n_o)
+    np.testing.assert_allclose(pot.cpu().numpy(), p_o, rtol=P99_TOL)
+
+
+@pytest.mark.parametrize("walk", ["group", "lanes"])
+def test_several_far_outliers_every_particle(oracle_mod, tpm, torch_dev, walk, tmp_path):
+    """Two clusters and five isolated particles: one chunk runs from one
+    cluster past four isolated particles into the other, another starts with
+    the farthest particle.  Both criteria: every particle's force and count as
+    the oracle walk's (the lane walk hands cut chunks to the group walk's runs
+    too)."""
+    import subprocess
+    import sys
+
+    out = tmp_path / "o.npz"
+    code = OUTLIER_SCRIPT
+    env = dict(__import__("os").environ, TPM_WALK=walk)
+    r = subprocess.run([sys.executable, "-c", code, str(out)], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    res = np.load(out)
+    pos, mass = W.clusters_with_outliers(4096, 78)
+    shift = tuple(W.root_shift(78))
+    ref = oracle_mod.Tree(pos, mass, bucket=8, shift=shift)
+    a_o, p_o, n_o = ref.walk(np.arange(4096), 1.0, 0.01, theta=0.5)
+    compare_forces(res["acc_bh"].astype(np.float64), a_o, res["n_bh"], n_o)
+    a_old = np.linalg.norm(a_o, axis=1).astype(np.float32)
+    a_r, p_r, n_r = ref.walk(np.arange(4096), 1.0, 0.01, crit="relative", alpha=0.001, a_old=a_old)
+    compare_forces(res["acc_rel"].astype(np.float64), a_r, res["n_rel"], n_r)
+
+
+OUTLIER_SCRIPT = r"""
+import sys
+import numpy as np
+import torch
+sys.path.insert(0, %r)
+import workloads as W
+import paper_1909_04667_gb300 as tpm
+dev = torch.device("cuda", 0)
+ctx = tpm.Context(0)
+pos, mass = W.clusters_with_outliers(4096, 78)
+s = ctx.build_tree(torch.from_numpy(pos).to(dev), torch.from_numpy(mass).to(dev),
+                   tpm.BuildParams(G=1.0, h=0.01, shift=tuple(W.root_shift(78)), leaf_bucket=8))
+a, p, n = s.compute_forces(fp=tpm.ForceParams(crit=tpm.CRIT_BH, theta=0.5))
+s.sync_status()
+out = dict(acc_bh=a.cpu().numpy(), n_bh=n.cpu().numpy())
+import oracle
+ref = oracle.Tree(pos, mass, bucket=8, shift=tuple(W.root_shift(78)))
+a_o, _, _ = ref.walk(np.arange(4096), 1.0, 0.01, theta=0.5)
+a_old = torch.from_numpy(np.linalg.norm(a_o, axis=1).astype(np.float32)).to(dev)
+a, p, n = s.compute_forces(a_old=a_old, fp=tpm.ForceParams(crit=tpm.CRIT_RELATIVE, alpha=0.001))
+s.sync_status()
+out.update(acc_rel=a.cpu().numpy(), n_rel=n.cpu().numpy())
+np.savez(sys.argv[1], **out)
+""" % ROOT_DIR
 
 
 def test_walk_relative_hernquist(oracle_mod, tpm, ctx, torch_dev):

@@ -32,3 +32,12 @@ def test_timebins_give_power_of_two_active_fractions():
 def test_request_sizes_cover_the_set():
     s = W.request_sizes(100000, 7)
     assert s.sum() == 100000 and s.min() >= 1 and s.max() <= 65536
+
+
+def test_clusters_with_outliers_layout():
+    pos, mass = W.clusters_with_outliers(4096, 78)
+    assert pos.shape == (4096, 3) and mass.dtype == np.float32 and abs(mass.sum() - 1.0) < 1e-5
+    far = pos[2030:2035]
+    assert np.all(np.abs(far) >= 300.0) and np.abs(far).max() == 3.0e4
+    np.testing.assert_allclose(pos[:2030].mean(0), -300.0, atol=1.0)
+    np.testing.assert_allclose(pos[2035:].mean(0), 300.0, atol=1.0)

@@ -106,6 +106,20 @@ def hernquist(n: int, seed: int, a: float = 1.0, M: float = 1.0, rmax: float = 1
     return pos.astype(np.float64), mass
 
 
+def clusters_with_outliers(n: int, seed: int, n_a: int = 2030):
+    """Two Plummer clusters (scale 1) 600 units apart per axis, with five
+    isolated particles between them, in different directions (one at 4e4):
+    a stress case for walk frames.  In key order one 32-particle chunk runs
+    from the end of one cluster past four isolated particles into the other
+    cluster, and another starts with the farthest particle."""
+    pa, _ = plummer(n_a, seed)
+    pb, _ = plummer(n - n_a - 5, seed + 1)
+    far = np.array([[300.0, -300.0, -300.0], [-300.0, 300.0, -300.0], [300.0, 300.0, -300.0],
+                    [-300.0, -300.0, 300.0], [3.0e4, -3.0e4, 300.0]])
+    pos = np.concatenate([pa - 300.0, far, pb + 300.0])
+    return pos, np.full(n, 1.0 / n, np.float32)
+
+
 def lattice(ngrid: int, box: float = 1.0) -> np.ndarray:
     """Unperturbed cubic lattice of ngrid^3 points at (i, j, k) * box / ngrid."""
     i = np.arange(ngrid, dtype=np.float64) * (box / ngrid)
