@@ -323,17 +323,41 @@ def pm_potential(pos, mass, box: float, ngrid: int, rs: float, G: float = 1.0) -
     return phi
 
 
-def pm_interpolate(phi: np.ndarray, pos, box: float):
-    """Mesh force by the 4-point finite difference
-    dPhi/dx ~ [4/3 (Phi_{+1} - Phi_{-1}) / 2 - 1/3 (Phi_{+2} - Phi_{-2}) / 4] / dx,
-    a = -grad Phi, then CIC interpolation of a and Phi to the particles."""
+def mesh_forces(phi: np.ndarray, box: float, grad: str = "fd4"):
+    """The three force meshes a = -grad Phi of a periodic potential mesh.
+
+    ``fd4``: the 4-point finite difference (Sec. 3.3 leaves the stencil open)
+      dPhi/dx ~ [4/3 (Phi_{+1} - Phi_{-1}) / 2 - 1/3 (Phi_{+2} - Phi_{-2}) / 4] / dx.
+    ``ik``: the spectral derivative, a_k = -i k Phi_k per axis, with the
+      Nyquist mode of each axis (whose derivative a real mesh cannot carry) set
+      to zero.
+    """
     ngrid = phi.shape[0]
     dx = box / ngrid
-    grads = []
-    for ax in range(3):
-        d1 = np.roll(phi, -1, axis=ax) - np.roll(phi, 1, axis=ax)
-        d2 = np.roll(phi, -2, axis=ax) - np.roll(phi, 2, axis=ax)
-        grads.append(-((4.0 / 3.0) * d1 / 2.0 - (1.0 / 3.0) * d2 / 4.0) / dx)
+    if grad == "fd4":
+        out = []
+        for ax in range(3):
+            d1 = np.roll(phi, -1, axis=ax) - np.roll(phi, 1, axis=ax)
+            d2 = np.roll(phi, -2, axis=ax) - np.roll(phi, 2, axis=ax)
+            out.append(-((4.0 / 3.0) * d1 / 2.0 - (1.0 / 3.0) * d2 / 4.0) / dx)
+        return out
+    if grad != "ik":
+        raise ValueError("grad must be 'fd4' or 'ik'")
+    phik = np.fft.rfftn(phi)
+    kf = 2.0 * math.pi / box
+    n = np.fft.fftfreq(ngrid, d=1.0 / ngrid)
+    nz = np.fft.rfftfreq(ngrid, d=1.0 / ngrid)
+    n = np.where(np.abs(n) == ngrid // 2, 0.0, n)
+    nz = np.where(nz == ngrid // 2, 0.0, nz)
+    ks = [(kf * n)[:, None, None], (kf * n)[None, :, None], (kf * nz)[None, None, :]]
+    return [np.fft.irfftn(-1j * k * phik, s=phi.shape, axes=(0, 1, 2)) for k in ks]
+
+
+def pm_interpolate(phi: np.ndarray, pos, box: float, grad: str = "fd4"):
+    """Mesh force -grad Phi (``mesh_forces``: 4-point difference or spectral),
+    then CIC interpolation of the force and of Phi to the particles."""
+    ngrid = phi.shape[0]
+    grads = mesh_forces(phi, box, grad)
     fields = [g.ravel() for g in grads] + [phi.ravel()]
     i0, f = _cic_weights(pos, box, ngrid)
     out = np.zeros((len(i0), 4))
@@ -355,15 +379,16 @@ def pm_interpolate(phi: np.ndarray, pos, box: float):
 
 def treepm(pos, mass, targets, box: float, ngrid: int, asmth: float, rcut_cells: float, G: float, h: float,
            crit: str = "bh", theta: float = 0.5, alpha: float = 0.005, a_old=None, bucket: int = 8,
-           shift=(0.0, 0.0, 0.0), nthreads: int = 0):
-    """Periodic TreePM force (Sec. 3.4): short-range tree walk plus PM."""
+           shift=(0.0, 0.0, 0.0), nthreads: int = 0, grad: str = "fd4"):
+    """Periodic TreePM force (Sec. 3.4): short-range tree walk plus PM (mesh
+    force by ``grad``: the 4-point difference or the spectral derivative)."""
     rs = asmth * box / ngrid
     rcut = rcut_cells * rs
     tree = Tree(pos, mass, bucket=bucket, periodic=True, box=box, shift=shift)
     a_s, p_s, nint = tree.walk(targets, G, h, crit=crit, theta=theta, alpha=alpha, a_old=a_old, treepm=True, rs=rs,
                                rcut=rcut, nthreads=nthreads)
     phi = pm_potential(pos, mass, box, ngrid, rs, G)
-    a_l, p_l = pm_interpolate(phi, np.asarray(pos)[np.asarray(targets, dtype=np.int64)], box)
+    a_l, p_l = pm_interpolate(phi, np.asarray(pos)[np.asarray(targets, dtype=np.int64)], box, grad)
     return a_s + a_l, p_s + p_l, nint
 
 

@@ -313,7 +313,53 @@ def test_pm_long_range_plane_wave(oracle_mod):
     assert np.abs(a[:, 1:]).max() < 1e-6 * amp
 
 
-def test_pm_pair_force_matches_long_range_closed_form(oracle_mod):
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_mesh_forces_single_mode_closed_forms(oracle_mod, axis):
+    # Phi = A cos(k x_a + p) on the mesh nodes: the spectral derivative gives
+    # -dPhi/dx_a = A k sin(k x_a + p) exactly, the 4-point difference gives it
+    # times its transfer function (4/3 sin(k dx) - 1/6 sin(2 k dx)) / (k dx);
+    # the other components vanish
+    ng, m, A, p = 32, 3, 0.7, 0.4
+    x = np.arange(ng) / ng
+    k = 2 * math.pi * m
+    shape = [1, 1, 1]
+    shape[axis] = ng
+    phi = np.broadcast_to((A * np.cos(k * x + p)).reshape(shape), (ng, ng, ng)).copy()
+    want = np.broadcast_to((A * k * np.sin(k * x + p)).reshape(shape), (ng, ng, ng))
+    f_ik = oracle_mod.mesh_forces(phi, 1.0, "ik")
+    np.testing.assert_allclose(f_ik[axis], want, atol=1e-12 * A * k)
+    kdx = k / ng
+    tf = ((4.0 / 3.0) * math.sin(kdx) - (1.0 / 6.0) * math.sin(2 * kdx)) / kdx
+    f_fd = oracle_mod.mesh_forces(phi, 1.0, "fd4")
+    np.testing.assert_allclose(f_fd[axis], tf * want, atol=1e-12 * A * k)
+    for other in range(3):
+        if other != axis:
+            assert np.abs(f_ik[other]).max() < 1e-12 * A * k
+            assert np.abs(f_fd[other]).max() < 1e-12 * A * k
+    # the Nyquist mode (alternating signs) has no derivative on a real mesh
+    nyq = np.broadcast_to(((-1.0) ** np.arange(ng)).reshape(shape), (ng, ng, ng)).copy()
+    assert np.abs(oracle_mod.mesh_forces(nyq, 1.0, "ik")[axis]).max() < 1e-12
+
+
+def test_pm_long_range_plane_wave_spectral(oracle_mod):
+    # the linear plane wave of test_pm_long_range_plane_wave with the spectral
+    # gradient: the same filtered closed form
+    n, ng = 32, 64
+    pos, psi = plane_wave(n, 1e-3, mode=3, offset=0.5 / ng)
+    mass = np.full(n ** 3, 1.0 / n ** 3, np.float32)
+    rs = 1.25 / ng
+    phi = oracle_mod.pm_potential(pos, mass, 1.0, ng, rs)
+    tg = np.arange(0, n ** 3, 3)
+    a, _ = oracle_mod.pm_interpolate(phi, pos[tg], 1.0, grad="ik")
+    k = 2 * math.pi * 3
+    lin = 4 * math.pi * psi[tg] * math.exp(-k * k * rs * rs)
+    amp = np.abs(lin).max()
+    assert np.abs(a[:, 0] - lin).max() < 5e-3 * amp
+    assert np.abs(a[:, 1:]).max() < 1e-6 * amp
+
+
+@pytest.mark.parametrize("grad", ["fd4", "ik"])
+def test_pm_pair_force_matches_long_range_closed_form(oracle_mod, grad):
     # one unit mass: the mesh force at r = 2..4 r_s must follow the long-range
     # closed form g_l(r) / r^2, g_l = erf(x) - 2x/sqrt(pi) e^{-x^2}, x = r/2r_s,
     # less the uniform background's pull (4 pi / 3) r (periodic box, mean
@@ -332,7 +378,7 @@ def test_pm_pair_force_matches_long_range_closed_form(oracle_mod):
             mass = np.zeros(len(pos), np.float32)
             mass[0] = 1.0
             phi = oracle_mod.pm_potential(pos, mass, 1.0, ng, rs)
-            a, _ = oracle_mod.pm_interpolate(phi, probes, 1.0)
+            a, _ = oracle_mod.pm_interpolate(phi, probes, 1.0, grad=grad)
             x = r / (2 * rs)
             gl = math.erf(x) - 2 * x / math.sqrt(math.pi) * math.exp(-x * x)
             expect = gl / r ** 2 - 4 * math.pi / 3 * r
