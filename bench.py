@@ -61,6 +61,7 @@ def walk_capture():
 
 # ------------------------------------------------------------------ configs
 HERNQUIST = dict(n=1 << 20, seed=W.CONFIG_SEEDS[2], h=0.005, G=1.0, bucket=8, theta=0.5, alpha=0.0025)
+PLUMMER = dict(n=8192, h=0.01, G=1.0, bucket=8, theta=0.7)
 SERVING = dict(seed=W.CONFIG_SEEDS[5], budget_gb=60, n_requests=2000, warmup_requests=4000, rate=200.0,
                load_factors=(1, 8), nmin=1 << 12, nmax=1 << 20, overcommit=1.5, bytes_per_particle=118,
                round_ids=1 << 21)
@@ -164,6 +165,46 @@ def l2_flush(buf):
     buf.zero_()
 
 
+EXACT_SUMS = os.path.join(ROOT, "tests", "golden", "exact_sums.npz")
+EXACT_DESC = {
+    "hernquist": "FP64 softened direct sum (oracle), 4096 seeded targets",
+    "zeldovich": "FP64 Ewald sum with neutralising background (oracle), 2048 seeded targets",
+    "two_species": "FP64 direct sum with the larger of the two supports (oracle), 4096 seeded targets",
+    "plummer": "FP64 softened direct sum (oracle), all 8192 particles",
+}
+
+
+def exact_sums():
+    """The stored exact forces (tests/golden/make_exact_sums.py writes them
+    with the FP64 oracle), or None."""
+    try:
+        with np.load(EXACT_SUMS) as f:
+            return {k: f[k] for k in f.files}
+    except Exception:
+        return None
+
+
+def error_stats(acc, exact) -> dict:
+    """Relative force error |a - a_exact| / |a_exact| over the targets."""
+    e = np.linalg.norm(np.asarray(acc, np.float64) - exact, axis=1) / np.linalg.norm(exact, axis=1)
+    return {"p50": float(np.percentile(e, 50)), "p90": float(np.percentile(e, 90)),
+            "p99": float(np.percentile(e, 99)), "max": float(e.max()), "targets": int(len(e)),
+            "p99_within_5e-3": bool(np.percentile(e, 99) <= 5e-3)}
+
+
+def accuracy_at(acc_dev, name) -> dict:
+    """Accuracy of forces computed for all particles (device tensor, caller's
+    order) against the stored exact sums of workload `name`."""
+    ex = exact_sums()
+    if ex is None or name + "_targets" not in ex:
+        return {"unavailable": "stored exact sums missing (run tests/golden/make_exact_sums.py)"}
+    tg = ex[name + "_targets"].astype(np.int64)
+    import torch
+
+    got = acc_dev[torch.from_numpy(tg).to(acc_dev.device)].cpu().numpy()
+    return dict(error_stats(got, ex[name + "_acc"]), reference=EXACT_DESC[name])
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args, rank, world):
     import torch
@@ -239,6 +280,16 @@ def run_ours(args, rank, world):
     interactions = int(nint_buf.to(torch.int64).sum().item())
     walk_ms = statistics.mean(t_walk)
     build_ms = statistics.mean(t_build)
+    # accuracy of the last timed step against the exact sum; the oracle walk's
+    # floor on the same targets (same tree shift and |a_old|) is added by the
+    # cpu_baseline leg
+    accuracy = accuracy_at(acc_buf, "hernquist")
+    ex = exact_sums()
+    floor_ctx = None
+    if ex is not None:
+        tg = ex["hernquist_targets"].astype(np.int64)
+        floor_ctx = {"shift": root_shift(1000 + args.steps - 1, 2), "targets": tg,
+                     "a_old": a_old[torch.from_numpy(tg).to(dev)].cpu().numpy()}
 
     # ---------------- FP64 conservation diagnostics of one relative step (untimed)
     sy = ctx.build_tree(pos_d, mass_d, bp(9999))
@@ -275,6 +326,8 @@ def run_ours(args, rank, world):
     # ---------------- periodic TreePM box (128^3, PM 256^3)
     periodic = None if args.no_periodic else run_periodic(ctx, tpm, torch, dev, stream, flush,
                                                           max(2, min(args.steps, 5)))
+    periodic_ik = None if args.no_periodic else run_periodic(ctx, tpm, torch, dev, stream, flush,
+                                                             max(2, min(args.steps, 5)), grad="ik")
     batching = None if args.no_batching else run_batching(ctx, tpm, torch, dev, stream, pos_d, mass_d)
     hierarchy = None if args.no_hierarchy else run_hierarchy(ctx, tpm, torch, dev, stream)
     isolated = None if args.no_isolated else run_isolated(ctx, tpm, torch, dev, stream, flush, pos_d, mass_d,
@@ -282,6 +335,7 @@ def run_ours(args, rank, world):
     ewald = None if args.no_ewald else run_ewald(ctx, tpm, torch, dev, stream, flush, max(2, min(args.steps, 3)))
     species = None if args.no_species else run_two_species(ctx, tpm, torch, dev, stream, flush,
                                                            max(2, min(args.steps, 5)))
+    plummer = run_plummer(ctx, tpm, torch, dev, stream, flush, max(3, min(args.steps, 10)))
 
     ctx.close()
     serving = None if args.no_serving else run_serving(tpm, torch, dev)
@@ -314,15 +368,19 @@ def run_ours(args, rank, world):
                   "algorithmic": "%d flops x %d useful interactions per launch" % (FLOPS_PER_INTERACTION,
                                                                                     interactions)},
         gpu_launches=int(k1 - k0),
+        accuracy=accuracy,
+        _floor_ctx=floor_ctx,
         diagnostics=diagnostics,
         cub_calls=int(c1 - c0),
         clocks=clocks,
         periodic_treepm=periodic,
+        periodic_treepm_spectral=periodic_ik,
         batching=batching,
         hierarchy=hierarchy,
         isolated_treepm=isolated,
         periodic_ewald_tree=ewald,
         two_species_softening=species,
+        plummer_8192=plummer,
         serving=serving,
     )
 
@@ -546,7 +604,10 @@ def run_serving(tpm, torch, dev):
     return res
 
 
-def run_periodic(ctx, tpm, torch, dev, stream, flush, steps):
+def run_periodic(ctx, tpm, torch, dev, stream, flush, steps, grad="fd4"):
+    """The periodic TreePM box: one step = build + mesh + short-range relative
+    walk with interpolation; mesh force by the 4-point difference (`fd4`) or
+    the spectral derivative (`ik`)."""
     cfg = ZELDOVICH
     pos, mass = zeldovich_inputs()
     n = len(pos)
@@ -555,7 +616,8 @@ def run_periodic(ctx, tpm, torch, dev, stream, flush, steps):
     h = zeldovich_h()
     bp = lambda k: tpm.BuildParams(G=cfg["G"], h=h, periodic=True, box=1.0, shift=root_shift(k, 3),
                                    leaf_bucket=cfg["bucket"])
-    common = dict(treepm=True, pm_n=cfg["pm_n"], asmth=cfg["asmth"], rcut=cfg["rcut"])
+    common = dict(treepm=True, pm_n=cfg["pm_n"], asmth=cfg["asmth"], rcut=cfg["rcut"],
+                  pm_grad=tpm.GRAD_IK if grad == "ik" else tpm.GRAD_FD4)
     fp_bh = tpm.ForceParams(crit=tpm.CRIT_BH, theta=cfg["theta"], **common)
     fp_rel = tpm.ForceParams(crit=tpm.CRIT_RELATIVE, alpha=cfg["alpha"], **common)
     s = ctx.build_tree(pos_d, mass_d, bp(0))
@@ -584,9 +646,44 @@ def run_periodic(ctx, tpm, torch, dev, stream, flush, steps):
     r = np.array(res).mean(0)
     ms = float(r.sum())
     inter = int(nint_b.to(torch.int64).sum().item())
-    return {"workload": "zeldovich_128^3_pm256_relative_alpha0.005", "value": n / (ms * 1e-3), "unit": "forces/s",
+    return {"workload": "zeldovich_128^3_pm256_%s_relative_alpha0.005" % grad, "value": n / (ms * 1e-3),
+            "unit": "forces/s",
             "ms_per_step": ms, "build_ms": float(r[0]), "pm_ms": float(r[1]), "walk_interp_ms": float(r[2]),
-            "interactions_per_particle": inter / n}
+            "interactions_per_particle": inter / n, "accuracy": accuracy_at(acc_b, "zeldovich")}
+
+
+def run_plummer(ctx, tpm, torch, dev, stream, flush, steps):
+    """The Plummer sphere, N = 8192, support 0.01, all active, geometric
+    criterion theta = 0.7: one step = build + walk."""
+    cfg = PLUMMER
+    pos, mass = W.plummer(cfg["n"], W.CONFIG_SEEDS[1])
+    n = len(pos)
+    pos_d, mass_d = torch.from_numpy(pos).to(dev), torch.from_numpy(mass).to(dev)
+    bp = lambda k: tpm.BuildParams(G=cfg["G"], h=cfg["h"], shift=root_shift(k, 1), leaf_bucket=cfg["bucket"])
+    fp = tpm.ForceParams(crit=tpm.CRIT_BH, theta=cfg["theta"])
+    acc = torch.empty((n, 3), device=dev)
+    pot = torch.empty(n, device=dev)
+    nint = torch.empty(n, dtype=torch.int32, device=dev)
+    res = []
+    for k in range(steps + 3):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        l2_flush(flush)
+        ev[0].record(stream)
+        sy = ctx.build_tree(pos_d, mass_d, bp(100 + k))
+        ev[1].record(stream)
+        sy.compute_forces(fp=fp, acc=acc, pot=pot, n_int=nint)
+        ev[2].record(stream)
+        sy.release()
+        torch.cuda.synchronize()
+        if k >= 3:
+            res.append([ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])])
+    r = np.array(res).mean(0)
+    ms = float(r.sum())
+    inter = int(nint.to(torch.int64).sum().item())
+    return {"workload": "plummer_n8192_bh_theta%g" % cfg["theta"], "value": n / (ms * 1e-3), "unit": "forces/s",
+            "ms_per_step": ms, "build_ms": float(r[0]), "walk_ms": float(r[1]),
+            "interactions_per_particle": inter / n, "accuracy": accuracy_at(acc, "plummer"),
+            "note": "a small system: launch and latency bound, not a throughput figure"}
 
 
 def run_ewald(ctx, tpm, torch, dev, stream, flush, steps):
@@ -624,7 +721,7 @@ def run_ewald(ctx, tpm, torch, dev, stream, flush, steps):
     inter = int(nint.to(torch.int64).sum().item())
     return {"workload": "zeldovich_128^3_ewald_tree_relative_alpha%g" % cfg["alpha"], "value": n / (ms * 1e-3),
             "unit": "forces/s", "ms_per_step": ms, "build_ms": float(r[0]), "walk_ms": float(r[1]),
-            "interactions_per_particle": inter / n}
+            "interactions_per_particle": inter / n, "accuracy": accuracy_at(acc, "zeldovich")}
 
 
 def run_two_species(ctx, tpm, torch, dev, stream, flush, steps):
@@ -660,7 +757,8 @@ def run_two_species(ctx, tpm, torch, dev, stream, flush, steps):
     inter = int(nint.to(torch.int64).sum().item())
     return {"workload": "two_species_hernquist2^20_h0.005_plummer2^18_h0.001_relative_alpha%g" % cfg["alpha"],
             "value": n / (ms * 1e-3), "unit": "forces/s", "ms_per_step": ms, "build_ms": float(r[0]),
-            "walk_ms": float(r[1]), "interactions_per_particle": inter / n}
+            "walk_ms": float(r[1]), "interactions_per_particle": inter / n,
+            "accuracy": accuracy_at(acc, "two_species")}
 
 
 def run_isolated(ctx, tpm, torch, dev, stream, flush, pos_d, mass_d, steps):
@@ -699,7 +797,8 @@ def run_isolated(ctx, tpm, torch, dev, stream, flush, pos_d, mass_d, steps):
     return {"workload": "hernquist_n2^20_treepm_open_pm%d_padded%d^3_asmth%g_relative_alpha%g" % (
                 ic["pm_n"], 2 * ic["pm_n"], ic["asmth"], cfg["alpha"]),
             "value": n / (ms * 1e-3), "unit": "forces/s", "ms_per_step": ms, "build_ms": float(r[0]),
-            "pm_ms": float(r[1]), "walk_interp_ms": float(r[2]), "interactions_per_particle": inter / n}
+            "pm_ms": float(r[1]), "walk_interp_ms": float(r[2]), "interactions_per_particle": inter / n,
+            "accuracy": accuracy_at(acc, "hernquist")}
 
 
 def run_profile(name):
@@ -769,6 +868,21 @@ def run_oracle_sample(sample: int, nthreads: int = 0):
     t_step = t_build + t_walk * n / len(tg)
     return dict(value=n / t_step, unit="forces/s", t_build=t_build, t_walk_sample=t_walk, sample=len(tg),
                 interactions_per_particle=float(nint.mean()))
+
+
+def oracle_floor(ctx) -> dict:
+    """The FP64 oracle walk on the accuracy targets of the headline step (the
+    same tree shift and |a_old|) against the stored exact sum: the method's
+    own error, which the GPU walk reproduces up to FP32 rounding."""
+    import oracle
+
+    cfg = HERNQUIST
+    pos, mass = hernquist_inputs()
+    tree = oracle.Tree(pos, mass, bucket=cfg["bucket"], shift=ctx["shift"])
+    a, _, _ = tree.walk(ctx["targets"].astype(np.uint32), cfg["G"], cfg["h"], crit="rel", alpha=cfg["alpha"],
+                        a_old=ctx["a_old"].astype(np.float32))
+    ex = exact_sums()
+    return error_stats(a, ex["hernquist_acc"])
 
 
 def cores():
@@ -860,10 +974,13 @@ def main():
         torch.distributed.init_process_group("nccl")
     out = run_ours(args, rank, world)
     if rank == 0:
+        floor_ctx = out.pop("_floor_ctx", None)
         if not args.no_cpu_baseline:
             import oracle
 
             oracle.build()
+            if floor_ctx is not None and isinstance(out.get("accuracy"), dict) and "p99" in out["accuracy"]:
+                out["accuracy"]["oracle_walk_floor"] = oracle_floor(floor_ctx)
             r = run_oracle_sample(65536)
             r1 = run_oracle_sample(4096, nthreads=1)
             out["cpu_baseline"] = {"value": r["value"], "unit": "forces/s", "cores": cores(), "kind": "oracle",

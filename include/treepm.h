@@ -48,7 +48,7 @@
 extern "C" {
 #endif
 
-#define TPM_API_VERSION 1
+#define TPM_API_VERSION 2
 
 typedef struct tpm_ctx tpm_ctx; /* opaque: device, memory pool, resident systems */
 typedef uint64_t tpm_sys;       /* handle of a resident particle system; 0 is never valid */
@@ -91,7 +91,14 @@ typedef struct {
     int32_t pm_n;       /* PMGRID: mesh points per side (power of two, 8..1024) */
     double asmth;       /* ASMTH a_s: split scale r_s = a_s box / pm_n */
     double rcut;        /* RCUT a_cut: tree cutoff radius a_cut r_s */
+    int32_t pm_grad;    /* mesh force of a periodic system (Sec. 3.3 leaves the stencil open):
+                           TPM_GRAD_FD4 (0) the 4-point finite difference of the potential mesh,
+                           TPM_GRAD_IK (1) the spectral derivative -i k Phi_k (three more inverse
+                           transforms, three force meshes kept with the system) */
 } tpm_force_params;
+
+#define TPM_GRAD_FD4 0
+#define TPM_GRAD_IK 1
 
 /* Version of this header the library was built from (TPM_API_VERSION). */
 int tpm_version(void);
@@ -165,11 +172,15 @@ int tpm_build_tree_soft(tpm_ctx *ctx, const double *pos, const float *mass, cons
  * bounding box (dx = L0 / pm_n), inside a zero-padded (2 pm_n)^3 mesh; the
  * potential is the convolution of the CIC masses with the long-range kernel
  * -G erf(r / 2 r_s) / r sampled at the padded mesh's circular separations,
- * divided by W(k)^2 in k-space, k = 0 kept (pm_n <= 512).  Both: 4-point
- * finite-difference force meshes.  The meshes stay with the system until the
- * next call or release; tpm_compute_forces with treepm = 1 interpolates from
- * them.  Errors: TPM_EINVAL (treepm = 0, bad pm_n / asmth / rcut),
- * TPM_ENOSYS_HANDLE, TPM_EBUDGET, TPM_ECUDA.
+ * divided by W(k)^2 in k-space, k = 0 kept (pm_n <= 512).  The mesh force is
+ * the 4-point finite difference of the potential mesh, or for a periodic
+ * system with pm_grad = TPM_GRAD_IK the spectral derivative: a_k = -i k_a
+ * Phi_k per axis (the Nyquist mode of each axis set to zero), three more
+ * inverse transforms into three force meshes.  The meshes stay with the
+ * system until the next call or release; tpm_compute_forces with treepm = 1
+ * interpolates from them (the call's pm_grad must match).  Errors: TPM_EINVAL
+ * (treepm = 0, bad pm_n / asmth / rcut / pm_grad, pm_grad = TPM_GRAD_IK on
+ * an open system), TPM_ENOSYS_HANDLE, TPM_EBUDGET, TPM_ECUDA.
  */
 int tpm_pm_long_range(tpm_ctx *ctx, tpm_sys s, const tpm_force_params *p, void *stream);
 

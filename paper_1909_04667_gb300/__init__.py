@@ -22,10 +22,12 @@ import numpy as np
 from . import _build
 
 __all__ = ["Context", "System", "Plan", "BuildParams", "ForceParams", "StepParams", "TreePMError", "lib_path",
-           "CRIT_BH", "CRIT_RELATIVE", "BATCH_PRESORTED"]
+           "CRIT_BH", "CRIT_RELATIVE", "BATCH_PRESORTED", "GRAD_FD4", "GRAD_IK"]
 
 CRIT_BH = 0
 CRIT_RELATIVE = 1
+GRAD_FD4 = 0  # TPM_GRAD_FD4
+GRAD_IK = 1   # TPM_GRAD_IK
 NOALLOC_MAX_ACTIVE = 1 << 18  # TPM_NOALLOC_MAX_ACTIVE
 
 _STATUS = {0: "TPM_OK", -1: "TPM_EINVAL", -2: "TPM_EBUDGET", -3: "TPM_ENOSYS_HANDLE", -4: "TPM_ECUDA",
@@ -45,7 +47,8 @@ class _BuildParams(C.Structure):
 
 class _ForceParams(C.Structure):
     _fields_ = [("crit", C.c_int32), ("theta", C.c_double), ("alpha", C.c_double), ("box_guard", C.c_int32),
-                ("treepm", C.c_int32), ("pm_n", C.c_int32), ("asmth", C.c_double), ("rcut", C.c_double)]
+                ("treepm", C.c_int32), ("pm_n", C.c_int32), ("asmth", C.c_double), ("rcut", C.c_double),
+                ("pm_grad", C.c_int32)]
 
 
 class _StepParams(C.Structure):
@@ -161,10 +164,11 @@ class ForceParams:
     pm_n: int = 256
     asmth: float = 1.25
     rcut: float = 4.5
+    pm_grad: int = 0  # GRAD_FD4 or GRAD_IK (periodic systems)
 
     def _c(self):
         return _ForceParams(int(self.crit), self.theta, self.alpha, int(self.box_guard), int(self.treepm),
-                            int(self.pm_n), self.asmth, self.rcut)
+                            int(self.pm_n), self.asmth, self.rcut, int(self.pm_grad))
 
 
 @dataclass

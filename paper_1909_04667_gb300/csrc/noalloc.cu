@@ -133,7 +133,7 @@ extern "C" int tpm_compute_forces_noalloc(tpm_ctx *h, tpm_sys sid, const uint32_
         set_error("the relative criterion needs a_old");
         return TPM_EINVAL;
     }
-    if (p->treepm && (!s->phi || s->pm_n != p->pm_n)) {
+    if (p->treepm && (!s->phi || s->pm_n != p->pm_n || s->pm_grad != p->pm_grad)) {
         set_error("no long-range mesh for these parameters: call tpm_pm_long_range first");
         return TPM_EINVAL;
     }

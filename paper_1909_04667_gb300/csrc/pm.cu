@@ -144,6 +144,30 @@ __global__ void __launch_bounds__(kGreenThreads)
     }
 }
 
+// The spectral mesh force of one axis: out = -i k_a Phi_k on the half
+// spectrum [ng][ng][ng/2+1] (Phi_k already carries the Green's function and
+// the inverse transform's 1/ng^3); the Nyquist mode of the axis, whose
+// derivative a real mesh cannot carry, gets zero.
+__global__ void __launch_bounds__(kGreenThreads)
+    k_spec_grad(const cufftComplex *__restrict__ spec, cufftComplex *__restrict__ out, int ng, int axis,
+                float kfund) {
+    const int nzh = ng / 2 + 1;
+    const int64_t rows = (int64_t)ng * ng;
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (int64_t r = (int64_t)blockIdx.x * wpb + (threadIdx.x >> 5); r < rows; r += (int64_t)gridDim.x * wpb) {
+        const int ix = (int)(r / ng), iy = (int)(r - (int64_t)ix * ng);
+        const int nx = ix < ng / 2 ? ix : ix - ng, ny = iy < ng / 2 ? iy : iy - ng;
+        const cufftComplex *__restrict__ row = spec + r * nzh;
+        cufftComplex *__restrict__ orow = out + r * nzh;
+        for (int iz = lane; iz < nzh; iz += 32) {
+            const int n = axis == 0 ? nx : axis == 1 ? ny : iz;
+            const float k = (2 * n == ng || 2 * n == -ng) ? 0.0f : kfund * (float)n;
+            const cufftComplex v = row[iz];
+            orow[iz] = make_float2(k * v.y, -k * v.x);  // -i k (re + i im)
+        }
+    }
+}
+
 // Open boundaries: CIC masses (not densities) into the corner ng^3 block of
 // the zero-padded n2^3 mesh; mesh point i sits at corner + i / cells_per_len.
 // Positions lie inside the block with a margin (no wrap needed).
@@ -344,6 +368,49 @@ __global__ void __launch_bounds__(kThreads, 4) k_pm_interp(const float *__restri
         pot[out] = ph;
 }
 
+// K8 with the spectral force meshes (periodic): CIC interpolation of the
+// three force meshes and the potential mesh, 32 loads per particle.
+__global__ void __launch_bounds__(kThreads, 4)
+    k_pm_interp_meshes(const float *__restrict__ phi, const float *__restrict__ fm, int ng, double cells_per_len,
+                       const double *__restrict__ pos, const uint32_t *__restrict__ perm,
+                       const uint32_t *__restrict__ sidx, const uint32_t *__restrict__ slot, int64_t n_act,
+                       float *__restrict__ acc, float *__restrict__ pot) {
+    int64_t gi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (gi >= n_act)
+        return;
+    const uint32_t s = sidx ? sidx[gi] : (uint32_t)gi;
+    const uint32_t out = slot ? slot[gi] : perm[s];
+    const uint32_t j = perm[s];
+    int i0[3], i1[3];
+    float f[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        const double t = pos[3 * j + a] * cells_per_len;
+        const double fl = floor(t);
+        f[a] = (float)(t - fl);
+        i0[a] = wrapi((int)fl, ng);
+        i1[a] = wrapi(i0[a] + 1, ng);
+    }
+    const size_t cell = (size_t)ng * ng * ng;
+    float ph = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+        const int ix = (c & 4) ? i1[0] : i0[0], iy = (c & 2) ? i1[1] : i0[1], iz = (c & 1) ? i1[2] : i0[2];
+        const float w = ((c & 4) ? f[0] : 1.0f - f[0]) * ((c & 2) ? f[1] : 1.0f - f[1]) *
+                        ((c & 1) ? f[2] : 1.0f - f[2]);
+        const size_t q = ((size_t)ix * ng + iy) * ng + iz;
+        ph = fmaf(w, __ldg(&phi[q]), ph);
+        gx = fmaf(w, __ldg(&fm[q]), gx);
+        gy = fmaf(w, __ldg(&fm[cell + q]), gy);
+        gz = fmaf(w, __ldg(&fm[2 * cell + q]), gz);
+    }
+    acc[3 * (size_t)out] = gx;
+    acc[3 * (size_t)out + 1] = gy;
+    acc[3 * (size_t)out + 2] = gz;
+    if (pot)
+        pot[out] = ph;
+}
+
 // cuFFT plans for an m^3 mesh (R2C and C2R), cached.
 int fft_plans_for(Ctx *c, int m, cufftHandle *fwd, cufftHandle *inv) {
     std::lock_guard<std::mutex> lk(c->mu);
@@ -435,6 +502,7 @@ int pm_solve_iso(Ctx *c, System *s, const tpm_force_params *p, cudaStream_t st) 
         s->pm_mesh = n2;
     }
     s->pm_n = ng;
+    s->pm_grad = TPM_GRAD_FD4;
     for (int a = 0; a < 3; a++)  // the region: a root-sized cube centred on the bounding box
         s->pm_corner[a] = (s->bb_lo[a] + s->bb_hi[a]) * 0.5 - 0.5 * side;
     AllocSet tmp;
@@ -482,14 +550,19 @@ int pm_solve_device(Ctx *c, System *s, const tpm_force_params *p, cudaStream_t s
     const int64_t nspec = (int64_t)ng * ng * (ng / 2 + 1);
     cufftHandle fwd, inv;
     TPM_CHECK(fft_plans_for(c, ng, &fwd, &inv));
-    if (s->pm_mesh != ng) {
+    const bool ik = p->pm_grad == TPM_GRAD_IK;
+    if (s->pm_mesh != ng || (ik && !s->fmesh)) {
         s->pm_mem.release(st);
         s->phi = nullptr;
+        s->fmesh = nullptr;
         s->pm_mem.ctx = c;
         TPM_CHECK(s->pm_mem.get(&s->phi, ncell, st));
+        if (ik)
+            TPM_CHECK(s->pm_mem.get(&s->fmesh, 3 * ncell, st));
         s->pm_mesh = ng;
     }
     s->pm_n = ng;
+    s->pm_grad = p->pm_grad;
     AllocSet tmp;
     tmp.ctx = c;
     struct Guard {
@@ -517,7 +590,25 @@ int pm_solve_device(Ctx *c, System *s, const tpm_force_params *p, cudaStream_t s
         spec, ng, (float)(2.0 * kPi / box), (float)(rs * rs), (float)pref);
     count_launch();
     TPM_CUDA(cudaGetLastError());
-    if (cufftSetStream(inv, st) != CUFFT_SUCCESS || cufftExecC2R(inv, spec, s->phi) != CUFFT_SUCCESS) {
+    if (cufftSetStream(inv, st) != CUFFT_SUCCESS) {
+        set_error("cufftSetStream failed");
+        return TPM_ECUDA;
+    }
+    if (ik) {  // the force spectra first: the inverse transform may overwrite its input
+        cufftComplex *gspec;
+        TPM_CHECK(tmp.get(&gspec, nspec, st));
+        for (int a = 0; a < 3; a++) {
+            k_spec_grad<<<(unsigned)(c->num_sms * 8), kGreenThreads, 0, st>>>(spec, gspec, ng, a,
+                                                                              (float)(2.0 * kPi / box));
+            count_launch();
+            TPM_CUDA(cudaGetLastError());
+            if (cufftExecC2R(inv, gspec, s->fmesh + a * ncell) != CUFFT_SUCCESS) {
+                set_error("cufftExecC2R (force mesh) failed");
+                return TPM_ECUDA;
+            }
+        }
+    }
+    if (cufftExecC2R(inv, spec, s->phi) != CUFFT_SUCCESS) {
         set_error("cufftExecC2R failed");
         return TPM_ECUDA;
     }
@@ -540,6 +631,13 @@ int pm_interp_device(Ctx *, const System *s, const WalkRequest &r, cudaStream_t 
     }
     const int ng = s->pm_n;
     const double box = s->bp.box;
+    if (s->pm_grad == TPM_GRAD_IK) {
+        k_pm_interp_meshes<<<(unsigned)((r.n_act + kThreads - 1) / kThreads), kThreads, 0, st>>>(
+            s->phi, s->fmesh, ng, ng / box, s->pos, s->perm, r.sorted_idx, r.slot, r.n_act, r.acc, r.pot);
+        count_launch();
+        TPM_CUDA(cudaGetLastError());
+        return TPM_OK;
+    }
     k_pm_interp<<<(unsigned)((r.n_act + kThreads - 1) / kThreads), kThreads, 0, st>>>(
         s->phi, ng, ng / box, (float)(ng / box), s->pos, s->perm, r.sorted_idx, r.slot, r.n_act, r.acc, r.pot);
     count_launch();

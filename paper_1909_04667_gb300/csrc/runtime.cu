@@ -171,6 +171,14 @@ int check_force_params(const System *s, const tpm_force_params *p) {
             set_error("cutoff radius must stay below a quarter of the box");
             return TPM_EINVAL;
         }
+        if (p->pm_grad != TPM_GRAD_FD4 && p->pm_grad != TPM_GRAD_IK) {
+            set_error("pm_grad must be TPM_GRAD_FD4 or TPM_GRAD_IK");
+            return TPM_EINVAL;
+        }
+        if (s && !s->bp.periodic && p->pm_grad != TPM_GRAD_FD4) {
+            set_error("the spectral mesh gradient is available for periodic systems");
+            return TPM_EINVAL;
+        }
     }
     return TPM_OK;
 }
@@ -485,7 +493,8 @@ int tpm_compute_forces(tpm_ctx *h, tpm_sys sid, const uint32_t *active_ids, int6
     }
     if (p->treepm) {
         const double rs = p->asmth * pm_side(s) / p->pm_n;
-        if (!s->phi || s->pm_n != p->pm_n || std::fabs(s->pm_rs - rs) > 1e-12 * rs || s->pm_G != s->bp.G) {
+        if (!s->phi || s->pm_n != p->pm_n || std::fabs(s->pm_rs - rs) > 1e-12 * rs || s->pm_G != s->bp.G ||
+            s->pm_grad != p->pm_grad) {
             set_error("no long-range mesh for these parameters: call tpm_pm_long_range first");
             return TPM_EINVAL;
         }

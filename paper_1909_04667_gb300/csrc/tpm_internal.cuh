@@ -139,6 +139,10 @@ struct System {
     // pm_corner + i pm_side / pm_n
     AllocSet pm_mem;
     float *phi = nullptr;
+    // spectral gradient (periodic, TPM_GRAD_IK): x, y, z force meshes of
+    // pm_mesh^3 points each, one after the other; null for the 4-point difference
+    float *fmesh = nullptr;
+    int pm_grad = TPM_GRAD_FD4;
     int pm_n = 0;
     int pm_mesh = 0;
     double pm_corner[3] = {0, 0, 0};

@@ -43,7 +43,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_version_and_clean_failure_without_device(lib):
     import paper_1909_04667_gb300 as tpm
 
-    assert tpm.version() == 1
+    assert tpm.version() == 2
     try:
         import torch
 

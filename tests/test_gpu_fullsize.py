@@ -64,7 +64,8 @@ def test_hernquist_full_size(oracle_mod, tpm):
     assert gpu_p99 <= 5e-3 and gpu_p99 <= 1.05 * floor_p99 + 1e-5
 
 
-def test_zeldovich_full_size(oracle_mod, tpm):
+@pytest.mark.parametrize("grad", ["fd4", "ik"])
+def test_zeldovich_full_size(oracle_mod, tpm, grad):
     import torch
 
     dev = torch.device("cuda", 0)
@@ -73,7 +74,8 @@ def test_zeldovich_full_size(oracle_mod, tpm):
     n = len(pos)
     h = bench.zeldovich_h()
     shift = bench.root_shift(0, 3)
-    common = dict(treepm=True, pm_n=cfg["pm_n"], asmth=cfg["asmth"], rcut=cfg["rcut"])
+    common = dict(treepm=True, pm_n=cfg["pm_n"], asmth=cfg["asmth"], rcut=cfg["rcut"],
+                  pm_grad=tpm.GRAD_IK if grad == "ik" else tpm.GRAD_FD4)
     fp_bh = tpm.ForceParams(crit=tpm.CRIT_BH, theta=cfg["theta"], **common)
     fp_rel = tpm.ForceParams(crit=tpm.CRIT_RELATIVE, alpha=cfg["alpha"], **common)
     ctx = tpm.Context(0)
@@ -92,7 +94,7 @@ def test_zeldovich_full_size(oracle_mod, tpm):
     rs = cfg["asmth"] / cfg["pm_n"]
     tree = oracle_mod.Tree(pos, mass, bucket=cfg["bucket"], periodic=True, box=1.0, shift=shift)
     phi = oracle_mod.pm_potential(xtree, mass, 1.0, cfg["pm_n"], rs)
-    a_l, _ = oracle_mod.pm_interpolate(phi, xtree[tg], 1.0)
+    a_l, _ = oracle_mod.pm_interpolate(phi, xtree[tg], 1.0, grad=grad)
     o_bh, _, _ = tree.walk(tg, cfg["G"], h, theta=cfg["theta"], treepm=True, rs=rs, rcut=cfg["rcut"] * rs)
     aold_o = np.linalg.norm(o_bh + a_l, axis=1).astype(np.float32)
     o_s, _, on_rel = tree.walk(tg, cfg["G"], h, crit="rel", alpha=cfg["alpha"], a_old=aold_o, treepm=True, rs=rs,
@@ -105,8 +107,8 @@ def test_zeldovich_full_size(oracle_mod, tpm):
     ae, _ = oracle_mod.ewald(pos, mass, tg, cfg["G"], 1.0)
     gpu = rel(a_rel[tg], ae)
     floor = rel(o_rel, ae)
-    print("periodic TreePM vs Ewald: GPU p50 %.3g p99 %.3g; oracle p50 %.3g p99 %.3g" % (
-        np.median(gpu), np.percentile(gpu, 99), np.median(floor), np.percentile(floor, 99)))
+    print("periodic TreePM (%s) vs Ewald: GPU p50 %.3g p99 %.3g; oracle p50 %.3g p99 %.3g" % (
+        grad, np.median(gpu), np.percentile(gpu, 99), np.median(floor), np.percentile(floor, 99)))
     assert np.percentile(gpu, 99) <= 1.05 * np.percentile(floor, 99) + 1e-4
 
 

@@ -428,13 +428,16 @@ def test_budget_admission_has_no_side_effects(tpm):
     small.close()
 
 
-def test_periodic_treepm_matches_oracle(oracle_mod, tpm, ctx, torch_dev):
+@pytest.mark.parametrize("grad", ["fd4", "ik"])
+def test_periodic_treepm_matches_oracle(oracle_mod, tpm, ctx, torch_dev, grad):
+    """The 4-point difference and the spectral gradient of the mesh force."""
     ng_part, ng = 32, 64
     pos, mass = W.zeldovich(ng_part, 1003)
     n = len(pos)
     shift = tuple(W.root_shift(3))
     h = (1.0 / ng_part) / 40
-    fp = tpm.ForceParams(crit=tpm.CRIT_BH, theta=0.5, treepm=True, pm_n=ng, asmth=1.25, rcut=4.5)
+    fp = tpm.ForceParams(crit=tpm.CRIT_BH, theta=0.5, treepm=True, pm_n=ng, asmth=1.25, rcut=4.5,
+                         pm_grad=tpm.GRAD_IK if grad == "ik" else tpm.GRAD_FD4)
     s = ctx.build_tree(to_dev(pos, torch_dev), to_dev(mass, torch_dev),
                        tpm.BuildParams(G=1.0, h=h, periodic=True, box=1.0, shift=shift, leaf_bucket=8))
     s.pm_long_range(fp)
@@ -450,8 +453,33 @@ def test_periodic_treepm_matches_oracle(oracle_mod, tpm, ctx, torch_dev):
     # short-range walk + long-range mesh, element by element
     tree = oracle_mod.Tree(pos, mass, bucket=8, periodic=True, box=1.0, shift=shift)
     a_s, p_s, n_o = tree.walk(tg, 1.0, h, theta=0.5, treepm=True, rs=rs, rcut=4.5 * rs)
-    a_l, p_l = oracle_mod.pm_interpolate(phi_o, xtree[tg], 1.0)
+    a_l, p_l = oracle_mod.pm_interpolate(phi_o, xtree[tg], 1.0, grad=grad)
     compare_forces(acc.cpu().numpy().astype(np.float64), a_s + a_l, nint.cpu().numpy(), n_o, p99=1e-4, mx=1e-3)
+    pot = pot.cpu().numpy().astype(np.float64)
+    po = p_s + p_l
+    assert np.abs((pot - pot.mean()) - (po - po.mean())).max() < 1e-4 * np.abs(po).max()
+
+
+def test_spectral_gradient_needs_its_mesh(tpm, ctx, torch_dev):
+    """A force call whose gradient differs from the solved mesh's is refused,
+    and an open system takes only the 4-point difference."""
+    pos, mass = W.zeldovich(16, 1003)
+    s = ctx.build_tree(to_dev(pos, torch_dev), to_dev(mass, torch_dev),
+                       tpm.BuildParams(G=1.0, h=1e-3, periodic=True, box=1.0, leaf_bucket=8))
+    fp = tpm.ForceParams(theta=0.5, treepm=True, pm_n=32, asmth=1.25, rcut=4.5)
+    s.pm_long_range(fp)
+    with pytest.raises(tpm.TreePMError, match="TPM_EINVAL"):
+        s.compute_forces(fp=tpm.ForceParams(theta=0.5, treepm=True, pm_n=32, asmth=1.25, rcut=4.5,
+                                            pm_grad=tpm.GRAD_IK))
+    with pytest.raises(tpm.TreePMError, match="TPM_EINVAL"):
+        s.pm_long_range(tpm.ForceParams(theta=0.5, treepm=True, pm_n=32, asmth=1.25, rcut=4.5, pm_grad=7))
+    s.release()
+    p2, m2 = W.plummer(2000, 3)
+    s2 = ctx.build_tree(p2, m2, tpm.BuildParams())
+    with pytest.raises(tpm.TreePMError, match="periodic"):
+        s2.pm_long_range(tpm.ForceParams(theta=0.5, treepm=True, pm_n=32, asmth=1.25, rcut=4.5,
+                                         pm_grad=tpm.GRAD_IK))
+    s2.release()
 
 
 LANE_SCRIPT = r"""
