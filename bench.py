@@ -62,9 +62,9 @@ def walk_capture():
 # ------------------------------------------------------------------ configs
 HERNQUIST = dict(n=1 << 20, seed=W.CONFIG_SEEDS[2], h=0.005, G=1.0, bucket=8, theta=0.5, alpha=0.0025)
 PLUMMER = dict(n=8192, h=0.01, G=1.0, bucket=8, theta=0.7)
-SERVING = dict(seed=W.CONFIG_SEEDS[5], budget_gb=60, n_requests=2000, warmup_requests=4000, rate=200.0,
+SERVING = dict(seed=W.CONFIG_SEEDS[5], budget_gb=60, n_requests=10000, warmup_requests=4000, rate=200.0,
                load_factors=(1, 8), nmin=1 << 12, nmax=1 << 20, overcommit=1.5, bytes_per_particle=118,
-               round_ids=1 << 21)
+               round_ids=1 << 21, accuracy_every=1000, accuracy_targets=1024)
 TIMEBINS = dict(nbins=8, seed=W.CONFIG_SEEDS[4], req_lo=64, req_hi=65536)
 HIERARCHY = dict(nbins=8, dt_tick=0.005, c_grav=0.025)
 ISOLATED = dict(pm_n=64, asmth=2.5, rcut=4.5)
@@ -575,10 +575,23 @@ def run_serving(tpm, torch, dev):
             r.arrival /= factor
         return out
 
+    # accuracy: every accuracy_every-th timed request keeps its first
+    # accuracy_targets results in every arm (the exact sums are taken by the
+    # cpu_baseline leg)
+    every, ntg = cfg["accuracy_every"], cfg["accuracy_targets"]
+    sampled = lambda r: r.rid >= nw and (r.rid - nw) % every == 0
+    samples = {}
+
+    def keep(arm, out):
+        for r in out:
+            if sampled(r) and r.acc is not None:
+                samples.setdefault(r.rid, {"sid": r.sid, "ids": r.ids[:ntg].copy(), "acc": {}})
+                samples[r.rid]["acc"][arm] = r.acc[:ntg].copy()
+
     res = {}
     ctx = tpm.Context(dev.index, budget_bytes=budget)
     srv = ForceServer(ctx, source, max_round_ids=cfg["round_ids"], max_round_requests=512, policy="adaptive",
-                      keep_results=False)
+                      keep_results=sampled)
     srv.serve(make(True), realtime=False)
     for f in cfg["load_factors"]:
         b0, e0 = srv.builds, srv.evictions
@@ -586,22 +599,59 @@ def run_serving(tpm, torch, dev):
         out = srv.serve(paced(f), realtime=True)
         key = "continuous_batching" if f == 1 else "continuous_batching_x%d" % f
         res[key] = dict(stats(out, time.perf_counter() - t0), builds=srv.builds - b0, evictions=srv.evictions - e0)
+        if f == 1:
+            keep("continuous_batching", out)
     srv.close()
-    resident = collections.OrderedDict()
-    serve_per_request(ctx, source, make(True), policy="adaptive", realtime=False, keep_results=False,
-                      resident=resident)
-    for f in cfg["load_factors"]:
-        t0 = time.perf_counter()
-        out = serve_per_request(ctx, source, paced(f), policy="adaptive", realtime=True, keep_results=False,
-                                resident=resident)
-        res["per_request" if f == 1 else "per_request_x%d" % f] = stats(out, time.perf_counter() - t0)
-    for system, _, _ in resident.values():
-        system.release()
+    for plain in (False, True):
+        resident = collections.OrderedDict()
+        serve_per_request(ctx, source, make(True), policy="adaptive", realtime=False, keep_results=False,
+                          resident=resident, plain_fp32=plain)
+        arm = "per_request_plain_fp32" if plain else "per_request"
+        for f in cfg["load_factors"]:
+            t0 = time.perf_counter()
+            out = serve_per_request(ctx, source, paced(f), policy="adaptive", realtime=True, keep_results=sampled,
+                                    resident=resident, plain_fp32=plain)
+            res[arm if f == 1 else arm + "_x%d" % f] = stats(out, time.perf_counter() - t0)
+            if f == 1:
+                keep(arm, out)
+        for system, _, _ in resident.values():
+            system.release()
+    # the sampled systems' particles on the host, for the exact sums
+    for rid, smp in samples.items():
+        pos, mass, bp = source(smp["sid"])
+        smp.update(pos=pos.cpu().numpy(), mass=mass.cpu().numpy(), h=bp.h)
     ctx.close()
     res.update(workload="serving_%d_systems_N2^12-2^20_poisson%dHz_%d_requests_after_%d_budget%dGB" % (
         len(cat), int(cfg["rate"]), cfg["n_requests"], nw, cfg["budget_gb"]), hbm_budget_bytes=budget,
-        catalogue_bytes=footprint)
+        catalogue_bytes=footprint,
+        arms={"continuous_batching": "server: mixed precision, up to two batched rounds in flight",
+              "per_request": "one build (if needed), one compute_forces call and one synchronisation per "
+                             "request, mixed precision",
+              "per_request_plain_fp32": "the same with the plain FP32 form (absolute FP32 coordinates)"},
+        _samples=samples)
     return res
+
+
+def serving_accuracy(samples) -> dict:
+    """Per arm: the relative force error of the sampled served requests
+    against the FP64 direct sum on their first targets (cpu_baseline leg)."""
+    import oracle
+
+    errs = {}
+    for rid, smp in sorted(samples.items()):
+        ex, _ = oracle.direct(smp["pos"], smp["mass"], smp["ids"].astype(np.uint32), 1.0, smp["h"])
+        for arm, acc in smp["acc"].items():
+            e = np.linalg.norm(acc.astype(np.float64) - ex, axis=1) / np.linalg.norm(ex, axis=1)
+            errs.setdefault(arm, []).append(e)
+    out = {}
+    for arm, es in errs.items():
+        e = np.concatenate(es)
+        out[arm] = {"p50": float(np.percentile(e, 50)), "p99": float(np.percentile(e, 99)), "max": float(e.max()),
+                    "requests": len(es), "targets": int(len(e)),
+                    "p99_within_5e-3": bool(np.percentile(e, 99) <= 5e-3)}
+    out["reference"] = "FP64 softened direct sum (oracle) on the first %d ids of every %dth timed request" % (
+        SERVING["accuracy_targets"], SERVING["accuracy_every"])
+    return out
 
 
 def run_periodic(ctx, tpm, torch, dev, stream, flush, steps, grad="fd4"):
@@ -975,12 +1025,15 @@ def main():
     out = run_ours(args, rank, world)
     if rank == 0:
         floor_ctx = out.pop("_floor_ctx", None)
+        samples = out["serving"].pop("_samples", None) if out.get("serving") else None
         if not args.no_cpu_baseline:
             import oracle
 
             oracle.build()
             if floor_ctx is not None and isinstance(out.get("accuracy"), dict) and "p99" in out["accuracy"]:
                 out["accuracy"]["oracle_walk_floor"] = oracle_floor(floor_ctx)
+            if samples:
+                out["serving"]["accuracy"] = serving_accuracy(samples)
             r = run_oracle_sample(65536)
             r1 = run_oracle_sample(4096, nthreads=1)
             out["cpu_baseline"] = {"value": r["value"], "unit": "forces/s", "cores": cores(), "kind": "oracle",

@@ -95,6 +95,10 @@ typedef struct {
                            TPM_GRAD_FD4 (0) the 4-point finite difference of the potential mesh,
                            TPM_GRAD_IK (1) the spectral derivative -i k Phi_k (three more inverse
                            transforms, three force meshes kept with the system) */
+    int32_t plain_fp32; /* 0: mixed precision (offsets from each walk group's frame taken in FP64, pair math
+                           in FP32); 1 (open boundaries; a comparison arm, not a recommendation): the plain
+                           FP32 form, every pair vector a difference of absolute FP32 coordinates, as a
+                           code that holds its positions in FP32 computes it */
 } tpm_force_params;
 
 #define TPM_GRAD_FD4 0

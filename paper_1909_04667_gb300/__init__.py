@@ -48,7 +48,7 @@ class _BuildParams(C.Structure):
 class _ForceParams(C.Structure):
     _fields_ = [("crit", C.c_int32), ("theta", C.c_double), ("alpha", C.c_double), ("box_guard", C.c_int32),
                 ("treepm", C.c_int32), ("pm_n", C.c_int32), ("asmth", C.c_double), ("rcut", C.c_double),
-                ("pm_grad", C.c_int32)]
+                ("pm_grad", C.c_int32), ("plain_fp32", C.c_int32)]
 
 
 class _StepParams(C.Structure):
@@ -165,10 +165,11 @@ class ForceParams:
     asmth: float = 1.25
     rcut: float = 4.5
     pm_grad: int = 0  # GRAD_FD4 or GRAD_IK (periodic systems)
+    plain_fp32: bool = False  # the plain FP32 comparison arm (open boundaries)
 
     def _c(self):
         return _ForceParams(int(self.crit), self.theta, self.alpha, int(self.box_guard), int(self.treepm),
-                            int(self.pm_n), self.asmth, self.rcut, int(self.pm_grad))
+                            int(self.pm_n), self.asmth, self.rcut, int(self.pm_grad), int(self.plain_fp32))
 
 
 @dataclass

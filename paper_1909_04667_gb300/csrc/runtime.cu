@@ -156,6 +156,14 @@ int check_force_params(const System *s, const tpm_force_params *p) {
         set_error("alpha must be finite and >= 0");
         return TPM_EINVAL;
     }
+    if (p->plain_fp32 != 0 && p->plain_fp32 != 1) {
+        set_error("plain_fp32 must be 0 or 1");
+        return TPM_EINVAL;
+    }
+    if (p->plain_fp32 && s && s->bp.periodic) {
+        set_error("the plain FP32 form is available for open boundaries");
+        return TPM_EINVAL;
+    }
     if (p->treepm) {
         int n = p->pm_n;
         const int nmax = (s && !s->bp.periodic) ? 512 : 1024;  // open boundaries: a (2 n)^3 padded mesh

@@ -41,6 +41,7 @@ struct WalkConsts {
     float box, boxinv, bigL;
     float G;
     int box_guard;
+    int plain;  // 1: the plain FP32 form (absolute FP32 coordinates)
     // Ewald correction (periodic tree without the mesh): unit-box table of
     // (ent + 1)^3 float4, index scale 2 ent / box, force and potential scales
     // 1 / box^2 and 1 / box, and the own-lattice potential at d = 0
@@ -269,7 +270,7 @@ __global__ void __launch_bounds__(kWalkThreads)
     const int64_t g0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane);
     if (g0 >= n_act)
         return;  // the whole warp leaves together
-    if (!PERIODIC) {  // spread-out chunks are walked in runs by the group walk
+    if (!PERIODIC && !k.plain) {  // spread-out chunks are walked in runs by the group walk
         const int gcount = (int)min((int64_t)32, n_act - g0);
         const unsigned cut = chunk_cuts(key, sidx, g0, gcount);
         if (cut) {
@@ -291,9 +292,10 @@ __global__ void __launch_bounds__(kWalkThreads)
     const int glevel = kx ? min((__clzll(kx) - 1) / 3, kMaxLevel) : kMaxLevel;
     const uint64_t gpre = kf >> (3 * (kMaxLevel - glevel));
     const double ghalf = ldexp(L0, -(glevel + 1));
-    const double gcx_d = (double)(2 * (uint64_t)compact3w(gpre) + 1) * ghalf;
-    const double gcy_d = (double)(2 * (uint64_t)compact3w(gpre >> 1) + 1) * ghalf;
-    const double gcz_d = (double)(2 * (uint64_t)compact3w(gpre >> 2) + 1) * ghalf;
+    const bool abs_frame = !PERIODIC && k.plain;  // the plain FP32 form: absolute FP32 coordinates
+    const double gcx_d = abs_frame ? -x0 : (double)(2 * (uint64_t)compact3w(gpre) + 1) * ghalf;
+    const double gcy_d = abs_frame ? -y0 : (double)(2 * (uint64_t)compact3w(gpre >> 1) + 1) * ghalf;
+    const double gcz_d = abs_frame ? -z0 : (double)(2 * (uint64_t)compact3w(gpre >> 2) + 1) * ghalf;
     const float gcx = (float)gcx_d, gcy = (float)gcy_d, gcz = (float)gcz_d;
     const uint32_t j = perm[s];
     const float xox = (float)(pos[3 * j] - (x0 + gcx_d));
@@ -1003,6 +1005,11 @@ __device__ __forceinline__ void group_walk(const TreeView &T, const WalkConsts &
     double gcx_d = (double)(2 * (uint64_t)compact3w(gpre) + 1) * ghalf;
     double gcy_d = (double)(2 * (uint64_t)compact3w(gpre >> 1) + 1) * ghalf;
     double gcz_d = (double)(2 * (uint64_t)compact3w(gpre >> 2) + 1) * ghalf;
+    if (!PERIODIC && k.plain) {  // the plain FP32 form: absolute FP32 coordinates
+        gcx_d = -x0;
+        gcy_d = -y0;
+        gcz_d = -z0;
+    }
     const uint32_t j = perm[s];
     const double dxo = pos[3 * j] - (x0 + gcx_d), dyo = pos[3 * j + 1] - (y0 + gcy_d),
                  dzo = pos[3 * j + 2] - (z0 + gcz_d);
@@ -1033,7 +1040,7 @@ __device__ __forceinline__ void group_walk(const TreeView &T, const WalkConsts &
         }
     };
     bounding_box();
-    if (!PERIODIC) {
+    if (!PERIODIC && !k.plain) {
         // Open boundaries: move the frame centre to the middle of the group's
         // bounding box, on the grid of the node centres (2^-22 L0, so that
         // node-to-frame offsets stay exact in FP32), and take the offsets
@@ -1343,7 +1350,8 @@ __device__ __forceinline__ void walk_runs_of_chunk(const TreeView &T, const Walk
                                                    int64_t g0, int gcount, const float *__restrict__ a_old,
                                                    float *__restrict__ acc, float *__restrict__ pot,
                                                    uint32_t *__restrict__ nint, int accumulate, int *__restrict__ err) {
-    unsigned cut = PERIODIC ? 0u : chunk_cuts(T.key, sidx, g0, gcount);  // a periodic box bounds every frame
+    // a periodic box bounds every frame; the plain FP32 form has one frame
+    unsigned cut = (PERIODIC || k.plain) ? 0u : chunk_cuts(T.key, sidx, g0, gcount);
     int start = 0;
     for (;;) {
         const int end = cut ? __ffs(cut) : gcount;
@@ -1503,6 +1511,7 @@ WalkConsts make_consts(const System *s, const tpm_force_params *p) {
     k.alpha_over_G = (float)(p->alpha / s->bp.G);
     k.G = (float)s->bp.G;
     k.box_guard = p->box_guard ? 1 : 0;
+    k.plain = p->plain_fp32 ? 1 : 0;
     k.box = (float)s->bp.box;
     k.boxinv = (float)(1.0 / s->bp.box);
     k.bigL = (float)(0.25 * s->bp.box);

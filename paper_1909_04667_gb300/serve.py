@@ -2,11 +2,12 @@
 
 A request asks for the forces on a subset of one system's particles.  The
 server keeps the trees of recently used systems resident on the GPU under the
-context's HBM budget and serves requests in rounds: all requests that have
-arrived while the previous round was on the GPU are admitted (as long as the
-plan's slots last and their trees fit in memory), their missing trees are
-built on a second stream -- overlapping the walk still in flight -- and the
-whole round runs as one batched walk launch (``tpm_compute_forces_batch``).
+context's HBM budget and serves requests in rounds: requests that arrive while
+rounds are on the GPU are admitted as round slots, plan capacity and memory
+free up (up to two rounds in flight, on their own streams, so that a request
+need not wait for a long round to finish), their missing trees are built on a
+separate stream -- overlapping the walks in flight -- and each round runs as
+one batched walk launch (``tpm_compute_forces_batch``).
 When memory runs short, resident systems that no request in flight needs are
 evicted, least recently used first.
 
@@ -56,6 +57,7 @@ class _Resident:
     aold_valid: object    # numpy bool (n,), on the host: which particles have an |a|
     inflight: int = 0
     n_valid: int = 0      # particles with an |a| (once all have one, no per-id checks)
+    built: object = None  # event recorded after the build on the build stream
 
     def all_valid(self, ids) -> bool:
         return self.n_valid == len(self.aold_valid) or bool(self.aold_valid[ids].all())
@@ -64,6 +66,9 @@ class _Resident:
         if self.n_valid < len(self.aold_valid):
             self.aold_valid[ids] = True
             self.n_valid = int(np.count_nonzero(self.aold_valid))
+
+    def ready(self) -> bool:
+        return self.built is None or self.built.query()
 
 
 @dataclass
@@ -76,57 +81,87 @@ class _Round:
     event: object          # results copied to the host
     done: object = None    # and the |a| bookkeeping after them
     sids: list = field(default_factory=list)
+    slot: object = None
+
+
+class _Slot:
+    """What one round in flight needs: a stream, a plan (batched calls on one
+    plan must not overlap), device buffers and pinned staging."""
+
+    def __init__(self, torch, ctx, dev, max_ids, max_req, group_size, priority=0):
+        self.stream = torch.cuda.Stream(dev, priority=priority)
+        self.plan = ctx.create_plan(max_ids, max_req)
+        if group_size:
+            self.plan.group_size = group_size
+        m = max_ids
+        self.ids_h = torch.empty(m, dtype=torch.int32).pin_memory()
+        self.acc_h = torch.empty((m, 3), dtype=torch.float32).pin_memory()
+        self.pot_h = torch.empty(m, dtype=torch.float32).pin_memory()
+        self.nint_h = torch.empty(m, dtype=torch.int32).pin_memory()
+        with torch.cuda.stream(self.stream):
+            self.ids_d = torch.empty(m, dtype=torch.int32, device=dev)
+            self.acc_d = torch.empty((m, 3), dtype=torch.float32, device=dev)
+            self.pot_d = torch.empty(m, dtype=torch.float32, device=dev)
+            self.nint_d = torch.empty(m, dtype=torch.int32, device=dev)
+        self.busy = False
 
 
 class ForceServer:
     """Serves ``ServeRequest``s for systems described by ``source(sid)``, which
-    returns ``(pos float64 (n,3), mass float32 (n,), BuildParams)`` as host
-    arrays (pinned memory keeps the uploads asynchronous)."""
+    returns ``(pos float64 (n,3), mass float32 (n,), BuildParams)`` (host
+    arrays in pinned memory keep the uploads asynchronous; device tensors are
+    taken as they are).
+
+    Up to ``slots`` rounds are in flight at once, each on its own stream with
+    its own plan and buffers, so that requests arriving while a long round
+    walks start at once and share the GPU with it; a system is in at most one
+    round in flight, with at most one request (its |a| bookkeeping is ordered
+    on that round's stream, and a later request on it can use the relative
+    criterion with this round's |a|).
+    A round takes the waiting requests whose trees are ready first (in arrival
+    order); requests whose trees are still building wait for a later round
+    rather than hold ready ones back.  A tree that a queued request needs is
+    not evicted before that request has been served (trees built ahead for
+    waiting requests would otherwise be evicted by the next build ahead).
+    ``keep_results`` is a bool or a
+    predicate on the request: results of the others are timed back to the
+    host and dropped."""
 
     def __init__(self, ctx: Context, source, max_round_ids: int = 1 << 21, max_round_requests: int = 512,
                  theta: float = 0.5, alpha: float = 0.0025, policy: str = "adaptive", group_size: int = None,
-                 keep_results: bool = True):
+                 keep_results=True, slots: int = 2):
         import torch
 
         self.torch = torch
         self.ctx = ctx
         self.source = source
-        self.plan = ctx.create_plan(max_round_ids, max_round_requests)
-        if group_size:
-            self.plan.group_size = group_size
         self.max_ids, self.max_req = int(max_round_ids), int(max_round_requests)
         self.theta, self.alpha, self.policy = theta, alpha, policy
         self.dev = torch.device("cuda", ctx.device)
-        self.walk_stream = torch.cuda.Stream(self.dev)
         self.build_stream = torch.cuda.Stream(self.dev)
+        self.slots = [_Slot(torch, ctx, self.dev, self.max_ids, self.max_req, group_size) for _ in range(slots)]
+        self.plan = self.slots[0].plan
         self.resident: "collections.OrderedDict[int, _Resident]" = collections.OrderedDict()
         self.builds = 0
         self.evictions = 0
-        self.keep_results = keep_results  # False: time the results' return, then drop them
-        # pinned staging, reused by every round (one round is in flight at a
-        # time): ids in, results out -- asynchronous copies need pinned memory
-        m = self.max_ids
-        self.ids_h = torch.empty(m, dtype=torch.int32).pin_memory()
-        self.acc_h = torch.empty((m, 3), dtype=torch.float32).pin_memory()
-        self.pot_h = torch.empty(m, dtype=torch.float32).pin_memory()
-        self.nint_h = torch.empty(m, dtype=torch.int32).pin_memory()
-        # and their device counterparts (the walk stream orders the rounds)
-        with torch.cuda.stream(self.walk_stream):
-            self.ids_d = torch.empty(m, dtype=torch.int32, device=self.dev)
-            self.acc_d = torch.empty((m, 3), dtype=torch.float32, device=self.dev)
-            self.pot_d = torch.empty(m, dtype=torch.float32, device=self.dev)
-            self.nint_d = torch.empty(m, dtype=torch.int32, device=self.dev)
+        self.keep_results = keep_results
+        self._reserved = set()  # systems picked for the round being formed: not evictable
+        self._wanted = collections.Counter()  # queued requests per system: not evictable either
 
     def close(self):
         for r in self.resident.values():
             r.system.release()
         self.resident.clear()
-        self.plan.close()
+        for sl in self.slots:
+            sl.plan.close()
+
+    def _keep(self, r) -> bool:
+        return self.keep_results(r) if callable(self.keep_results) else bool(self.keep_results)
 
     # -------------------------------------------------------------- residency
     def _evict_one(self) -> bool:
         for sid, r in self.resident.items():  # least recently used first
-            if r.inflight == 0:
+            if r.inflight == 0 and r.ready() and sid not in self._reserved and not self._wanted[sid]:
                 r.system.release()
                 del self.resident[sid]
                 self.evictions += 1
@@ -134,8 +169,9 @@ class ForceServer:
         return False
 
     def ensure_resident(self, sid: int) -> bool:
-        """Builds the tree of ``sid`` on the build stream if it is not resident;
-        False if the budget cannot hold it while the systems in flight stay."""
+        """Enqueues the build of ``sid`` on the build stream if it is not
+        resident; False if the budget cannot hold it while the systems in
+        flight stay."""
         torch = self.torch
         if sid in self.resident:
             self.resident.move_to_end(sid)
@@ -154,7 +190,9 @@ class ForceServer:
         n = system.n
         with torch.cuda.stream(self.build_stream):
             aold = torch.zeros(n, dtype=torch.float32, device=self.dev)
-        self.resident[sid] = _Resident(system, aold, np.zeros(n, dtype=bool))
+            ev = torch.cuda.Event()
+            ev.record(self.build_stream)
+        self.resident[sid] = _Resident(system, aold, np.zeros(n, dtype=bool), built=ev)
         self.builds += 1
         return True
 
@@ -166,21 +204,27 @@ class ForceServer:
             return ForceParams(crit=CRIT_RELATIVE, alpha=self.alpha)
         return ForceParams(crit=CRIT_BH, theta=self.theta)
 
-    def _launch(self, reqs) -> _Round:
-        """Enqueues one round: the walk and the copies of its results come
-        first (the round is complete when they are), the bookkeeping of |a|
-        for later criteria after them, overlapping the walk."""
+    def _launch(self, reqs, slot: _Slot) -> _Round:
+        """Enqueues one round on ``slot``: the walk and the copies of its
+        results come first (the round is complete when they are), the
+        bookkeeping of |a| for later criteria after them, overlapping the
+        walk."""
         torch = self.torch
-        self.walk_stream.wait_stream(self.build_stream)
-        with torch.cuda.stream(self.walk_stream):
+        st = slot.stream
+        slot.busy = True
+        for r in reqs:  # the round waits for its own systems' builds only
+            b = self.resident[r.sid].built
+            if b is not None:
+                st.wait_event(b)
+        with torch.cuda.stream(st):
             sizes = [len(r.ids) for r in reqs]
             off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
             n = int(off[-1])
-            ids_np = self.ids_h.numpy()
+            ids_np = slot.ids_h.numpy()
             for k, r in enumerate(reqs):
                 ids_np[off[k]:off[k + 1]] = r.ids
-            ids_d = self.ids_d[:n]
-            ids_d.copy_(self.ids_h[:n], non_blocking=True)
+            ids_d = slot.ids_d[:n]
+            ids_d.copy_(slot.ids_h[:n], non_blocking=True)
             systems, params, aolds, parts = [], [], [], []
             for k, r in enumerate(reqs):
                 res = self.resident[r.sid]
@@ -193,37 +237,40 @@ class ForceServer:
                 parts.append(part)
                 aolds.append(torch.index_select(res.aold, 0, part))
             a_old = aolds[0] if len(aolds) == 1 else torch.cat(aolds)
-            acc, pot, nint = self.acc_d[:n], self.pot_d[:n], self.nint_d[:n]
+            acc, pot, nint = slot.acc_d[:n], slot.pot_d[:n], slot.nint_d[:n]
             walked = False
-            if len(reqs) == 1 and self.plan.group_size == 32 and self.plan.stack_depth == 192:
+            plan = slot.plan
+            if len(reqs) == 1 and plan.group_size == 32 and plan.stack_depth == 192:
                 # a round of one request (light load): the plain call runs the
                 # same walk without the batch's request sort and group table;
                 # its scratch comes from the budget, else the batch path runs
                 try:
                     systems[0].compute_forces(active_ids=ids_d, a_old=a_old, fp=params[0], acc=acc, pot=pot,
-                                              n_int=nint, stream=self.walk_stream.cuda_stream)
+                                              n_int=nint, stream=st.cuda_stream)
                     walked = True
                 except TreePMError as e:
                     if e.status != _EBUDGET:
                         raise
             if not walked:
-                self.plan.compute_forces_batch(systems, off, params, ids_d, acc, a_old=a_old, pot=pot, n_int=nint,
-                                               stream=self.walk_stream.cuda_stream)
-            self.acc_h[:n].copy_(acc, non_blocking=True)
-            self.pot_h[:n].copy_(pot, non_blocking=True)
-            self.nint_h[:n].copy_(nint, non_blocking=True)
+                plan.compute_forces_batch(systems, off, params, ids_d, acc, a_old=a_old, pot=pot, n_int=nint,
+                                          stream=st.cuda_stream)
+            slot.acc_h[:n].copy_(acc, non_blocking=True)
+            slot.pot_h[:n].copy_(pot, non_blocking=True)
+            slot.nint_h[:n].copy_(nint, non_blocking=True)
             ev = torch.cuda.Event()
-            ev.record(self.walk_stream)
+            ev.record(st)
             # |a| of this evaluation becomes a_old of later ones (stream-ordered
-            # before any later round)
+            # before any later round on this system: a system is in one round
+            # in flight at a time)
             amag = torch.linalg.vector_norm(acc, dim=1)
             for k, r in enumerate(reqs):
                 res = self.resident[r.sid]
                 res.aold.index_copy_(0, parts[k].long(), amag[off[k]:off[k + 1]])
                 res.mark_valid(r.ids)
             done = torch.cuda.Event()
-            done.record(self.walk_stream)
-        return _Round(reqs, self.acc_h[:n], self.pot_h[:n], self.nint_h[:n], off, ev, done, [r.sid for r in reqs])
+            done.record(st)
+        return _Round(reqs, slot.acc_h[:n], slot.pot_h[:n], slot.nint_h[:n], off, ev, done,
+                      [r.sid for r in reqs], slot)
 
     def _complete(self, rnd: _Round, t0: float):
         rnd.event.synchronize()
@@ -232,12 +279,57 @@ class ForceServer:
         acc, pot, nint = rnd.acc.numpy(), rnd.pot.numpy(), rnd.nint.numpy()
         for k, r in enumerate(rnd.reqs):
             lo, hi = rnd.offsets[k], rnd.offsets[k + 1]
-            if self.keep_results:  # copies: the pinned buffers serve the next round
+            if self._keep(r):  # copies: the pinned buffers serve the next round
                 r.acc, r.pot, r.n_int = acc[lo:hi].copy(), pot[lo:hi].copy(), nint[lo:hi].copy()
             r.t_done = now
             res = self.resident.get(r.sid)
             if res is not None:
                 res.inflight -= 1
+        rnd.slot.busy = False
+
+    def _form_round(self, queue):
+        """Requests for one round, taken out of ``queue``: those whose trees
+        are ready first (arrival order), else -- none being ready -- those
+        whose trees are building (the round then waits for their builds on the
+        GPU).  Requests of a system in flight stay queued."""
+        # a system goes into one round once: a second request for it waits
+        # for the next round, whose criterion can then use this round's |a|
+        busy = {sid for sid, r in self.resident.items() if r.inflight}
+        ready, building = [], []
+        nids_r = nids_b = 0
+        self._reserved = set()
+        can_build = True
+        try:
+            for r in list(queue):
+                if len(ready) >= self.max_req:
+                    break
+                if r.sid in busy:
+                    continue
+                if r.sid not in self.resident:
+                    # no memory: this request waits for rounds in flight, and
+                    # later ones whose trees are resident still go
+                    if not can_build or not self.ensure_resident(r.sid):
+                        can_build = False
+                        continue
+                res = self.resident[r.sid]
+                if res.ready():
+                    if nids_r + len(r.ids) <= self.max_ids:
+                        ready.append(r)
+                        nids_r += len(r.ids)
+                        self._reserved.add(r.sid)
+                        busy.add(r.sid)
+                elif len(building) < self.max_req and nids_b + len(r.ids) <= self.max_ids:
+                    building.append(r)
+                    nids_b += len(r.ids)
+                    self._reserved.add(r.sid)
+                    busy.add(r.sid)
+        finally:
+            self._reserved = set()
+        batch = ready if ready else building
+        for r in batch:
+            queue.remove(r)
+            self._wanted[r.sid] -= 1
+        return batch
 
     def serve(self, requests, realtime: bool = True):
         """Serves ``requests`` (sorted by arrival).  With ``realtime`` a request
@@ -245,41 +337,42 @@ class ForceServer:
         Returns the requests with results and completion times."""
         reqs = sorted(requests, key=lambda r: r.arrival)
         queue = collections.deque()
-        inflight = None
+        inflight = []
         i = 0
         t0 = time.perf_counter()
-        while i < len(reqs) or queue or inflight is not None:
+        while i < len(reqs) or queue or inflight:
             now = time.perf_counter() - t0
             while i < len(reqs) and (not realtime or reqs[i].arrival <= now):
                 queue.append(reqs[i])
+                self._wanted[reqs[i].sid] += 1
                 i += 1
-            if inflight is not None and inflight.event.query():
-                self._complete(inflight, t0)
-                inflight = None
-            if queue and inflight is None:
-                batch, nids = [], 0
-                while queue and len(batch) < self.max_req and nids + len(queue[0].ids) <= self.max_ids:
-                    if not self.ensure_resident(queue[0].sid):
-                        break  # waits for memory held by the round in flight
-                    r = queue.popleft()
-                    batch.append(r)
-                    nids += len(r.ids)
-                if not batch:
-                    if len(queue[0].ids) > self.max_ids:
-                        raise ValueError("request %d larger than the server's round size" % queue[0].rid)
-                    raise MemoryError("the tree of system %d does not fit in the HBM budget" % queue[0].sid)
-                inflight = self._launch(batch)
-            elif queue and inflight is not None:
-                # admit while the GPU walks: build a tree a waiting request
-                # needs -- one per pass, so that the round in flight is seen
-                # to finish between builds
+            for rnd in [x for x in inflight if x.event.query()]:
+                self._complete(rnd, t0)
+                inflight.remove(rnd)
+            free = [sl for sl in self.slots if not sl.busy]
+            launched = False
+            if queue and free:
+                batch = self._form_round(queue)
+                if batch:
+                    inflight.append(self._launch(batch, free[0]))
+                    launched = True
+                elif not inflight:
+                    r = queue[0]
+                    if len(r.ids) > self.max_ids:
+                        raise ValueError("request %d larger than the server's round size" % r.rid)
+                    if r.sid not in self.resident:
+                        raise MemoryError("the tree of system %d does not fit in the HBM budget" % r.sid)
+            if launched:
+                continue
+            if queue:
+                # admit while the GPU walks: start a build a waiting request
+                # needs -- one per pass, so that finished rounds are seen
                 for r in list(queue)[:self.max_req]:
                     if r.sid not in self.resident:
                         self.ensure_resident(r.sid)
                         break
-                if not inflight.event.query():
-                    time.sleep(0)
-            elif inflight is not None:
+                time.sleep(0)
+            elif inflight:
                 time.sleep(0)
             elif i < len(reqs):
                 time.sleep(max(0.0, min(1e-3, reqs[i].arrival - now)))
@@ -287,12 +380,16 @@ class ForceServer:
 
 
 def serve_per_request(ctx: Context, source, requests, theta: float = 0.5, alpha: float = 0.0025,
-                      policy: str = "adaptive", realtime: bool = True, keep_results: bool = True, resident=None):
+                      policy: str = "adaptive", realtime: bool = True, keep_results=True, resident=None,
+                      plain_fp32: bool = False):
     """Baseline: requests in arrival order, each with its own build (if the
     system is not resident), ``tpm_compute_forces`` call and synchronisation;
     LRU eviction under the same budget, for a build or for the scratch memory
     of a force call.  ``resident`` (an OrderedDict) keeps the resident systems
-    across calls; without it they are released at the end."""
+    across calls; without it they are released at the end.  ``plain_fp32``
+    evaluates in the plain FP32 form (absolute FP32 coordinates), the
+    comparison arm of the mixed-precision scheme.  ``keep_results`` is a bool
+    or a predicate on the request."""
     import torch
 
     dev = torch.device("cuda", ctx.device)
@@ -324,9 +421,9 @@ def serve_per_request(ctx: Context, source, requests, theta: float = 0.5, alpha:
         ids_d = torch.from_numpy(r.ids.astype(np.int32)).to(dev)
         part = ids_d.long()
         if policy == "bh" or (policy == "adaptive" and not valid.all_valid(r.ids)):
-            fp = ForceParams(crit=CRIT_BH, theta=theta)
+            fp = ForceParams(crit=CRIT_BH, theta=theta, plain_fp32=plain_fp32)
         else:
-            fp = ForceParams(crit=CRIT_RELATIVE, alpha=alpha)
+            fp = ForceParams(crit=CRIT_RELATIVE, alpha=alpha, plain_fp32=plain_fp32)
         r.criterion = fp.crit
         while True:
             try:
@@ -341,7 +438,7 @@ def serve_per_request(ctx: Context, source, requests, theta: float = 0.5, alpha:
         aold[part] = torch.linalg.vector_norm(acc, dim=1)
         valid.mark_valid(r.ids)
         a_h, p_h, n_h = acc.cpu().numpy(), pot.cpu().numpy(), nint.cpu().numpy()
-        if keep_results:
+        if (keep_results(r) if callable(keep_results) else keep_results):
             r.acc, r.pot, r.n_int = a_h, p_h, n_h
         r.t_done = time.perf_counter() - t0
     if not keep:

@@ -227,6 +227,34 @@ np.savez(sys.argv[1], **out)
 """ % ROOT_DIR
 
 
+def test_plain_fp32_arm_loses_precision_far_from_the_origin(oracle_mod, tpm, ctx, torch_dev):
+    """The plain FP32 comparison arm (every pair vector a difference of
+    absolute FP32 coordinates) against the mixed scheme, both against the
+    oracle walk: at the origin both are at the FP32 rounding floor; 10^3
+    scale lengths away the plain form's coordinates carry ~6e-5 of rounding,
+    while the mixed scheme's offsets from each group's frame do not grow."""
+    pos0, mass = W.plummer(8192, 1001)
+    fp = tpm.ForceParams(crit=tpm.CRIT_BH, theta=0.7)
+    fpp = tpm.ForceParams(crit=tpm.CRIT_BH, theta=0.7, plain_fp32=True)
+    p99 = {}
+    for off in (0.0, 1.0e3):
+        pos = pos0 + off
+        shift = tuple(W.root_shift(4))
+        s = ctx.build_tree(to_dev(pos, torch_dev), to_dev(mass, torch_dev),
+                           tpm.BuildParams(G=1.0, h=0.01, shift=shift, leaf_bucket=8))
+        a_m, _, n_m = s.compute_forces(fp=fp)
+        a_p, _, _ = s.compute_forces(fp=fpp)
+        s.sync_status()
+        a_m, a_p, n_m = a_m.cpu().numpy().astype(np.float64), a_p.cpu().numpy().astype(np.float64), n_m.cpu().numpy()
+        s.release()
+        ref = oracle_mod.Tree(pos, mass, bucket=8, shift=shift)
+        a_o, _, n_o = ref.walk(np.arange(len(pos)), 1.0, 0.01, theta=0.7)
+        compare_forces(a_m, a_o, n_m, n_o)
+        p99[off] = (np.percentile(rel(a_m, a_o), 99), np.percentile(rel(a_p, a_o), 99))
+    assert p99[0.0][1] < 1e-4
+    assert p99[1.0e3][1] > 1e-4 and p99[1.0e3][1] > 20 * p99[1.0e3][0], p99
+
+
 def test_walk_relative_hernquist(oracle_mod, tpm, ctx, torch_dev):
     n = 1 << 16
     pos, mass = W.hernquist(n, 1002)

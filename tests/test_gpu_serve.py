@@ -91,12 +91,13 @@ def test_budget_evictions_keep_results(setup):
     # resident tree holds that tree's build (its scratch nearly doubles it) but
     # not the five smaller trees (together ~0.9 of it) next to the build
     probe = tpm.Context(0)
-    plan = probe.create_plan(1 << 16, 8)
+    plans = [probe.create_plan(1 << 16, 8) for _ in range(2)]  # the server's two round slots
     plan_bytes = probe.memory()[0]
     tree = probe.build_tree(*source(order[-1]))
     tree_bytes = probe.memory()[0] - plan_bytes
     tree.release()
-    plan.close()
+    for plan in plans:
+        plan.close()
     probe.close()
     small = tpm.Context(0, budget_bytes=plan_bytes + int(2.2 * tree_bytes))
     srv = ForceServer(small, source, max_round_ids=1 << 16, max_round_requests=8, policy="bh")
@@ -111,3 +112,25 @@ def test_budget_evictions_keep_results(setup):
         e = rel(r.acc.astype(np.float64), ref[r.rid].acc.astype(np.float64))
         assert np.percentile(e, 99) < 2e-5
     small.close()
+
+
+def test_rounds_in_flight_together_give_the_same_results(setup):
+    """Two round slots (a request arriving while a round walks starts at once
+    on the other stream) against one: the same results, request by request."""
+    tpm, torch, cat, source, reqs = setup
+    from paper_1909_04667_gb300.serve import ForceServer
+
+    ctx = tpm.Context(0)
+    out = {}
+    for slots in (1, 2):
+        srv = ForceServer(ctx, source, max_round_ids=1 << 18, max_round_requests=4, policy="bh", slots=slots)
+        rq = fresh(reqs)
+        for r in rq:
+            r.arrival = 0.0005 * r.rid  # arrivals faster than the walks: rounds overlap
+        out[slots] = {r.rid: r for r in srv.serve(rq, realtime=True)}
+        srv.close()
+    for rid, r in out[2].items():
+        np.testing.assert_array_equal(r.n_int, out[1][rid].n_int)
+        e = rel(r.acc.astype(np.float64), out[1][rid].acc.astype(np.float64))
+        assert e.max() < 1e-5
+    ctx.close()
