@@ -184,6 +184,29 @@ __device__ __forceinline__ void ewald_term(float rx, float ry, float rz, float m
     ph = fmaf(m * k.eps, v[3], ph);
 }
 
+// Compensated (Kahan) addition s += t with the lost low part kept in c.
+__device__ __forceinline__ void kahan_add(float &s, float &c, float t) {
+    const float y = t - c;
+    const float u = s + y;
+    c = (u - s) - y;
+    s = u;
+}
+
+// One interaction of the periodic tree with the Ewald correction: the pair
+// term and its correction are added up first, then into the sums with
+// compensation (c), since a particle of a near-uniform box sums some 10^4
+// such terms to a small total.
+__device__ __forceinline__ void ewald_pair_term(float rx, float ry, float rz, float r2, float m, const WalkConsts &k,
+                                                float &ax, float &ay, float &az, float &ph, float4 &c) {
+    float tx = 0.f, ty = 0.f, tz = 0.f, tp = 0.f;
+    pair_term<false>(rx, ry, rz, r2, m, k, tx, ty, tz, tp);
+    ewald_term(rx, ry, rz, m, k, tx, ty, tz, tp);
+    kahan_add(ax, c.x, tx);
+    kahan_add(ay, c.y, ty);
+    kahan_add(az, c.z, tz);
+    kahan_add(ph, c.w, tp);
+}
+
 // ----------------------------------------------------------------------
 // Walk frames of spread-out chunks.
 //
@@ -308,6 +331,7 @@ __global__ void __launch_bounds__(kWalkThreads)
     const float hi = VARH ? __ldg(&psoft[s]) : 0.0f;  // this particle's spline support
 
     float ax = 0.f, ay = 0.f, az = 0.f, ph = 0.f;
+    float4 ec = make_float4(0.f, 0.f, 0.f, 0.f);  // compensation of the Ewald sums
     uint32_t cnt = 0;
     int skip_until = valid ? 0 : 0x7fffffff;
     int n = 0;
@@ -353,12 +377,12 @@ __global__ void __launch_bounds__(kWalkThreads)
         const bool open = act && !far && (guard || crit);
         if (act && !open) {
             if (!far) {
-                if (VARH)
+                if (EWALD)
+                    ewald_pair_term(rx, ry, rz, r2, O.w, k, ax, ay, az, ph, ec);
+                else if (VARH)
                     pair_term_h<TREEPM>(rx, ry, rz, r2, O.w, fmaxf(hi, hn), k, ax, ay, az, ph);
                 else
                     pair_term<TREEPM>(rx, ry, rz, r2, O.w, k, ax, ay, az, ph);
-                if (EWALD)
-                    ewald_term(rx, ry, rz, O.w, k, ax, ay, az, ph);
                 cnt++;
             }
             skip_until = Lk.x;
@@ -385,12 +409,12 @@ __global__ void __launch_bounds__(kWalkThreads)
                 }
                 const float q2 = fmaf(qx, qx, fmaf(qy, qy, qz * qz));
                 if (!TREEPM || q2 <= k.rcut2) {
-                    if (VARH)
+                    if (EWALD)
+                        ewald_pair_term(qx, qy, qz, q2, P.w, k, ax, ay, az, ph, ec);
+                    else if (VARH)
                         pair_term_h<TREEPM>(qx, qy, qz, q2, P.w, fmaxf(hi, __ldg(&psoft[jj])), k, ax, ay, az, ph);
                     else
                         pair_term<TREEPM>(qx, qy, qz, q2, P.w, k, ax, ay, az, ph);
-                    if (EWALD)
-                        ewald_term(qx, qy, qz, P.w, k, ax, ay, az, ph);
                     cnt++;
                 }
             }
@@ -612,7 +636,8 @@ __device__ __forceinline__ void newton_term(float rx, float ry, float rz, float 
 // node's largest (Sec. 3.2), and such entries add zero mass in the first pass.
 template <bool PERIODIC, bool TREEPM, bool VARH, class SH>
 __device__ __forceinline__ void sweep_full(const SH &sh, int nf, float xox, float xoy, float xoz, float hi,
-                                           const WalkConsts &k, float &ax, float &ay, float &az, float &ph) {
+                                           const WalkConsts &k, float &ax, float &ay, float &az, float &ph,
+                                           float4 &ec) {
     if (TREEPM || PERIODIC) {
         for (int e = 0; e < nf; e++) {
             const float4 A = node_entry(sh, e);
@@ -623,12 +648,12 @@ __device__ __forceinline__ void sweep_full(const SH &sh, int nf, float xox, floa
                 rz = wrap_min_image(rz, k);
             }
             const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-            if (VARH)
+            if (PERIODIC && !TREEPM)
+                ewald_pair_term(rx, ry, rz, r2, A.w, k, ax, ay, az, ph, ec);
+            else if (VARH)
                 pair_term_h<TREEPM>(rx, ry, rz, r2, A.w, fmaxf(hi, sh.nsoft[e]), k, ax, ay, az, ph);
             else
                 pair_term<TREEPM>(rx, ry, rz, r2, A.w, k, ax, ay, az, ph);
-            if (PERIODIC && !TREEPM)
-                ewald_term(rx, ry, rz, A.w, k, ax, ay, az, ph);
         }
         return;
     }
@@ -737,7 +762,7 @@ __device__ __forceinline__ void sweep_full(const SH &sh, int nf, float xox, floa
 template <bool PERIODIC, bool TREEPM, bool VARH, class SH>
 __device__ __forceinline__ void sweep_partial(const SH &sh, int np, unsigned lanebit, float xox, float xoy,
                                               float xoz, float hi, const WalkConsts &k, float &ax, float &ay,
-                                              float &az, float &ph, uint32_t &cnt) {
+                                              float &az, float &ph, uint32_t &cnt, float4 &ec) {
     const int e0 = kNodeCap - np;
     if (TREEPM || PERIODIC) {
         for (int e = e0; e < kNodeCap; e++) {
@@ -751,13 +776,13 @@ __device__ __forceinline__ void sweep_partial(const SH &sh, int np, unsigned lan
             }
             const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
             cnt += mine ? 1u : 0u;
-            if (VARH)
+            if (PERIODIC && !TREEPM)
+                ewald_pair_term(rx, ry, rz, mine ? r2 : 1.0f, mine ? E.w : 0.0f, k, ax, ay, az, ph, ec);
+            else if (VARH)
                 pair_term_h<TREEPM>(rx, ry, rz, mine ? r2 : 1.0f, mine ? E.w : 0.0f, fmaxf(hi, sh.nsoft[e]), k, ax,
                                     ay, az, ph);
             else
                 pair_term<TREEPM>(rx, ry, rz, mine ? r2 : 1.0f, mine ? E.w : 0.0f, k, ax, ay, az, ph);
-            if (PERIODIC && !TREEPM)
-                ewald_term(rx, ry, rz, mine ? E.w : 0.0f, k, ax, ay, az, ph);
         }
         return;
     }
@@ -859,7 +884,7 @@ __device__ __forceinline__ void sweep_leaves(const SH &sh, int nl, unsigned lane
                                              float xox, float xoy, float xoz, float hi,
                                              const float4 *__restrict__ spart, const float *__restrict__ psoft,
                                              const WalkConsts &k, float &ax, float &ay, float &az, float &ph,
-                                             uint32_t &cnt) {
+                                             uint32_t &cnt, float4 &ec) {
     if (!TREEPM && !PERIODIC) {
         for (int e = 0; e < nl; e++) {
             const float4 E = sh.lsrc[e];
@@ -932,12 +957,12 @@ __device__ __forceinline__ void sweep_leaves(const SH &sh, int nl, unsigned lane
             }
             const float q2 = fmaf(qx, qx, fmaf(qy, qy, qz * qz));
             if (mine && (uint32_t)jj != self && (!TREEPM || q2 <= k.rcut2)) {
-                if (VARH)
+                if (PERIODIC && !TREEPM)
+                    ewald_pair_term(qx, qy, qz, q2, P.w, k, ax, ay, az, ph, ec);
+                else if (VARH)
                     pair_term_h<TREEPM>(qx, qy, qz, q2, P.w, fmaxf(hi, __ldg(&psoft[jj])), k, ax, ay, az, ph);
                 else
                     pair_term<TREEPM>(qx, qy, qz, q2, P.w, k, ax, ay, az, ph);
-                if (PERIODIC && !TREEPM)
-                    ewald_term(qx, qy, qz, P.w, k, ax, ay, az, ph);
                 cnt++;
             }
         }
@@ -1075,6 +1100,7 @@ __device__ __forceinline__ void group_walk(const TreeView &T, const WalkConsts &
     const unsigned valid_mask = __ballot_sync(FULL, valid);
 
     float ax = 0.f, ay = 0.f, az = 0.f, ph = 0.f;
+    float4 ec = make_float4(0.f, 0.f, 0.f, 0.f);  // compensation of the Ewald sums
     uint32_t cnt = 0;
     put_part_entry(sh, lane, make_float4(xox, xoy, xoz, thr));  // read by the transposed decisions
     if (lane == 0) {
@@ -1305,14 +1331,14 @@ __device__ __forceinline__ void group_walk(const TreeView &T, const WalkConsts &
         __syncwarp();
         }
         if (done || nf + np >= kNodeFlush) {
-            sweep_full<PERIODIC, TREEPM, VARH>(sh, nf, xox, xoy, xoz, hi, k, ax, ay, az, ph);
-            sweep_partial<PERIODIC, TREEPM, VARH>(sh, np, lanebit, xox, xoy, xoz, hi, k, ax, ay, az, ph, cnt);
+            sweep_full<PERIODIC, TREEPM, VARH>(sh, nf, xox, xoy, xoz, hi, k, ax, ay, az, ph, ec);
+            sweep_partial<PERIODIC, TREEPM, VARH>(sh, np, lanebit, xox, xoy, xoz, hi, k, ax, ay, az, ph, cnt, ec);
             cnt += valid ? (uint32_t)nf : 0u;
             nf = np = 0;
         }
         if (done || nl >= kLeafFlush) {
             sweep_leaves<PERIODIC, TREEPM, VARH>(sh, nl, lanebit, s, xox, xoy, xoz, hi, spart, T.psoft, k, ax, ay, az,
-                                                 ph, cnt);
+                                                 ph, cnt, ec);
             nl = 0;
         }
         if (done)

@@ -3,10 +3,11 @@ periodic system) against the FP64 oracle walk with the same correction.
 
 Same decisions as the oracle walk; the pair terms and the trilinear table
 interpolation run in FP32 (table values rounded to FP32 from the FP64 Ewald
-sums), so forces agree to p99 1e-4, max 1e-3 where the interaction counts
-agree -- the periodic TreePM tolerance: the linear box's total forces are
-small sums of large cancelling terms.  Potentials are compared up to a
-constant (periodic potentials)."""
+sums).  A linear box's total forces are small sums of thousands of large,
+nearly cancelling terms; each interaction's pair term and correction are
+added first and then into compensated sums, so forces agree at the FP32 tier
+(p99 1e-5, max 5e-5) where the interaction counts agree.  Potentials are
+compared up to a constant (periodic potentials)."""
 import numpy as np
 import pytest
 
@@ -61,7 +62,9 @@ def test_ewald_tree_matches_oracle(oracle_mod, tpm, crit):
     same = nint == n_o
     assert np.mean(~same) <= 0.005
     e = rel(a, a_o)
-    assert np.percentile(e[same], 99) <= 1e-4 and e[same].max() <= 1e-3, (np.percentile(e[same], 99), e.max())
+    print("Ewald tree (%s) vs oracle: p99 %.3g max %.3g, counts differ %d" % (
+        crit, np.percentile(e[same], 99), e[same].max(), (~same).sum()))
+    assert np.percentile(e[same], 99) <= 1e-5 and e[same].max() <= 5e-5, (np.percentile(e[same], 99), e.max())
     dp = p - p_o
     assert np.percentile(np.abs(dp - dp.mean())[same], 99) <= 1e-4 * np.abs(p_o).mean()
 

@@ -184,13 +184,16 @@ def test_zeldovich_ewald_tree_full_size(oracle_mod, tpm):
     ctx.close()
     o_rel, _, on_rel = tree.walk(tg, cfg["G"], h, crit="rel", alpha=cfg["alpha"], a_old=aold_o, ewald=True)
     same = n_rel[tg] == on_rel
-    assert same.mean() >= 0.98
-    # FP32 accumulation of ~3500 terms that nearly cancel (a linear box): the
-    # running sum reaches ~4 pi G rho L/2 ~ 6 while a force is ~0.03, so the
-    # rounding walk is ~6e-8 x 6 x sqrt(3500) / 0.03 ~ 7e-4 of the rms force
+    assert same.mean() >= 0.995
+    # ~10^4 terms that nearly cancel (a linear box): the running sum reaches
+    # ~4 pi G rho L/2 ~ 6 while a force is ~0.03; with compensated sums the
+    # rounding stays at the FP32 tier of the rms force
     scale = np.sqrt(np.mean(np.sum(o_rel * o_rel, axis=1)))
     e = np.linalg.norm(a_rel[tg] - o_rel, axis=1) / scale
-    assert np.percentile(e[same], 99) < 2e-3 and e[same].max() < 1e-2, (np.percentile(e[same], 99), e.max())
+    e_rel = rel(a_rel[tg], o_rel)
+    print("periodic Ewald tree vs oracle walk: same counts %.4f, p99 %.3g of the rms force, p99 %.3g relative" % (
+        same.mean(), np.percentile(e[same], 99), np.percentile(e_rel[same], 99)))
+    assert np.percentile(e[same], 99) < 2e-5 and e[same].max() < 1e-4, (np.percentile(e[same], 99), e.max())
     ae, _ = oracle_mod.ewald(pos, mass, tg, cfg["G"], 1.0)
     gpu, floor = rel(a_rel[tg], ae), rel(o_rel, ae)
     print("periodic Ewald tree vs Ewald: GPU p50 %.3g p99 %.3g; oracle p50 %.3g p99 %.3g" % (
