@@ -35,6 +35,27 @@ def test_active_range_partitions(shard):
         shard.active_range(10, 2, 2)
 
 
+def test_weighted_ranges_balance_work(shard):
+    """Ranges weighted by per-particle cost (interaction counts) cover the set
+    in order and hold equal work to within one item's weight."""
+    rng = np.random.default_rng(1)
+    for n, world in ((1000, 2), (1001, 3), (5000, 8), (3, 4), (1, 2)):
+        w = rng.lognormal(0.0, 1.5, n) * 700  # a halo's centre costs far more than its outskirts
+        w[: n // 10] *= 5
+        ranges = [shard.active_range(n, r, world, w) for r in range(world)]
+        assert ranges[0][0] == 0 and ranges[-1][1] == n
+        for (a, b), (c, d) in zip(ranges, ranges[1:]):
+            assert b == c and a <= b
+        loads = [w[a:b].sum() for a, b in ranges]
+        assert max(loads) <= w.sum() / world + w.max() + 1e-9 * w.sum()
+    # zero weights fall back to equal counts
+    assert [shard.active_range(10, r, 2, np.zeros(10)) for r in range(2)] == [(0, 5), (5, 10)]
+    with pytest.raises(ValueError):
+        shard.active_range(4, 0, 2, [1.0, 2.0])
+    with pytest.raises(ValueError):
+        shard.active_range(2, 0, 2, [1.0, -1.0])
+
+
 def free_port():
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
@@ -60,7 +81,10 @@ def rank_main(rank, world, port, n, n_active, out_dir):
             acc, pot, nint = tree.walk(part, 1.0, 0.01, theta=0.6, nthreads=1)
             return torch.from_numpy(acc), torch.from_numpy(pot), torch.from_numpy(nint.astype(np.int64))
 
-        acc, pot, nint = shard.sharded_compute_forces(compute, ids, rank, world)
+        # ranges balanced by each particle's interaction count from a previous
+        # evaluation (the same on every rank)
+        weights = tree.walk(ids, 1.0, 0.01, theta=0.6, nthreads=1)[2].astype(np.float64) if n_active > 1 else None
+        acc, pot, nint = shard.sharded_compute_forces(compute, ids, rank, world, weights=weights)
         slowest = shard.max_over_ranks(1.5 + rank)
         np.savez(os.path.join(out_dir, "rank%d.npz" % rank), acc=acc.numpy(), pot=pot.numpy(), nint=nint.numpy(),
                  slowest=slowest)
