@@ -437,26 +437,43 @@ def run_hierarchy(ctx, tpm, torch, dev, stream):
 
 
 def run_batching(ctx, tpm, torch, dev, stream, pos_d, mass_d, reps=3):
-    """Hierarchical time-step batching on the Hernquist 2^20 set: one tree, the
-    requests of one 128-substep cycle as (a) one compute_forces call each and
-    (b) one autotuned batch captured in a CUDA graph."""
+    """Hierarchical time-step batching on the Hernquist 2^20 set: the requests
+    of one 128-substep cycle on one tree.  The autotuner picks the walk group
+    size G in {8, 16, 32, 64} and the stack depth for trees of leaf bucket B in
+    {1, 4, 8, 16}; at the best B the cycle runs (a) as one compute_forces call
+    per request and (b) as one tuned batch captured in a CUDA graph."""
     cfg = HERNQUIST
     n = pos_d.shape[0]
-    sy = ctx.build_tree(pos_d, mass_d, tpm.BuildParams(G=cfg["G"], h=cfg["h"], shift=root_shift(7, 4),
-                                                       leaf_bucket=cfg["bucket"]))
-    a, _, _ = sy.compute_forces(fp=tpm.ForceParams(crit=tpm.CRIT_BH, theta=cfg["theta"]))
-    a_full = torch.linalg.vector_norm(a, dim=1).contiguous()
-    perm = sy.tree_export()["perm"].astype(np.int64)
-    pos = pos_d.cpu().numpy()
-    bins = W.timebins(pos, TIMEBINS["seed"], TIMEBINS["nbins"])
-    ids, off, subs = timebin_requests(perm, bins, TIMEBINS["seed"])
-    n_ids, n_req = len(ids), len(off) - 1
-    ids_d = torch.from_numpy(ids).to(dev)
-    aold = a_full[ids_d.long()].contiguous()
-    acc = torch.empty((n_ids, 3), device=dev)
-    pot = torch.empty(n_ids, device=dev)
-    nint = torch.empty(n_ids, dtype=torch.int32, device=dev)
     fp = tpm.ForceParams(crit=tpm.CRIT_RELATIVE, alpha=cfg["alpha"])
+    bins = W.timebins(pos_d.cpu().numpy(), TIMEBINS["seed"], TIMEBINS["nbins"])
+    sweep, best = {}, None
+    for B in (1, 4, 8, 16):
+        sy = ctx.build_tree(pos_d, mass_d, tpm.BuildParams(G=cfg["G"], h=cfg["h"], shift=root_shift(7, 4),
+                                                           leaf_bucket=B))
+        a, _, _ = sy.compute_forces(fp=tpm.ForceParams(crit=tpm.CRIT_BH, theta=cfg["theta"]))
+        a_full = torch.linalg.vector_norm(a, dim=1).contiguous()
+        perm = sy.tree_export()["perm"].astype(np.int64)
+        ids, off, subs = timebin_requests(perm, bins, TIMEBINS["seed"])
+        n_ids, n_req = len(ids), len(off) - 1
+        ids_d = torch.from_numpy(ids).to(dev)
+        aold = a_full[ids_d.long()].contiguous()
+        acc = torch.empty((n_ids, 3), device=dev)
+        pot = torch.empty(n_ids, device=dev)
+        nint = torch.empty(n_ids, dtype=torch.int32, device=dev)
+        plan = ctx.create_plan(n_ids, n_req)
+        g_best, ms_tune = plan.autotune([sy] * n_req, off, fp, ids_d, acc, a_old=aold, pot=pot, n_int=nint,
+                                        presorted=True, reps=2)
+        sweep[B] = {"group_size": g_best, "stack_depth": plan.stack_depth, "ms_per_cycle": ms_tune}
+        plan.close()
+        if best is None or ms_tune < best[0]:
+            if best is not None:
+                best[1].release()
+            best = (ms_tune, sy, B, ids, off, ids_d, aold, acc, pot, nint, g_best, sweep[B]["stack_depth"])
+        else:
+            sy.release()
+    _, sy, B, ids, off, ids_d, aold, acc, pot, nint, g_best, depth_best = best
+    n_ids, n_req = len(ids), len(off) - 1
+
     # (a) one call per request
     def per_request():
         for r in range(n_req):
@@ -472,12 +489,12 @@ def run_batching(ctx, tpm, torch, dev, stream, pos_d, mass_d, reps=3):
         torch.cuda.synchronize()
         t_req.append((time.perf_counter() - t0) * 1e3)
     ref = acc.cpu().numpy().copy()
-    # (b) one batch per cycle, autotuned, in a CUDA graph
+    # (b) one batch per cycle at the tuned G and depth, in a CUDA graph
     plan = ctx.create_plan(n_ids, n_req)
+    plan.group_size = g_best
+    plan.stack_depth = depth_best
     systems = [sy] * n_req
-    g_best, ms_tune = plan.autotune(systems, off, fp, ids_d, acc, a_old=aold, pot=pot, n_int=nint, presorted=True,
-                                    reps=2)
-    depth_best = plan.stack_depth
+    plan.compute_forces_batch(systems, off, fp, ids_d, acc, a_old=aold, pot=pot, n_int=nint, presorted=True)
     torch.cuda.synchronize()
     graph = torch.cuda.CUDAGraph()
     side = torch.cuda.Stream()
@@ -503,7 +520,8 @@ def run_batching(ctx, tpm, torch, dev, stream, pos_d, mass_d, reps=3):
     sy.release()
     ms_req, ms_b = statistics.median(t_req), statistics.median(t_b)
     return {"workload": "hernquist_n2^20_timebins8_cycle128_requests64-65536", "forces_per_cycle": n_ids,
-            "requests_per_cycle": n_req, "interactions_per_force": inter / n_ids,
+            "requests_per_cycle": n_req, "interactions_per_force": inter / n_ids, "leaf_bucket": B,
+            "autotune": {"B%d" % b: v for b, v in sweep.items()},
             "per_request_launches": {"ms_per_cycle": ms_req, "forces_per_s": n_ids / (ms_req * 1e-3)},
             "batched_graph": {"ms_per_cycle": ms_b, "forces_per_s": n_ids / (ms_b * 1e-3), "group_size": g_best,
                               "stack_depth": depth_best,

@@ -283,7 +283,9 @@ int tpm_plan_create(tpm_ctx *ctx, int64_t max_ids, int64_t max_requests, tpm_pla
 /* Frees a plan (waits for the device). */
 int tpm_plan_destroy(tpm_ctx *ctx, tpm_plan *plan);
 
-/* Walk group size G in [8, 32] (default 32) and its current value. */
+/* Walk group size G in [8, 32] (one particle per lane of a warp) or 64 (two
+ * particles per lane: each node record the warp reads serves 64 particles),
+ * default 32, and its current value. */
 int tpm_plan_set_group_size(tpm_plan *plan, int group_size);
 int tpm_plan_group_size(const tpm_plan *plan);
 
@@ -317,7 +319,7 @@ int tpm_compute_forces_batch(tpm_ctx *ctx, tpm_plan *plan, int64_t n_req, const 
  * batches (TPM_EINVAL: an id out of range; TPM_ECUDA: walk stack overflow). */
 int tpm_plan_sync_status(tpm_ctx *ctx, tpm_plan *plan, void *stream);
 
-/* Times the batch for G in {8, 16, 32} x stack depth in {128, 192, 256}
+/* Times the batch for G in {8, 16, 32, 64} x stack depth in {128, 192, 256}
  * (reps timed runs each, after one warm-up), keeps the fastest pair in the
  * plan and returns its G (read the depth with tpm_plan_stack_depth) with its
  * median time in milliseconds.  Synchronises.  Arguments as

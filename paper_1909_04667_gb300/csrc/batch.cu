@@ -250,8 +250,8 @@ int run_batch(Ctx *c, Plan *pl, int64_t n_req, const tpm_sys *systems, const int
     count_launch();
     TPM_CUDA(cudaMemsetAsync(pl->next, 0, sizeof(unsigned), st));
     TPM_CUDA(cudaGetLastError());
-    return launch_walk_batch(c, pl->stack_depth, pl->reqs_dev, pl->groups, pl->ngroups, pl->next, pl->sidx, pl->slot,
-                             a_old, acc, pot, nint, pl->err, st);
+    return launch_walk_batch(c, g, pl->stack_depth, pl->reqs_dev, pl->groups, pl->ngroups, pl->next, pl->sidx,
+                             pl->slot, a_old, acc, pot, nint, pl->err, st);
 }
 
 }  // namespace
@@ -340,8 +340,8 @@ int tpm_plan_destroy(tpm_ctx *h, tpm_plan *plan) {
 
 int tpm_plan_set_group_size(tpm_plan *plan, int group_size) {
     clear_error();
-    if (!plan || group_size < 8 || group_size > 32) {
-        set_error("group size must lie in [8, 32]");
+    if (!plan || ((group_size < 8 || group_size > 32) && group_size != 64)) {
+        set_error("group size must lie in [8, 32] or be 64");
         return TPM_EINVAL;
     }
     plan->p.group_size = group_size;
@@ -420,11 +420,11 @@ int tpm_plan_autotune(tpm_ctx *h, tpm_plan *plan, int64_t n_req, const tpm_sys *
     cudaEvent_t e0, e1;
     TPM_CUDA(cudaEventCreate(&e0));
     TPM_CUDA(cudaEventCreate(&e1));
-    const int groups[3] = {8, 16, 32}, depths[3] = {128, 192, 256};
+    const int groups[4] = {8, 16, 32, 64}, depths[3] = {128, 192, 256};
     int best = plan->p.group_size, best_depth = plan->p.stack_depth;
     float best_t = 1e30f;
     int rc = TPM_OK;
-    for (int cand = 0; cand < 9 && rc == TPM_OK; cand++) {
+    for (int cand = 0; cand < 12 && rc == TPM_OK; cand++) {
         const int g = groups[cand / 3];
         plan->p.group_size = g;
         plan->p.stack_depth = depths[cand % 3];

@@ -215,13 +215,14 @@ int walk_device(Ctx *c, const System *s, const tpm_force_params *p, const WalkRe
 
 // Batched walk (open boundaries): request descriptors are opaque records of
 // batch_req_bytes() bytes filled by fill_batch_req; groups are (start, count,
-// request, 0) over the sorted active list; stack_depth is the candidate-stack
-// capacity of the walk (128, 192 or 256).
+// request, 0) over the sorted active list; group_size 64 takes the walk with
+// two particles per lane (else groups of at most 32, one per lane);
+// stack_depth is the candidate-stack capacity of the walk (128, 192 or 256).
 size_t batch_req_bytes();
 void fill_batch_req(void *dst, const System *s, const tpm_force_params *p);
-int launch_walk_batch(Ctx *c, int stack_depth, const void *reqs, const uint4 *groups, const unsigned *n_groups,
-                      unsigned *next, const uint32_t *sidx, const uint32_t *slot, const float *a_old, float *acc,
-                      float *pot, uint32_t *nint, int *err, cudaStream_t st);
+int launch_walk_batch(Ctx *c, int group_size, int stack_depth, const void *reqs, const uint4 *groups,
+                      const unsigned *n_groups, unsigned *next, const uint32_t *sidx, const uint32_t *slot,
+                      const float *a_old, float *acc, float *pot, uint32_t *nint, int *err, cudaStream_t st);
 
 // FP64 conservation diagnostics over all particles of s (device arrays in the
 // caller's order): out_host[0..2] total force, [3] potential energy, [4]

@@ -1431,6 +1431,488 @@ __global__ void __launch_bounds__(kGroupWarps * 32)
     }
 }
 
+// ======================================================================
+// 64-particle groups (the batched walk: open boundaries, one softening
+// length).  Lane l holds particles l and l + 32 of the group; lane masks are
+// 64-bit (bit p = particle p).  Candidates, bounds, undecided nodes and
+// queues work as in group_walk; each pair term runs through the two-wide
+// FP32 instructions over the lane's two particles, so every node record the
+// warp reads serves 64 particles.
+// ======================================================================
+template <int STACK>
+struct GroupShared64 {
+    static constexpr int kStack = STACK;
+    static constexpr int kSafe = STACK - 64;  // above this, take one candidate at a time
+    uint32_t schild[STACK];                  // first child of a range
+    unsigned long long smask[STACK];         // particles that need it
+    uint8_t scount[STACK];
+    float4 nsrc[kNodeCap];                   // accepted node: centre of mass (group frame) + mass
+    unsigned long long nmask[kNodeCap];
+    float4 lsrc[kLeafCap];                   // opened leaf: centre (group frame) + first particle
+    unsigned long long lmask[kLeafCap];
+    uint32_t lcount[kLeafCap];
+    uint32_t unode[kUndCap];                 // nodes the bounds left undecided
+    unsigned long long umask[kUndCap];
+    float4 pxy[32];                          // the particles by pairs (2i, 2i + 1): (x, x', y, y')
+    float4 pzt[32];                          // (z, z', t, t')
+};
+
+template <class SH>
+__device__ __forceinline__ void put_part64(SH &sh, int p, float x, float y, float z, float t) {
+    float *a = reinterpret_cast<float *>(&sh.pxy[p >> 1]);
+    float *b = reinterpret_cast<float *>(&sh.pzt[p >> 1]);
+    const int o = p & 1;
+    a[o] = x;
+    a[2 + o] = y;
+    b[o] = z;
+    b[2 + o] = t;
+}
+
+__device__ __forceinline__ unsigned long long ballot64(bool lo, bool hi) {
+    return (unsigned long long)__ballot_sync(0xffffffffu, lo) |
+           ((unsigned long long)__ballot_sync(0xffffffffu, hi) << 32);
+}
+
+// Walks the tree for the group of gcount <= 64 active particles at positions
+// [g0, g0 + gcount) of the sorted active list, two per lane.
+template <bool RELATIVE, class SH>
+__device__ __forceinline__ void group_walk64(const TreeView &T, const WalkConsts &k, SH &sh,
+                                             const uint32_t *__restrict__ sidx, const uint32_t *__restrict__ slot,
+                                             int64_t g0, int gcount, const float *__restrict__ a_old,
+                                             float *__restrict__ acc, float *__restrict__ pot,
+                                             uint32_t *__restrict__ nint, int *__restrict__ err) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    const double x0 = T.x0, y0 = T.y0, z0 = T.z0, L0 = T.L0;
+    const float4 *__restrict__ bcen = T.bcen;
+    const float4 *__restrict__ bcom = T.bcom;
+    const int4 *__restrict__ blink = T.blink;
+    const float4 *__restrict__ spart = T.spart;
+    const uint32_t *__restrict__ perm = T.perm;
+    const double *__restrict__ pos = T.pos;
+    const bool v0 = lane < gcount, v1 = lane + 32 < gcount;
+    const int64_t glast = g0 + gcount - 1;
+    const int64_t i0 = v0 ? g0 + lane : g0, i1 = v1 ? g0 + 32 + lane : g0;
+    const uint32_t s0 = sidx ? sidx[i0] : (uint32_t)i0, s1 = sidx ? sidx[i1] : (uint32_t)i1;
+    const uint32_t o0 = slot ? slot[i0] : perm[s0], o1 = slot ? slot[i1] : perm[s1];
+    const uint32_t s_first = sidx ? sidx[g0] : (uint32_t)g0;
+    const uint32_t s_last = sidx ? sidx[glast] : (uint32_t)glast;
+
+    // frame: the key cell of the first and last particle, moved to the middle
+    // of the group's bounding box on the grid of the node centres (as in
+    // group_walk)
+    const uint64_t kf = T.key[s_first], kl = T.key[s_last];
+    const uint64_t kx = kf ^ kl;
+    const int glevel = kx ? min((__clzll(kx) - 1) / 3, kMaxLevel) : kMaxLevel;
+    const uint64_t gpre = kf >> (3 * (kMaxLevel - glevel));
+    const double ghalf = ldexp(L0, -(glevel + 1));
+    double gc[3] = {(double)(2 * (uint64_t)compact3w(gpre) + 1) * ghalf,
+                    (double)(2 * (uint64_t)compact3w(gpre >> 1) + 1) * ghalf,
+                    (double)(2 * (uint64_t)compact3w(gpre >> 2) + 1) * ghalf};
+    const double org[3] = {x0, y0, z0};
+    if (k.plain)  // the plain FP32 form: absolute FP32 coordinates
+        for (int a = 0; a < 3; a++)
+            gc[a] = -org[a];
+    const uint32_t j0 = perm[s0], j1 = perm[s1];
+    double d0[3], d1[3];
+    float p0[3], p1[3];
+    for (int a = 0; a < 3; a++) {
+        d0[a] = pos[3 * j0 + a] - (org[a] + gc[a]);
+        d1[a] = pos[3 * j1 + a] - (org[a] + gc[a]);
+        p0[a] = (float)d0[a];
+        p1[a] = (float)d1[a];
+    }
+    const float inf = __int_as_float(0x7f800000);
+    float lo[3], hi[3];
+    auto bounding_box = [&]() {
+        for (int a = 0; a < 3; a++) {
+            lo[a] = fminf(v0 ? p0[a] : inf, v1 ? p1[a] : inf);
+            hi[a] = fmaxf(v0 ? p0[a] : -inf, v1 ? p1[a] : -inf);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                lo[a] = fminf(lo[a], __shfl_xor_sync(FULL, lo[a], o));
+                hi[a] = fmaxf(hi[a], __shfl_xor_sync(FULL, hi[a], o));
+            }
+        }
+    };
+    bounding_box();
+    if (!k.plain) {
+        const float q = (float)ldexp(L0, -22), iq = (float)ldexp(1.0 / L0, 22);
+        for (int a = 0; a < 3; a++) {
+            const float sa = q * rintf(0.5f * (lo[a] + hi[a]) * iq);
+            gc[a] += (double)sa;
+            p0[a] = (float)(d0[a] - (double)sa);
+            p1[a] = (float)(d1[a] - (double)sa);
+        }
+        bounding_box();
+    }
+    const float gcx = (float)gc[0], gcy = (float)gc[1], gcz = (float)gc[2];
+    float t0 = k.thr_const, t1 = k.thr_const;
+    if (RELATIVE) {
+        t0 = v0 ? k.alpha_over_G * fabsf(a_old[o0]) : 0.0f;
+        t1 = v1 ? k.alpha_over_G * fabsf(a_old[o1]) : 0.0f;
+    }
+    float tmin = fminf(v0 ? t0 : inf, v1 ? t1 : inf), tmax = fmaxf(v0 ? t0 : 0.0f, v1 ? t1 : 0.0f);
+    if (RELATIVE) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            tmin = fminf(tmin, __shfl_xor_sync(FULL, tmin, o));
+            tmax = fmaxf(tmax, __shfl_xor_sync(FULL, tmax, o));
+        }
+    }
+    const unsigned long long valid_mask = ballot64(v0, v1);
+    put_part64(sh, lane, p0[0], p0[1], p0[2], t0);
+    put_part64(sh, lane + 32, p1[0], p1[1], p1[2], t1);
+    // the lane's two particles as pairs for the two-wide instructions
+    const float2 nx = make_float2(-p0[0], -p1[0]), ny = make_float2(-p0[1], -p1[1]), nz = make_float2(-p0[2], -p1[2]);
+    float2 sx = make_float2(0.f, 0.f), sy = sx, sz = sx, sp = sx;  // acceleration and potential sums
+    uint32_t c0 = 0, c1 = 0;                                       // interaction counts
+    if (lane == 0) {
+        sh.schild[0] = 0u;  // the root, breadth-first index 0
+        sh.smask[0] = valid_mask;
+        sh.scount[0] = 1;
+    }
+    int sn = 1, nf = 0, np = 0, nl = 0, nu = 0;
+    __syncwarp();
+    for (;;) {
+        const bool done = sn == 0 && nu == 0;
+        if (!done) {
+            const int room = SH::kStack - 53 - sn;
+            const bool resolve = nu > 0 && (sn == 0 || (nu >= 32 && room >= 32) || nu > kUndCap - 33);
+            int cls = kNone;
+            unsigned long long nmask = 0ull, amask = 0ull;
+            float4 C = make_float4(0.f, 0.f, 0.f, 0.f), O = C;
+            int4 Lk = make_int4(0, 0, 0, 0);
+            float dcx = 0.f, dcy = 0.f, dcz = 0.f;
+            uint32_t node = 0;
+            if (resolve) {
+                // ---- one waiting node per lane, decided for all 64 particles
+                const int nr = min(min(nu, 32), max(room, 1));
+                unsigned long long um = 0ull;
+                if (lane < nr) {
+                    node = sh.unode[nu - nr + lane];
+                    um = sh.umask[nu - nr + lane];
+                    C = __ldg(&bcen[node]);
+                    O = __ldg(&bcom[node]);
+                    Lk = __ldg(&blink[node]);
+                }
+                nu -= nr;
+                dcx = C.x - gcx;
+                dcy = C.y - gcy;
+                dcz = C.z - gcz;  // exact
+                const float L = C.w;
+                const float q = RELATIVE ? O.w * L * L : L * L;
+                const float gl = 0.6f * L;
+                const float2 ndx = make_float2(-dcx, -dcx), ndy = make_float2(-dcy, -dcy), ndz = make_float2(-dcz, -dcz);
+                const float2 ox = make_float2(O.x, O.x), oy = make_float2(O.y, O.y), oz = make_float2(O.z, O.z);
+                const float2 m1 = make_float2(-1.0f, -1.0f);
+                const bool guard_on = k.box_guard != 0;
+                unsigned long long om = 0ull, am = 0ull, uy = um;
+#pragma unroll 2
+                for (int i = 0; i < 32; i++, uy >>= 2) {
+                    const float4 XY = sh.pxy[i], ZT = sh.pzt[i];
+                    const float2 px = __fadd2_rn(make_float2(XY.x, XY.y), ndx);
+                    const float2 py = __fadd2_rn(make_float2(XY.z, XY.w), ndy);
+                    const float2 pz = __fadd2_rn(make_float2(ZT.x, ZT.y), ndz);
+                    const float2 rx = __ffma2_rn(px, m1, ox), ry = __ffma2_rn(py, m1, oy), rz = __ffma2_rn(pz, m1, oz);
+                    const float2 r2 = __ffma2_rn(rx, rx, __ffma2_rn(ry, ry, __fmul2_rn(rz, rz)));
+                    float2 t = __fmul2_rn(make_float2(ZT.z, ZT.w), r2);
+                    if (RELATIVE)
+                        t = __fmul2_rn(t, r2);
+                    const bool g0b = guard_on && fmaxf(fabsf(px.x), fmaxf(fabsf(py.x), fabsf(pz.x))) <= gl;
+                    const bool g1b = guard_on && fmaxf(fabsf(px.y), fmaxf(fabsf(py.y), fabsf(pz.y))) <= gl;
+                    const bool oa = g0b || q > t.x, ob = g1b || q > t.y;
+                    const unsigned long long b0 = 1ull << (2 * i), b1 = 2ull << (2 * i);
+                    if (uy & 1ull)
+                        oa ? (om |= b0) : (am |= b0);
+                    if (uy & 2ull)
+                        ob ? (om |= b1) : (am |= b1);
+                }
+                nmask = om;
+                amask = am;
+                cls = lane < nr ? kMixed : kNone;
+            } else {
+                // ---- up to 32 candidates from the top child ranges
+                const int cap = sn > SH::kSafe ? 1 : 32;
+                const int idx = sn - 1 - lane;
+                uint32_t rchild = 0u;
+                unsigned long long rmask = 0ull;
+                int c = 0;
+                if (idx >= 0) {
+                    rchild = sh.schild[idx];
+                    rmask = sh.smask[idx];
+                    c = sh.scount[idx];
+                }
+                int incl = c;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(FULL, incl, o);
+                    if (lane >= o)
+                        incl += v;
+                }
+                const int excl = incl - c;
+                const bool take = idx >= 0 && c > 0 && excl < cap;
+                const bool whole = take && incl <= cap;
+                const int ntake = take ? min(c, cap - excl) : 0;
+                const int nwhole = __popc(__ballot_sync(FULL, whole));
+                const int ncand = min(__shfl_sync(FULL, incl, 31), cap);
+                int r = 0;
+#pragma unroll
+                for (int b = 16; b > 0; b >>= 1)
+                    if (__shfl_sync(FULL, incl, r + b - 1) <= lane)
+                        r += b;
+                const uint32_t cnode = __shfl_sync(FULL, rchild, r) + (uint32_t)(lane - __shfl_sync(FULL, excl, r));
+                const unsigned long long cmask = __shfl_sync(FULL, rmask, r);
+                if (take && !whole) {  // the partly taken range stays on top
+                    sh.schild[idx] = rchild + (uint32_t)ntake;
+                    sh.scount[idx] = (uint8_t)(c - ntake);
+                }
+                sn -= nwhole;
+                __syncwarp();
+                if (lane < ncand) {
+                    node = cnode;
+                    nmask = cmask;
+                    C = __ldg(&bcen[cnode]);
+                    O = __ldg(&bcom[cnode]);
+                    Lk = __ldg(&blink[cnode]);
+                    cls = classify_group<false, RELATIVE, false, false>(C, O, gcx, gcy, gcz, lo[0], lo[1], lo[2], hi[0],
+                                                                        hi[1], hi[2], tmin, tmax, false, 0.0f, inf, k,
+                                                                        dcx, dcy, dcz);
+                }
+                const unsigned bm = __ballot_sync(FULL, cls == kMixed);
+                if (cls == kMixed) {
+                    const int at = nu + __popc(bm & lt_mask);
+                    sh.unode[at] = node;
+                    sh.umask[at] = nmask;
+                }
+                nu += __popc(bm);
+                if (cls == kAccept) {
+                    amask = nmask;
+                    nmask = 0ull;
+                } else if (cls != kOpen) {
+                    nmask = 0ull;
+                }
+            }
+            __syncwarp();
+            // ---- queue what the particles accept and open
+            const bool is_leaf = Lk.y == 0;
+            const bool e_acc = amask != 0ull;
+            const bool e_full = e_acc && amask == valid_mask;
+            const unsigned bf = __ballot_sync(FULL, e_full);
+            const unsigned bq = __ballot_sync(FULL, e_acc && !e_full);
+            if (e_acc) {
+                const int at = e_full ? nf + __popc(bf & lt_mask) : kNodeCap - 1 - np - __popc(bq & lt_mask);
+                sh.nsrc[at] = make_float4(dcx + O.x, dcy + O.y, dcz + O.z, O.w);
+                sh.nmask[at] = amask;
+            }
+            nf += __popc(bf);
+            np += __popc(bq);
+            const bool e_leaf = nmask != 0ull && is_leaf, e_push = nmask != 0ull && !is_leaf;
+            const unsigned bl = __ballot_sync(FULL, e_leaf);
+            if (e_leaf) {
+                const int at = nl + __popc(bl & lt_mask);
+                sh.lsrc[at] = make_float4(dcx, dcy, dcz, __int_as_float(Lk.z));
+                sh.lmask[at] = nmask;
+                sh.lcount[at] = (uint32_t)Lk.w;
+            }
+            nl += __popc(bl);
+            const unsigned bp = __ballot_sync(FULL, e_push);
+            if (e_push) {
+                const int at = sn + __popc(bp & lt_mask);
+                if (at < SH::kStack) {
+                    sh.schild[at] = (uint32_t)Lk.x;
+                    sh.smask[at] = nmask;
+                    sh.scount[at] = (uint8_t)Lk.y;
+                } else {
+                    atomicOr(err, 2);
+                }
+            }
+            sn = min(sn + __popc(bp), SH::kStack);
+            __syncwarp();
+        }
+        if (done || nf + np >= kNodeFlush) {
+            // ---- monopoles: the lane's two particles per entry; a particle
+            // outside the entry's mask adds zero mass; every entry first at
+            // max(r, h), then the h-terms of entries inside h replaced
+            float rmin = inf;
+            const int e0 = kNodeCap - np;
+            for (int pass = 0; pass < 2; pass++) {
+                const int ea = pass ? e0 : 0, eb = pass ? kNodeCap : nf;
+#pragma unroll 2
+                for (int e = ea; e < eb; e++) {
+                    const float4 A = sh.nsrc[e];
+                    float2 m = make_float2(A.w, A.w);
+                    if (pass) {
+                        const unsigned long long M = sh.nmask[e];
+                        const bool ma = (M >> lane) & 1ull, mb = (M >> (lane + 32)) & 1ull;
+                        m = make_float2(ma ? A.w : 0.0f, mb ? A.w : 0.0f);
+                        c0 += ma ? 1u : 0u;
+                        c1 += mb ? 1u : 0u;
+                    }
+                    const float2 rx = __fadd2_rn(make_float2(A.x, A.x), nx);
+                    const float2 ry = __fadd2_rn(make_float2(A.y, A.y), ny);
+                    const float2 rz = __fadd2_rn(make_float2(A.z, A.z), nz);
+                    const float2 r2 = __ffma2_rn(rx, rx, __ffma2_rn(ry, ry, __fmul2_rn(rz, rz)));
+                    rmin = fminf(rmin, fminf(r2.x, r2.y));
+                    const float2 ri = make_float2(rsqrtf(fmaxf(r2.x, k.h2)), rsqrtf(fmaxf(r2.y, k.h2)));
+                    const float2 mr = __fmul2_rn(m, ri);
+                    const float2 mr3 = __fmul2_rn(__fmul2_rn(mr, ri), ri);
+                    sx = __ffma2_rn(mr3, rx, sx);
+                    sy = __ffma2_rn(mr3, ry, sy);
+                    sz = __ffma2_rn(mr3, rz, sz);
+                    sp = __fadd2_rn(sp, mr);
+                }
+            }
+            c0 += v0 ? (uint32_t)nf : 0u;
+            c1 += v1 ? (uint32_t)nf : 0u;
+            if (__any_sync(FULL, rmin < k.h2)) {
+                for (int pass = 0; pass < 2; pass++) {
+                    const int ea = pass ? e0 : 0, eb = pass ? kNodeCap : nf;
+                    for (int e = ea; e < eb; e++) {
+                        const float4 A = sh.nsrc[e];
+                        const unsigned long long M = pass ? sh.nmask[e] : ~0ull;
+                        for (int h = 0; h < 2; h++) {
+                            const float *pp = h ? p1 : p0;
+                            const bool mine = (M >> (lane + 32 * h)) & 1ull;
+                            const float rx = A.x - pp[0], ry = A.y - pp[1], rz = A.z - pp[2];
+                            const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+                            if (mine && r2 < k.h2) {
+                                float ax = 0.f, ay = 0.f, az = 0.f, ph = 0.f;
+                                newton_term(rx, ry, rz, k.h2, -A.w, ax, ay, az, ph);
+                                pair_term<false>(rx, ry, rz, r2, A.w, k, ax, ay, az, ph);
+                                if (h) {
+                                    sx.y += ax; sy.y += ay; sz.y += az; sp.y -= ph;
+                                } else {
+                                    sx.x += ax; sy.x += ay; sz.x += az; sp.x -= ph;
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+            nf = np = 0;
+        }
+        if (done || nl >= kLeafFlush) {
+            // ---- opened leaves, particle by particle (pairs inside h as above)
+            for (int e = 0; e < nl; e++) {
+                const float4 E = sh.lsrc[e];
+                const unsigned long long M = sh.lmask[e];
+                const bool ma = (M >> lane) & 1ull, mb = (M >> (lane + 32)) & 1ull;
+                const float2 qx0 = make_float2(p0[0] - E.x, p1[0] - E.x), qy0 = make_float2(p0[1] - E.y, p1[1] - E.y),
+                             qz0 = make_float2(p0[2] - E.z, p1[2] - E.z);  // particle relative to the leaf centre
+                const int ja = __float_as_int(E.w), jb = ja + (int)sh.lcount[e];
+                bool close = false;
+                for (int jj = ja; jj < jb; jj++) {
+                    const float4 P = __ldg(&spart[jj]);
+                    const bool ua = ma && (uint32_t)jj != s0, ub = mb && (uint32_t)jj != s1;
+                    const float2 qx = __fadd2_rn(make_float2(P.x, P.x), make_float2(-qx0.x, -qx0.y));
+                    const float2 qy = __fadd2_rn(make_float2(P.y, P.y), make_float2(-qy0.x, -qy0.y));
+                    const float2 qz = __fadd2_rn(make_float2(P.z, P.z), make_float2(-qz0.x, -qz0.y));
+                    const float2 q2 = __ffma2_rn(qx, qx, __ffma2_rn(qy, qy, __fmul2_rn(qz, qz)));
+                    close |= (ua && q2.x < k.h2) || (ub && q2.y < k.h2);
+                    c0 += ua ? 1u : 0u;
+                    c1 += ub ? 1u : 0u;
+                    const float2 ri = make_float2(rsqrtf(fmaxf(q2.x, k.h2)), rsqrtf(fmaxf(q2.y, k.h2)));
+                    const float2 mr = __fmul2_rn(make_float2(ua ? P.w : 0.0f, ub ? P.w : 0.0f), ri);
+                    const float2 mr3 = __fmul2_rn(__fmul2_rn(mr, ri), ri);
+                    sx = __ffma2_rn(mr3, qx, sx);
+                    sy = __ffma2_rn(mr3, qy, sy);
+                    sz = __ffma2_rn(mr3, qz, sz);
+                    sp = __fadd2_rn(sp, mr);
+                }
+                if (__any_sync(FULL, close)) {
+                    for (int jj = ja; jj < jb; jj++) {
+                        const float4 P = __ldg(&spart[jj]);
+                        for (int h = 0; h < 2; h++) {
+                            const bool u = h ? (mb && (uint32_t)jj != s1) : (ma && (uint32_t)jj != s0);
+                            const float qx = P.x - (h ? qx0.y : qx0.x), qy = P.y - (h ? qy0.y : qy0.x),
+                                        qz = P.z - (h ? qz0.y : qz0.x);
+                            const float q2 = fmaf(qx, qx, fmaf(qy, qy, qz * qz));
+                            if (u && q2 < k.h2) {
+                                float ax = 0.f, ay = 0.f, az = 0.f, ph = 0.f;
+                                newton_term(qx, qy, qz, k.h2, -P.w, ax, ay, az, ph);
+                                pair_term<false>(qx, qy, qz, q2, P.w, k, ax, ay, az, ph);
+                                if (h) {
+                                    sx.y += ax; sy.y += ay; sz.y += az; sp.y -= ph;
+                                } else {
+                                    sx.x += ax; sy.x += ay; sz.x += az; sp.x -= ph;
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+            nl = 0;
+        }
+        if (done)
+            break;
+        __syncwarp();
+    }
+    const float G = k.G;
+    if (v0) {
+        acc[3 * (size_t)o0] = G * sx.x;
+        acc[3 * (size_t)o0 + 1] = G * sy.x;
+        acc[3 * (size_t)o0 + 2] = G * sz.x;
+        if (pot)
+            pot[o0] = -G * sp.x;
+        if (nint)
+            nint[o0] = c0;
+    }
+    if (v1) {
+        acc[3 * (size_t)o1] = G * sx.y;
+        acc[3 * (size_t)o1 + 1] = G * sy.y;
+        acc[3 * (size_t)o1 + 2] = G * sz.y;
+        if (pot)
+            pot[o1] = -G * sp.y;
+        if (nint)
+            nint[o1] = c1;
+    }
+}
+
+// Walks a 64-particle group in one frame, or -- when a half of it needs
+// cutting (chunk_cuts) or the two halves lie far apart for their particles'
+// separations -- run by run, each run in its own frame.
+template <bool RELATIVE, class SH>
+__device__ __forceinline__ void walk_runs_of_group64(const TreeView &T, const WalkConsts &k, SH &sh,
+                                                     const uint32_t *__restrict__ sidx,
+                                                     const uint32_t *__restrict__ slot, int64_t g0, int gcount,
+                                                     const float *__restrict__ a_old, float *__restrict__ acc,
+                                                     float *__restrict__ pot, uint32_t *__restrict__ nint,
+                                                     int *__restrict__ err) {
+    unsigned long long cut = 0ull;  // bit i: a run ends after particle i
+    if (!k.plain && gcount > 1) {
+        const int na = min(gcount, 32), nb = gcount - na;
+        const unsigned ca = chunk_cuts(T.key, sidx, g0, na);
+        const unsigned cb = nb > 0 ? chunk_cuts(T.key, sidx, g0 + 32, nb) : 0u;
+        bool between = ca != 0u || cb != 0u;
+        if (!between && nb > 0) {
+            // the pair across the halves against the finest level a member
+            // shares with its neighbour
+            const int lane = threadIdx.x & 31;
+            const int64_t ia = g0 + min(lane, na - 1), ib = g0 + 32 + min(lane, nb - 1);
+            const uint64_t ka = T.key[sidx ? sidx[ia] : (uint32_t)ia], kb = T.key[sidx ? sidx[ib] : (uint32_t)ib];
+            const uint64_t kan = __shfl_down_sync(0xffffffffu, ka, 1), kbn = __shfl_down_sync(0xffffffffu, kb, 1);
+            int fin = max(lane + 1 < na ? common_level(ka, kan) : -1, lane + 1 < nb ? common_level(kb, kbn) : -1);
+            fin = __reduce_max_sync(0xffffffffu, fin + 1) - 1;
+            const int lvb = common_level(__shfl_sync(0xffffffffu, ka, na - 1), __shfl_sync(0xffffffffu, kb, 0));
+            between = fin - lvb > kFrameSpan;
+        }
+        if (between)
+            cut = (unsigned long long)ca | (nb > 0 ? (1ull << 31) : 0ull) | ((unsigned long long)cb << 32);
+    }
+    int start = 0;
+    for (;;) {
+        const int end = cut ? __ffsll((long long)cut) : gcount;
+        group_walk64<RELATIVE>(T, k, sh, sidx, slot, g0 + start, end - start, a_old, acc, pot, nint, err);
+        if (!cut)
+            break;
+        cut &= cut - 1ull;
+        start = end;
+        __syncwarp();
+    }
+}
+
 // One request of a batch: which tree, with which constants and criterion.
 struct BatchReq {
     TreeView T;
@@ -1479,6 +1961,46 @@ __global__ void __launch_bounds__(kGroupWarps * 32, 7)
         else
             walk_runs_of_chunk<PERIODIC, false, TREEPM, false>(R.T, R.k, sh, sidx, slot, G.x, (int)G.y, a_old, acc,
                                                                pot, nint, 0, err);
+        __syncwarp();
+    }
+}
+
+// The persistent batch walk with 64-particle groups (open boundaries, one
+// softening length); five blocks per SM leave the two particles' state in
+// registers (96) without spilling.
+template <int STACK>
+__global__ void __launch_bounds__(kGroupWarps * 32, 5)
+    k_walk_batch64(const BatchReq *__restrict__ reqs, const uint4 *__restrict__ groups,
+                   const unsigned *__restrict__ n_groups, unsigned *__restrict__ next,
+                   const uint32_t *__restrict__ sidx, const uint32_t *__restrict__ slot,
+                   const float *__restrict__ a_old, float *__restrict__ acc, float *__restrict__ pot,
+                   uint32_t *__restrict__ nint, int *__restrict__ err) {
+    using SH = GroupShared64<STACK>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SH &sh = reinterpret_cast<SH *>(smem_raw)[threadIdx.x >> 5];
+    __shared__ __align__(16) BatchReq breq[kGroupWarps];
+    BatchReq &R = breq[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const unsigned total = *n_groups;
+    for (;;) {
+        unsigned g = 0;
+        if (lane == 0)
+            g = atomicAdd(next, 1u);
+        g = __shfl_sync(0xffffffffu, g, 0);
+        if (g >= total)
+            break;
+        const uint4 G = groups[g];
+        {
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(&reqs[G.z]);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(&R);
+            for (int w = lane; w < (int)(sizeof(BatchReq) / 4); w += 32)
+                dst[w] = src[w];
+            __syncwarp();
+        }
+        if (R.relative)
+            walk_runs_of_group64<true>(R.T, R.k, sh, sidx, slot, G.x, (int)G.y, a_old, acc, pot, nint, err);
+        else
+            walk_runs_of_group64<false>(R.T, R.k, sh, sidx, slot, G.x, (int)G.y, a_old, acc, pot, nint, err);
         __syncwarp();
     }
 }
@@ -1574,6 +2096,33 @@ void fill_batch_req(void *dst, const System *s, const tpm_force_params *p) {
 }
 
 template <int STACK>
+int launch_walk_batch64_at(Ctx *c, const void *reqs, const uint4 *groups, const unsigned *n_groups, unsigned *next,
+                           const uint32_t *sidx, const uint32_t *slot, const float *a_old, float *acc, float *pot,
+                           uint32_t *nint, int *err, cudaStream_t st) {
+    const size_t smem = kGroupWarps * sizeof(GroupShared64<STACK>);
+    static int blocks_per_sm = 0;  // resident blocks of this variant (one persistent wave)
+    if (!blocks_per_sm) {
+        if (cudaFuncSetAttribute(k_walk_batch64<STACK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            set_error("64-particle groups: %zu bytes of shared memory per block are not available", smem);
+            return TPM_ECUDA;
+        }
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_walk_batch64<STACK>, kGroupWarps * 32, smem) !=
+                cudaSuccess ||
+            b < 1)
+            b = 1;
+        blocks_per_sm = b;
+    }
+    k_walk_batch64<STACK><<<(unsigned)(c->num_sms * blocks_per_sm), kGroupWarps * 32, smem, st>>>(
+        static_cast<const BatchReq *>(reqs), groups, n_groups, next, sidx, slot, a_old, acc, pot, nint, err);
+    count_launch();
+    TPM_CUDA(cudaGetLastError());
+    return TPM_OK;
+}
+
+template <int STACK>
 int launch_walk_batch_at(Ctx *c, const void *reqs, const uint4 *groups, const unsigned *n_groups, unsigned *next,
                          const uint32_t *sidx, const uint32_t *slot, const float *a_old, float *acc, float *pot,
                          uint32_t *nint, int *err, cudaStream_t st) {
@@ -1594,9 +2143,24 @@ int launch_walk_batch_at(Ctx *c, const void *reqs, const uint4 *groups, const un
     return TPM_OK;
 }
 
-int launch_walk_batch(Ctx *c, int stack_depth, const void *reqs, const uint4 *groups, const unsigned *n_groups,
-                      unsigned *next, const uint32_t *sidx, const uint32_t *slot, const float *a_old, float *acc,
-                      float *pot, uint32_t *nint, int *err, cudaStream_t st) {
+int launch_walk_batch(Ctx *c, int group_size, int stack_depth, const void *reqs, const uint4 *groups,
+                      const unsigned *n_groups, unsigned *next, const uint32_t *sidx, const uint32_t *slot,
+                      const float *a_old, float *acc, float *pot, uint32_t *nint, int *err, cudaStream_t st) {
+    if (group_size == 64) {
+        switch (stack_depth) {
+        case kStackDepths[0]:
+            return launch_walk_batch64_at<kStackDepths[0]>(c, reqs, groups, n_groups, next, sidx, slot, a_old, acc,
+                                                           pot, nint, err, st);
+        case kStackDepths[1]:
+            return launch_walk_batch64_at<kStackDepths[1]>(c, reqs, groups, n_groups, next, sidx, slot, a_old, acc,
+                                                           pot, nint, err, st);
+        case kStackDepths[2]:
+            return launch_walk_batch64_at<kStackDepths[2]>(c, reqs, groups, n_groups, next, sidx, slot, a_old, acc,
+                                                           pot, nint, err, st);
+        default:
+            break;
+        }
+    }
     switch (stack_depth) {
     case kStackDepths[0]:
         return launch_walk_batch_at<kStackDepths[0]>(c, reqs, groups, n_groups, next, sidx, slot, a_old, acc, pot,

@@ -92,7 +92,7 @@ def check(ref, acc, pot, nint, off):
         np.testing.assert_allclose(pot[sl][same], p[same], rtol=P99_TOL)
 
 
-@pytest.mark.parametrize("group", [32, 16, 8])
+@pytest.mark.parametrize("group", [64, 32, 16, 8])
 def test_batch_matches_per_request_calls(env, group):
     tpm, torch, dev, ctx, reqs, aold = env
     ids, off, a_old = batch_inputs(torch, dev, reqs, aold)
@@ -155,7 +155,7 @@ def test_autotune_and_errors(env):
     plan = ctx.create_plan(int(off[-1]), len(reqs))
     acc = torch.empty((len(ids), 3), device=dev)
     g, ms = plan.autotune([r[0] for r in reqs], off, [r[2] for r in reqs], ids, acc, a_old=a_old, reps=2)
-    assert g in (8, 16, 32) and plan.group_size == g and ms > 0
+    assert g in (8, 16, 32, 64) and plan.group_size == g and ms > 0
     assert plan.stack_depth in (128, 192, 256)
     # every stack depth makes the same decisions (interaction counts); the
     # order of the sums may differ where a shallower stack takes candidates one
@@ -232,7 +232,7 @@ def oracle_env(oracle_mod):
     ctx.close()
 
 
-@pytest.mark.parametrize("group", [8, 16, 32])
+@pytest.mark.parametrize("group", [8, 16, 32, 64])
 @pytest.mark.parametrize("depth", [128, 192, 256])
 def test_batch_matches_oracle_walk(oracle_env, group, depth):
     """Every group size and stack depth of the persistent batched walk against
