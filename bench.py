@@ -40,12 +40,12 @@ FLOPS_PER_INTERACTION = 20  # monopole pair term with potential, FP32: offset 3,
 
 # From the ncu capture of one k_walk_group launch of the headline step (its
 # summary is under profiles/), valid only for the walk source it was taken
-# from: DRAM bytes (read + write), and the
-# FP32 flops the kernel executed per cycle over the whole GPU (fadd + fmul +
-# 2 ffma thread instructions) against the FP32 peak per cycle (SMs x 128 x 2)
-WALK_TRAFFIC = {"bytes": 98.750464e6 + 13.277440e6,
-                "fp32_flops_per_cycle": 1761.259910 + 1454.992313 + 2 * 1418.840171,
-                "walk_cu_sha256": "9f18eb7c7639fa84dbc4947853cd28b6b02ba316f56f47b537d42f1ae7223bf3"}
+# from: DRAM bytes (read + write) and the pipe activity of that launch (the
+# FMA pipe's busy cycles, counting the two-wide FP32 instructions, and the
+# ALU pipe's instructions, both against their peaks)
+WALK_TRAFFIC = {"bytes": 100.765184e6 + 14.582784e6,
+                "fma_pipe_active": 0.43417447, "alu_pipe_inst": 0.54919054,
+                "walk_cu_sha256": "b5647f3b414cb0904d1dbc84cd4b2a472a79d8c57a0d2e47584f9ecc2cc3b967"}
 
 
 def walk_capture():
@@ -360,8 +360,8 @@ def run_ours(args, rank, world):
         roofline={"bound": "alu", "kernel": "k_walk_group (relative criterion)", "achieved": achieved,
                   "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                   "traffic": cap["bytes"] if cap else None,
-                  "executed_fp32_frac_ncu": (cap["fp32_flops_per_cycle"] / (props.multi_processor_count * 128 * 2)
-                                             if cap else None),
+                  "fma_pipe_active_ncu": cap["fma_pipe_active"] if cap else None,
+                  "alu_pipe_inst_ncu": cap["alu_pipe_inst"] if cap else None,
                   "frac_at_run_clock": (achieved / (fp32_peak * clocks["sm_mhz"] / sm_max)
                                         if clocks.get("sm_mhz") else None),
                   "peak_kind": "FP32 CUDA-core peak = SMs x 128 x 2 x %.0f MHz (%s sm_max)" % (sm_max, pk_kind),

@@ -54,7 +54,7 @@ def test_walk_traffic_only_for_the_captured_source(monkeypatch):
     monkeypatch.setattr(bench, "WALK_TRAFFIC", dict(same, walk_cu_sha256="0" * 64))
     assert bench.walk_capture() is None
     # the recorded figures are per launch: DRAM bytes of one walk and the executed FP32 rate
-    assert 1e7 < same["bytes"] < 1e9 and 0 < same["fp32_flops_per_cycle"] < 152 * 128 * 2
+    assert 1e7 < same["bytes"] < 1e9 and 0 < same["fma_pipe_active"] <= 1 and 0 < same["alu_pipe_inst"] <= 1
 
 
 def test_peaks_measured_or_fallback():
