@@ -31,9 +31,10 @@ from . import CRIT_BH, CRIT_RELATIVE, BuildParams, Context, ForceParams, TreePME
 _EBUDGET = -2
 
 
-@dataclass
+@dataclass(eq=False)
 class ServeRequest:
-    """Forces on particles ``ids`` of system ``sid`` (arrival in seconds)."""
+    """Forces on particles ``ids`` of system ``sid`` (arrival in seconds).
+    Requests compare by identity."""
 
     rid: int
     sid: int
@@ -68,7 +69,9 @@ class _Resident:
             self.n_valid = int(np.count_nonzero(self.aold_valid))
 
     def ready(self) -> bool:
-        return self.built is None or self.built.query()
+        if self.built is not None and self.built.query():
+            self.built = None  # built: no later round needs to wait for it
+        return self.built is None
 
 
 @dataclass
@@ -129,24 +132,33 @@ class ForceServer:
 
     def __init__(self, ctx: Context, source, max_round_ids: int = 1 << 21, max_round_requests: int = 512,
                  theta: float = 0.5, alpha: float = 0.0025, policy: str = "adaptive", group_size: int = None,
-                 keep_results=True, slots: int = 2):
+                 keep_results=True, slots: int = 2, prioritise_large: bool = True):
         import torch
 
         self.torch = torch
         self.ctx = ctx
         self.source = source
         self.max_ids, self.max_req = int(max_round_ids), int(max_round_requests)
+        self.large_round_ids = 1 << 16
         self.theta, self.alpha, self.policy = theta, alpha, policy
         self.dev = torch.device("cuda", ctx.device)
-        self.build_stream = torch.cuda.Stream(self.dev)
-        self.slots = [_Slot(torch, ctx, self.dev, self.max_ids, self.max_req, group_size) for _ in range(slots)]
+        # the first slot's stream (and the builds) run at high priority: a large
+        # round there keeps its pace while small rounds share the GPU with it
+        self.prioritise_large = bool(prioritise_large)
+        pri = -1 if self.prioritise_large else 0
+        self.build_stream = torch.cuda.Stream(self.dev, priority=pri)
+        self.slots = [_Slot(torch, ctx, self.dev, self.max_ids, self.max_req, group_size, priority=pri if k == 0 else 0)
+                      for k in range(slots)]
         self.plan = self.slots[0].plan
         self.resident: "collections.OrderedDict[int, _Resident]" = collections.OrderedDict()
         self.builds = 0
         self.evictions = 0
         self.keep_results = keep_results
-        self._reserved = set()  # systems picked for the round being formed: not evictable
-        self._wanted = collections.Counter()  # queued requests per system: not evictable either
+        self._wanted = collections.Counter()  # queued requests per system: not evictable
+        self._busy = set()  # systems in a round in flight
+        # a build was refused for memory: no other is tried (and no system drawn
+        # for it) until a round completes and systems become evictable again
+        self._blocked = False
 
     def close(self):
         for r in self.resident.values():
@@ -161,7 +173,7 @@ class ForceServer:
     # -------------------------------------------------------------- residency
     def _evict_one(self) -> bool:
         for sid, r in self.resident.items():  # least recently used first
-            if r.inflight == 0 and r.ready() and sid not in self._reserved and not self._wanted[sid]:
+            if r.inflight == 0 and r.ready() and not self._wanted[sid]:
                 r.system.release()
                 del self.resident[sid]
                 self.evictions += 1
@@ -171,11 +183,14 @@ class ForceServer:
     def ensure_resident(self, sid: int) -> bool:
         """Enqueues the build of ``sid`` on the build stream if it is not
         resident; False if the budget cannot hold it while the systems in
-        flight stay."""
+        flight or wanted by waiting requests stay (after one such refusal,
+        until a round completes)."""
         torch = self.torch
         if sid in self.resident:
             self.resident.move_to_end(sid)
             return True
+        if self._blocked:
+            return False
         with torch.cuda.stream(self.build_stream):  # a source may draw the particles on the device
             pos, mass, bp = self.source(sid)
         while True:
@@ -185,6 +200,7 @@ class ForceServer:
             except TreePMError as e:
                 if e.status != _EBUDGET or not self._evict_one():
                     if e.status == _EBUDGET:
+                        self._blocked = True
                         return False
                     raise
         n = system.n
@@ -213,6 +229,7 @@ class ForceServer:
         st = slot.stream
         slot.busy = True
         for r in reqs:  # the round waits for its own systems' builds only
+            self.resident.move_to_end(r.sid)  # most recently used
             b = self.resident[r.sid].built
             if b is not None:
                 st.wait_event(b)
@@ -229,6 +246,7 @@ class ForceServer:
             for k, r in enumerate(reqs):
                 res = self.resident[r.sid]
                 res.inflight += 1
+                self._busy.add(r.sid)
                 part = ids_d[off[k]:off[k + 1]]
                 fp = self._params_for(res, r.ids)
                 r.criterion = fp.crit
@@ -285,51 +303,73 @@ class ForceServer:
             res = self.resident.get(r.sid)
             if res is not None:
                 res.inflight -= 1
+            self._busy.discard(r.sid)
         rnd.slot.busy = False
+        self._blocked = False
 
     def _form_round(self, queue):
         """Requests for one round, taken out of ``queue``: those whose trees
         are ready first (arrival order), else -- none being ready -- those
         whose trees are building (the round then waits for their builds on the
-        GPU).  Requests of a system in flight stay queued."""
+        GPU), else the first waiting request whose build can start now.
+        Requests of a system in flight stay queued; no build is started while
+        ready requests can go (builds ahead start between rounds, one at a
+        time, in ``serve``)."""
         # a system goes into one round once: a second request for it waits
         # for the next round, whose criterion can then use this round's |a|
-        busy = {sid for sid, r in self.resident.items() if r.inflight}
+        busy = set(self._busy)
         ready, building = [], []
         nids_r = nids_b = 0
-        self._reserved = set()
-        can_build = True
-        try:
-            for r in list(queue):
-                if len(ready) >= self.max_req:
-                    break
-                if r.sid in busy:
-                    continue
-                if r.sid not in self.resident:
-                    # no memory: this request waits for rounds in flight, and
-                    # later ones whose trees are resident still go
-                    if not can_build or not self.ensure_resident(r.sid):
-                        can_build = False
-                        continue
-                res = self.resident[r.sid]
-                if res.ready():
-                    if nids_r + len(r.ids) <= self.max_ids:
-                        ready.append(r)
-                        nids_r += len(r.ids)
-                        self._reserved.add(r.sid)
-                        busy.add(r.sid)
-                elif len(building) < self.max_req and nids_b + len(r.ids) <= self.max_ids:
-                    building.append(r)
-                    nids_b += len(r.ids)
-                    self._reserved.add(r.sid)
+        first_cold = None
+        for r in queue:
+            if len(ready) >= self.max_req or nids_r >= self.max_ids:
+                break
+            if r.sid in busy:
+                continue
+            res = self.resident.get(r.sid)
+            if res is None:
+                if first_cold is None:
+                    first_cold = r
+                continue
+            if res.ready():
+                if nids_r + len(r.ids) <= self.max_ids:
+                    ready.append(r)
+                    nids_r += len(r.ids)
                     busy.add(r.sid)
-        finally:
-            self._reserved = set()
-        batch = ready if ready else building
-        for r in batch:
-            queue.remove(r)
-            self._wanted[r.sid] -= 1
+            elif len(building) < self.max_req and nids_b + len(r.ids) <= self.max_ids:
+                building.append(r)
+                nids_b += len(r.ids)
+                busy.add(r.sid)
+        batch = ready or building
+        if not batch and first_cold is not None and self.ensure_resident(first_cold.sid):
+            batch = [first_cold]
+        if batch:
+            taken = {id(r) for r in batch}
+            rest = [r for r in queue if id(r) not in taken]
+            queue.clear()
+            queue.extend(rest)
+            for r in batch:
+                self._wanted[r.sid] -= 1
         return batch
+
+    def _pick_slot(self, free, batch):
+        """The high-priority slot for a large round (or a round that waits for
+        a build), a low-priority one for a small round when one is free."""
+        if len(free) == 1 or not self.prioritise_large:
+            return free[0]
+        large = sum(len(r.ids) for r in batch) >= self.large_round_ids or any(
+            self.resident[r.sid].built is not None for r in batch)
+        return free[0] if large else free[-1]
+
+    def _build_ahead(self, queue) -> bool:
+        """Starts the build of the first waiting request's system that is not
+        resident (one per call); False if there is none or it does not fit."""
+        for k, r in enumerate(queue):
+            if k >= self.max_req:
+                break
+            if r.sid not in self.resident:
+                return self.ensure_resident(r.sid)
+        return False
 
     def serve(self, requests, realtime: bool = True):
         """Serves ``requests`` (sorted by arrival).  With ``realtime`` a request
@@ -349,28 +389,23 @@ class ForceServer:
             for rnd in [x for x in inflight if x.event.query()]:
                 self._complete(rnd, t0)
                 inflight.remove(rnd)
+            if not inflight:
+                self._blocked = False  # every resident system not wanted is evictable
             free = [sl for sl in self.slots if not sl.busy]
-            launched = False
             if queue and free:
                 batch = self._form_round(queue)
                 if batch:
-                    inflight.append(self._launch(batch, free[0]))
-                    launched = True
-                elif not inflight:
+                    inflight.append(self._launch(batch, self._pick_slot(free, batch)))
+                    continue
+                if not inflight:
                     r = queue[0]
                     if len(r.ids) > self.max_ids:
                         raise ValueError("request %d larger than the server's round size" % r.rid)
-                    if r.sid not in self.resident:
-                        raise MemoryError("the tree of system %d does not fit in the HBM budget" % r.sid)
-            if launched:
-                continue
+                    raise MemoryError("the tree of system %d does not fit in the HBM budget" % r.sid)
             if queue:
                 # admit while the GPU walks: start a build a waiting request
                 # needs -- one per pass, so that finished rounds are seen
-                for r in list(queue)[:self.max_req]:
-                    if r.sid not in self.resident:
-                        self.ensure_resident(r.sid)
-                        break
+                self._build_ahead(queue)
                 time.sleep(0)
             elif inflight:
                 time.sleep(0)
