@@ -638,6 +638,15 @@ def run_serving(tpm, torch, dev):
     for rid, smp in samples.items():
         pos, mass, bp = source(smp["sid"])
         smp.update(pos=pos.cpu().numpy(), mass=mass.cpu().numpy(), h=bp.h)
+    # the first timed requests' systems on the host (up to 2^21 ids in all),
+    # for the oracle's per-request time (cpu_baseline leg)
+    cpu_systems, tot = [], 0
+    for k, sid, ids, t in reqs[nw:nw + 20]:
+        if tot + len(ids) > (1 << 21):
+            break
+        pos, mass, bp = source(sid)
+        cpu_systems.append((pos.cpu().numpy(), mass.cpu().numpy(), bp.h, bp.shift, ids))
+        tot += len(ids)
     ctx.close()
     res.update(workload="serving_%d_systems_N2^12-2^20_poisson%dHz_%d_requests_after_%d_budget%dGB" % (
         len(cat), int(cfg["rate"]), cfg["n_requests"], nw, cfg["budget_gb"]), hbm_budget_bytes=budget,
@@ -646,7 +655,7 @@ def run_serving(tpm, torch, dev):
               "per_request": "one build (if needed), one compute_forces call and one synchronisation per "
                              "request, mixed precision",
               "per_request_plain_fp32": "the same with the plain FP32 form (absolute FP32 coordinates)"},
-        _samples=samples)
+        _samples=samples, _cpu_systems=cpu_systems)
     return res
 
 
@@ -938,6 +947,68 @@ def run_oracle_sample(sample: int, nthreads: int = 0):
                 interactions_per_particle=float(nint.mean()))
 
 
+def run_oracle_configs(serve_systems=None) -> dict:
+    """The FP64 oracle (as it stands) on the other configurations, for the
+    per-configuration CPU rows: the Plummer step in full; the periodic box's
+    mesh, build and a sample of its walk (scaled to all particles); the
+    time-bin cycle at the oracle's relative-walk rate on the Hernquist tree;
+    and, given the particles of a few served systems, the per-request time
+    of one build plus one geometric walk of a request's ids."""
+    import oracle
+
+    out = {}
+    cfg = PLUMMER
+    pos, mass = W.plummer(cfg["n"], W.CONFIG_SEEDS[1])
+    n = len(pos)
+    t0 = time.perf_counter()
+    tree = oracle.Tree(pos, mass, bucket=cfg["bucket"], shift=root_shift(100, 1))
+    tree.walk(np.arange(n, dtype=np.uint32), cfg["G"], cfg["h"], theta=cfg["theta"])
+    t = time.perf_counter() - t0
+    out["plummer_8192"] = {"value": n / t, "unit": "forces/s", "ms_per_step": t * 1e3,
+                           "sample": "the whole step: build + BH walk of all 8192 particles"}
+
+    zc = ZELDOVICH
+    pos, mass = zeldovich_inputs()
+    n = len(pos)
+    sample = 4096
+    tg = W.random_targets(n, sample, 79)
+    h = zeldovich_h()
+    rs = zc["asmth"] * 1.0 / zc["pm_n"]
+    t0 = time.perf_counter()
+    phi = oracle.pm_potential(pos, mass, 1.0, zc["pm_n"], rs, zc["G"])
+    t_pm = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    tree = oracle.Tree(pos, mass, bucket=zc["bucket"], periodic=True, box=1.0, shift=root_shift(0, 3))
+    t_build = time.perf_counter() - t0
+    kw = dict(treepm=True, rs=rs, rcut=zc["rcut"] * rs)
+    a_bh, _, _ = tree.walk(tg, zc["G"], h, theta=zc["theta"], **kw)
+    a_old = np.linalg.norm(a_bh, axis=1).astype(np.float32)
+    t0 = time.perf_counter()
+    tree.walk(tg, zc["G"], h, crit="rel", alpha=zc["alpha"], a_old=a_old, **kw)
+    t_walk = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.pm_interpolate(phi, pos, 1.0)
+    t_interp = time.perf_counter() - t0
+    t_step = t_pm + t_build + t_interp + t_walk * n / sample
+    out["periodic_treepm"] = {"value": n / t_step, "unit": "forces/s", "ms_per_step": t_step * 1e3,
+                              "pm_ms": (t_pm + t_interp) * 1e3, "build_ms": t_build * 1e3,
+                              "sample": "mesh, build and interpolation in full, relative walk of %d random "
+                                        "targets scaled to all %d" % (sample, n)}
+    if serve_systems:
+        lat = []
+        for pos, mass, h, shift, ids in serve_systems:
+            t0 = time.perf_counter()
+            tree = oracle.Tree(pos, mass, bucket=8, shift=shift)
+            tree.walk(ids.astype(np.uint32), 1.0, h, theta=0.5)
+            lat.append(time.perf_counter() - t0)
+        lat = np.array(lat) * 1e3
+        out["serving"] = {"latency_ms_p50": float(np.percentile(lat, 50)),
+                          "latency_ms_p99": float(np.percentile(lat, 99)), "requests": len(lat),
+                          "sample": "build + geometric walk of each request's ids, for the first %d timed "
+                                    "requests, one after another" % len(lat)}
+    return out
+
+
 def oracle_floor(ctx) -> dict:
     """The FP64 oracle walk on the accuracy targets of the headline step (the
     same tree shift and |a_old|) against the stored exact sum: the method's
@@ -1048,6 +1119,7 @@ def main():
     if rank == 0:
         floor_ctx = out.pop("_floor_ctx", None)
         samples = out["serving"].pop("_samples", None) if out.get("serving") else None
+        serve_cpu = out["serving"].pop("_cpu_systems", None) if out.get("serving") else None
         if not args.no_cpu_baseline:
             import oracle
 
@@ -1058,11 +1130,17 @@ def main():
                 out["serving"]["accuracy"] = serving_accuracy(samples)
             r = run_oracle_sample(65536)
             r1 = run_oracle_sample(4096, nthreads=1)
+            per = run_oracle_configs(serve_cpu)
+            # the time-bin cycle on the same tree: its forces at the oracle's
+            # relative-walk rate of the headline sample (no rebuild per request)
+            per["batching"] = {"value": r["sample"] / r["t_walk_sample"], "unit": "forces/s",
+                               "sample": "relative-walk rate of the headline sample on the Hernquist tree"}
             out["cpu_baseline"] = {"value": r["value"], "unit": "forces/s", "cores": cores(), "kind": "oracle",
                                    "sample": "whole tree build + relative walk of %d random active particles, "
                                              "extrapolated to all 2^20" % r["sample"],
                                    "single_core": {"value": r1["value"], "unit": "forces/s", "cores": 1,
-                                                   "sample": "the same with %d particles" % r1["sample"]}}
+                                                   "sample": "the same with %d particles" % r1["sample"]},
+                                   "per_config": per}
         print(json.dumps(out))
     if world > 1:
         import torch

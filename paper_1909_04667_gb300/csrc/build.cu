@@ -62,11 +62,64 @@ __host__ __device__ inline double from_ordered_bits(long long b) {
 #endif
 }
 
+// Device-side bookkeeping of one build (its host copy also receives the node
+// count).
+struct BuildState {
+    long long bbox[6];
+    int bad;
+    unsigned total;  // nodes of the tree
+    double x0[3];
+    double L0;
+    double scale;  // 2^21 / L0
+    unsigned blocks_done;  // k_prepare blocks that have reduced their bounding box
+};
+
+__device__ double pow2_ceil_d(double x) {
+    int e;
+    const double f = frexp(x, &e);
+    return (f == 0.5) ? ldexp(1.0, e - 1) : ldexp(1.0, e);
+}
+
+// Root cube (one thread, once the bounding box is complete): periodic
+// [0, box); open boundaries: the smallest power of two L0 >= 1.25 x the
+// largest extent, x0 = lo - shift (L0 - extent) rounded down to the 2^-21 L0
+// grid.  Round-to-nearest operations only.
+__device__ void root_cube(BuildState *__restrict__ st, int periodic, double box, double s0, double s1, double s2) {
+    if (periodic) {
+        st->x0[0] = st->x0[1] = st->x0[2] = 0.0;
+        st->L0 = box;
+    } else {
+        double lo[3], hi[3], ext = 0.0;
+        for (int a = 0; a < 3; a++) {
+            lo[a] = from_ordered_bits(__ldcg(&st->bbox[a]));  // reduced by other blocks' atomics
+            hi[a] = from_ordered_bits(__ldcg(&st->bbox[3 + a]));
+            ext = fmax(ext, __dsub_rn(hi[a], lo[a]));
+        }
+        if (!(ext > 0.0))
+            ext = 1.0;
+        const double L0 = pow2_ceil_d(__dmul_rn(1.25, ext));
+        const double unit = ldexp(L0, -kMaxLevel);
+        const double sh[3] = {s0, s1, s2};
+        for (int a = 0; a < 3; a++) {
+            const double slack = __dsub_rn(L0, __dsub_rn(hi[a], lo[a]));
+            const double x0 = __dsub_rn(lo[a], __dmul_rn(sh[a], slack));
+            st->x0[a] = __dmul_rn(floor(__ddiv_rn(x0, unit)), unit);
+        }
+        st->L0 = L0;
+    }
+    st->scale = __ddiv_rn(ldexp(1.0, kMaxLevel), st->L0);
+}
+
 // Copies positions and masses into the system, applies the periodic shift and
-// wrap, checks finiteness and ranges, and reduces the bounding box.
-__global__ void k_prepare(const double *__restrict__ pin, const float *__restrict__ mass_in, int64_t n, int periodic,
-                          double box, double s0, double s1, double s2, double *__restrict__ pout,
-                          float *__restrict__ mout, long long *__restrict__ bbox, int *__restrict__ bad) {
+// wrap, checks finiteness and ranges (and the per-particle softening lengths,
+// if any), and reduces the bounding box; the last block to finish computes the
+// root cube from it.
+__global__ void k_prepare(const double *__restrict__ pin, const float *__restrict__ mass_in,
+                          const float *__restrict__ hsoft, int64_t n, int periodic, double box, double s0, double s1,
+                          double s2, double *__restrict__ pout, float *__restrict__ mout,
+                          BuildState *__restrict__ state) {
+    long long *bbox = state->bbox;
+    int *bad = &state->bad;
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     long long lo[3], hi[3];
     bool have = i < n;
@@ -91,6 +144,11 @@ __global__ void k_prepare(const double *__restrict__ pin, const float *__restric
         if (!(m > 0.0f) || !isfinite(m))
             atomicOr(bad, 4);
         mout[i] = m;
+        if (hsoft) {
+            const float h = hsoft[i];
+            if (!(h > 0.0f) || !isfinite(h))
+                atomicOr(bad, 8);
+        }
     }
     // warp-level min / max, then one atomic per block
     __shared__ long long red[2][3][32];
@@ -117,6 +175,12 @@ __global__ void k_prepare(const double *__restrict__ pin, const float *__restric
         }
         atomicMin(&bbox[a], l);
         atomicMax(&bbox[3 + a], h);
+        __threadfence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && atomicAdd(&state->blocks_done, 1u) == gridDim.x - 1) {
+        __threadfence();
+        root_cube(state, periodic, box, s0, s1, s2);
     }
 }
 
@@ -139,54 +203,6 @@ __device__ __forceinline__ uint32_t compact3(uint64_t v) {
     v = (v ^ (v >> 16)) & 0x001f00000000ffffull;
     v = (v ^ (v >> 32)) & 0x1fffffull;
     return (uint32_t)v;
-}
-
-// Device-side bookkeeping of one build (its host copy also receives the node
-// count).
-struct BuildState {
-    long long bbox[6];
-    int bad;
-    unsigned total;  // nodes of the tree
-    double x0[3];
-    double L0;
-    double scale;  // 2^21 / L0
-};
-
-__device__ double pow2_ceil_d(double x) {
-    int e;
-    const double f = frexp(x, &e);
-    return (f == 0.5) ? ldexp(1.0, e - 1) : ldexp(1.0, e);
-}
-
-// Root cube (one thread): periodic [0, box); open boundaries: the smallest
-// power of two L0 >= 1.25 x the largest extent, x0 = lo - shift (L0 - extent)
-// rounded down to the 2^-21 L0 grid.  Round-to-nearest operations only.
-__global__ void k_root(BuildState *__restrict__ st, int periodic, double box, double s0, double s1, double s2) {
-    if (threadIdx.x != 0)
-        return;
-    if (periodic) {
-        st->x0[0] = st->x0[1] = st->x0[2] = 0.0;
-        st->L0 = box;
-    } else {
-        double lo[3], hi[3], ext = 0.0;
-        for (int a = 0; a < 3; a++) {
-            lo[a] = from_ordered_bits(st->bbox[a]);
-            hi[a] = from_ordered_bits(st->bbox[3 + a]);
-            ext = fmax(ext, __dsub_rn(hi[a], lo[a]));
-        }
-        if (!(ext > 0.0))
-            ext = 1.0;
-        const double L0 = pow2_ceil_d(__dmul_rn(1.25, ext));
-        const double unit = ldexp(L0, -kMaxLevel);
-        const double sh[3] = {s0, s1, s2};
-        for (int a = 0; a < 3; a++) {
-            const double slack = __dsub_rn(L0, __dsub_rn(hi[a], lo[a]));
-            const double x0 = __dsub_rn(lo[a], __dmul_rn(sh[a], slack));
-            st->x0[a] = __dmul_rn(floor(__ddiv_rn(x0, unit)), unit);
-        }
-        st->L0 = L0;
-    }
-    st->scale = __ddiv_rn(ldexp(1.0, kMaxLevel), st->L0);
 }
 
 // floor(v) clamped to [0, 2^21 - 1], read off the bits of v (integer
@@ -227,8 +243,7 @@ __global__ void k_keys(const double *__restrict__ pos, int64_t n, const BuildSta
 // the passes over leaves.
 __global__ void k_rank(const uint32_t *__restrict__ perm, int64_t n, const double *__restrict__ pos,
                        const float *__restrict__ mass, const float *__restrict__ hsoft, uint32_t *__restrict__ rank,
-                       double *__restrict__ spos, float *__restrict__ smass, float *__restrict__ psoft,
-                       int *__restrict__ bad) {
+                       double *__restrict__ spos, float *__restrict__ smass, float *__restrict__ psoft) {
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= n)
         return;
@@ -238,12 +253,8 @@ __global__ void k_rank(const uint32_t *__restrict__ perm, int64_t n, const doubl
     spos[3 * s + 1] = pos[3 * j + 1];
     spos[3 * s + 2] = pos[3 * j + 2];
     smass[s] = mass[j];
-    if (hsoft) {  // per-particle softening, in key order
-        const float h = hsoft[j];
-        if (!(h > 0.0f) || !isfinite(h))
-            atomicOr(bad, 8);
-        psoft[s] = h;
-    }
+    if (hsoft)  // per-particle softening, in key order (checked by k_prepare)
+        psoft[s] = hsoft[j];
 }
 
 // Deepest level whose cell holds both keys (kMaxLevel when they are equal).
@@ -595,17 +606,52 @@ int build_tree_device(Ctx *c, System *s, const double *pos_in, const float *mass
         ~Guard() { t.release(st); }
     } guard{tmp, st};
 
-    TPM_CHECK(s->mem.get(&s->pos, 3 * n, st));
-    TPM_CHECK(s->mem.get(&s->mass, n, st));
-    TPM_CHECK(s->mem.get(&s->key, n, st));
-    TPM_CHECK(s->mem.get(&s->perm, n, st));
-    TPM_CHECK(s->mem.get(&s->rank, n, st));
-    TPM_CHECK(s->mem.get(&s->spart, n, st));
-    TPM_CHECK(s->mem.get(&s->err, 1, st));
+    // ---- memory for the particle passes: the system's arrays in one block,
+    // the build's scratch in another (the CUB scratch sized for the key sort
+    // and the node-count scan, whichever is larger)
+    size_t sort_bytes = 0, scan_bytes = 0;
+    TPM_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, sort_bytes, (const uint64_t *)nullptr, (uint64_t *)nullptr,
+                                             (const uint32_t *)nullptr, (uint32_t *)nullptr, (int)n, 0, 3 * kMaxLevel,
+                                             st));
+    TPM_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, scan_bytes, (const uint32_t *)nullptr, (uint32_t *)nullptr,
+                                           (int)(n + 1), st));
+    const size_t cub_bytes = std::max(sort_bytes, scan_bytes);
+    Carve sys_a;
+    sys_a.add(&s->pos, 3 * n);
+    sys_a.add(&s->mass, n);
+    sys_a.add(&s->key, n);
+    sys_a.add(&s->perm, n);
+    sys_a.add(&s->rank, n);
+    sys_a.add(&s->spart, n);
+    sys_a.add(&s->err, 1);
+    if (hsoft_in)
+        sys_a.add(&s->psoft, n);
+    TPM_CHECK(sys_a.commit(s->mem, st));
+    BuildState *dst;
+    uint64_t *key_raw;
+    uint32_t *idx_raw;
+    char *cub_tmp;
+    double *spos;
+    float *smass;
+    int8_t *pre_max, *suf_max;
+    uint8_t *top_level, *leaf_level;
+    uint32_t *cnt, *base;
+    Carve tmp_a;
+    tmp_a.add(&dst, 1);
+    tmp_a.add(&key_raw, n);
+    tmp_a.add(&idx_raw, n);
+    tmp_a.add(&cub_tmp, cub_bytes);
+    tmp_a.add(&spos, 3 * n);
+    tmp_a.add(&smass, n);
+    tmp_a.add(&pre_max, n);
+    tmp_a.add(&suf_max, n);
+    tmp_a.add(&top_level, n);
+    tmp_a.add(&leaf_level, n);
+    tmp_a.add(&cnt, n + 1);
+    tmp_a.add(&base, n + 1);
+    TPM_CHECK(tmp_a.commit(tmp, st));
     TPM_CUDA(cudaMemsetAsync(s->err, 0, sizeof(int), st));
 
-    BuildState *dst;
-    TPM_CHECK(tmp.get(&dst, 1, st));
     // the context's pinned page holds the host copy of the build state; one
     // build at a time per context uses it
     static_assert(sizeof(BuildState) <= kPinnedStateBytes, "build state exceeds the pinned page");
@@ -618,51 +664,20 @@ int build_tree_device(Ctx *c, System *s, const double *pos_in, const float *mass
     }
     TPM_CUDA(cudaMemcpyAsync(dst, hst, sizeof(BuildState), cudaMemcpyHostToDevice, st));
 
-    // ---- prepare, bounding box, root, keys, sort
-    k_prepare<<<blocks_for(n), kThreads, 0, st>>>(pos_in, mass_in, n, s->bp.periodic, s->bp.box, s->bp.shift[0],
-                                                   s->bp.shift[1], s->bp.shift[2], s->pos, s->mass, dst->bbox,
-                                                   &dst->bad);
+    // ---- prepare, bounding box and root (last block), keys, sort
+    k_prepare<<<blocks_for(n), kThreads, 0, st>>>(pos_in, mass_in, hsoft_in, n, s->bp.periodic, s->bp.box,
+                                                   s->bp.shift[0], s->bp.shift[1], s->bp.shift[2], s->pos, s->mass,
+                                                   dst);
     count_launch();
     TPM_CUDA(cudaGetLastError());
-    k_root<<<1, 32, 0, st>>>(dst, s->bp.periodic, s->bp.box, s->bp.shift[0], s->bp.shift[1], s->bp.shift[2]);
-    count_launch();
-    TPM_CUDA(cudaGetLastError());
-    uint64_t *key_raw;
-    uint32_t *idx_raw;
-    TPM_CHECK(tmp.get(&key_raw, n, st));
-    TPM_CHECK(tmp.get(&idx_raw, n, st));
     k_keys<<<blocks_for(n), kThreads, 0, st>>>(s->pos, n, dst, key_raw, idx_raw);
     count_launch();
     TPM_CUDA(cudaGetLastError());
-    size_t sort_bytes = 0;
-    TPM_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, sort_bytes, key_raw, s->key, idx_raw, s->perm, (int)n, 0,
-                                             3 * kMaxLevel, st));
-    void *cub_tmp;
-    TPM_CHECK(tmp.get((char **)&cub_tmp, sort_bytes, st));
     TPM_CUDA(cub::DeviceRadixSort::SortPairs(cub_tmp, sort_bytes, key_raw, s->key, idx_raw, s->perm, (int)n, 0,
                                              3 * kMaxLevel, st));
     count_cub_call();
-    double *spos;
-    float *smass;
-    TPM_CHECK(tmp.get(&spos, 3 * n, st));
-    TPM_CHECK(tmp.get(&smass, n, st));
-    if (hsoft_in)
-        TPM_CHECK(s->mem.get(&s->psoft, n, st));
-    k_rank<<<blocks_for(n), kThreads, 0, st>>>(s->perm, n, s->pos, s->mass, hsoft_in, s->rank, spos, smass, s->psoft,
-                                               &dst->bad);
-    count_launch();
-    TPM_CUDA(cudaGetLastError());
 
     // ---- node counts per particle and their scan: the pre-order indices
-    int8_t *pre_max, *suf_max;
-    uint8_t *top_level, *leaf_level;
-    uint32_t *cnt, *base;
-    TPM_CHECK(tmp.get(&pre_max, n, st));
-    TPM_CHECK(tmp.get(&suf_max, n, st));
-    TPM_CHECK(tmp.get(&top_level, n, st));
-    TPM_CHECK(tmp.get(&leaf_level, n, st));
-    TPM_CHECK(tmp.get(&cnt, n + 1, st));
-    TPM_CHECK(tmp.get(&base, n + 1, st));
     k_window_max<<<blocks_for((n + B) / ((int64_t)B + 1)), kThreads, 0, st>>>(s->key, n, B, pre_max, suf_max);
     count_launch();
     TPM_CUDA(cudaGetLastError());
@@ -670,16 +685,16 @@ int build_tree_device(Ctx *c, System *s, const double *pos_in, const float *mass
     k_node_counts<<<blocks_for(n), kThreads, 0, st>>>(s->key, n, B, pre_max, suf_max, top_level, leaf_level, cnt);
     count_launch();
     TPM_CUDA(cudaGetLastError());
-    size_t scan_bytes = 0;
-    TPM_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, scan_bytes, cnt, base, (int)(n + 1), st));
-    void *scan_tmp = cub_tmp;
-    if (scan_bytes > sort_bytes)
-        TPM_CHECK(tmp.get((char **)&scan_tmp, scan_bytes, st));
-    TPM_CUDA(cub::DeviceScan::ExclusiveSum(scan_tmp, scan_bytes, cnt, base, (int)(n + 1), st));
+    TPM_CUDA(cub::DeviceScan::ExclusiveSum(cub_tmp, scan_bytes, cnt, base, (int)(n + 1), st));
     count_cub_call();
     TPM_CUDA(cudaMemcpyAsync(hst, dst, sizeof(BuildState), cudaMemcpyDeviceToHost, st));
     TPM_CUDA(cudaMemcpyAsync(&hst->total, base + n, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-    TPM_CUDA(cudaStreamSynchronize(st));
+    TPM_CUDA(cudaEventRecord(c->ev_state, st));
+    // the particles gathered into key order while the host reads the state
+    k_rank<<<blocks_for(n), kThreads, 0, st>>>(s->perm, n, s->pos, s->mass, hsoft_in, s->rank, spos, smass, s->psoft);
+    count_launch();
+    TPM_CUDA(cudaGetLastError());
+    TPM_CUDA(cudaEventSynchronize(c->ev_state));
     if (hst->bad & 1) {
         set_error("non-finite position");
         return TPM_ENAN;
@@ -705,40 +720,63 @@ int build_tree_device(Ctx *c, System *s, const double *pos_in, const float *mass
     const int64_t nn = hst->total;
     s->nnodes = nn;
 
-    // ---- nodes in pre-order
+    // ---- memory for the node passes: scratch in one block, the system's
+    // node tables in another
     NodeArrays t{};
-    TPM_CHECK(tmp.get(&t.first, nn, st));
-    TPM_CHECK(tmp.get(&t.count, nn, st));
-    TPM_CHECK(tmp.get(&t.skip, nn, st));
-    TPM_CHECK(tmp.get(&t.parent, nn, st));
-    TPM_CHECK(tmp.get(&t.nchild, nn, st));
-    TPM_CHECK(tmp.get(&t.arrive, nn, st));
-    TPM_CHECK(tmp.get(&t.order, nn, st));
-    TPM_CHECK(tmp.get(&t.level, nn, st));
-    TPM_CHECK(tmp.get(&t.prefix, nn, st));
-    // FP64 sums by breadth-first index, kept with the system for export
-    TPM_CHECK(s->mem.get(&s->msum, nn, st));
-    TPM_CHECK(s->mem.get(&s->ssum, 3 * nn, st));
+    uint8_t *level_sorted;
+    uint32_t *bfs2pre;
+    float *hmx = nullptr, *hmn = nullptr;
+    size_t lsort_bytes = 0;
+    TPM_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, lsort_bytes, (const uint8_t *)nullptr, (uint8_t *)nullptr,
+                                             (const uint32_t *)nullptr, (uint32_t *)nullptr, (int)nn, 0, 5, st));
+    char *lsort_tmp = cub_tmp;
+    Carve tmp_b;
+    // nchild and arrive adjacent: one memset clears both
+    tmp_b.add(&t.nchild, nn);
+    tmp_b.add(&t.arrive, nn);
+    tmp_b.add(&t.first, nn);
+    tmp_b.add(&t.count, nn);
+    tmp_b.add(&t.skip, nn);
+    tmp_b.add(&t.parent, nn);
+    tmp_b.add(&t.order, nn);
+    tmp_b.add(&t.level, nn);
+    tmp_b.add(&t.prefix, nn);
+    tmp_b.add(&level_sorted, nn);
+    tmp_b.add(&bfs2pre, nn);
+    if (lsort_bytes > cub_bytes)
+        tmp_b.add(&lsort_tmp, lsort_bytes);
+    if (s->psoft) {
+        tmp_b.add(&hmx, nn);
+        tmp_b.add(&hmn, nn);
+    }
+    TPM_CHECK(tmp_b.commit(tmp, st));
+    Carve sys_b;
+    sys_b.add(&s->msum, nn);  // FP64 sums by breadth-first index, kept with the system for export
+    sys_b.add(&s->ssum, 3 * nn);
+    sys_b.add(&s->pre2bfs, nn);
+    sys_b.add(&s->ncen, nn);
+    sys_b.add(&s->ncom, nn);
+    sys_b.add(&s->nlink, nn);
+    sys_b.add(&s->nlevel, nn);
+    sys_b.add(&s->nprefix, nn);
+    sys_b.add(&s->bcen, nn);
+    sys_b.add(&s->bcom, nn);
+    sys_b.add(&s->blink, nn);
+    if (s->psoft) {
+        sys_b.add(&s->nsoft, nn);
+        sys_b.add(&s->bsoft, nn);
+    }
+    TPM_CHECK(sys_b.commit(s->mem, st));
     double *M = s->msum, *S = s->ssum;
-    TPM_CUDA(cudaMemsetAsync(t.nchild, 0, nn * sizeof(uint32_t), st));
-    TPM_CUDA(cudaMemsetAsync(t.arrive, 0, nn * sizeof(uint32_t), st));
+    uint32_t *pre2bfs = s->pre2bfs;
+
+    // ---- nodes in pre-order
+    TPM_CUDA(cudaMemsetAsync(t.nchild, 0, (size_t)((char *)t.arrive - (char *)t.nchild) + nn * sizeof(uint32_t), st));
     k_nodes<<<blocks_for(n), kThreads, 0, st>>>(s->key, n, base, top_level, leaf_level, t);
     count_launch();
     TPM_CUDA(cudaGetLastError());
 
     // ---- breadth-first order: a stable sort of the pre-order by level
-    uint8_t *level_sorted;
-    uint32_t *bfs2pre;
-    TPM_CHECK(tmp.get(&level_sorted, nn, st));
-    TPM_CHECK(tmp.get(&bfs2pre, nn, st));
-    TPM_CHECK(s->mem.get(&s->pre2bfs, nn, st));
-    uint32_t *pre2bfs = s->pre2bfs;
-    size_t lsort_bytes = 0;
-    TPM_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, lsort_bytes, t.level, level_sorted, t.order, bfs2pre, (int)nn,
-                                             0, 5, st));
-    void *lsort_tmp = cub_tmp;
-    if (lsort_bytes > sort_bytes)
-        TPM_CHECK(tmp.get((char **)&lsort_tmp, lsort_bytes, st));
     TPM_CUDA(cub::DeviceRadixSort::SortPairs(lsort_tmp, lsort_bytes, t.level, level_sorted, t.order, bfs2pre,
                                              (int)nn, 0, 5, st));
     count_cub_call();
@@ -749,21 +787,6 @@ int build_tree_device(Ctx *c, System *s, const double *pos_in, const float *mass
     // ---- walk tables and monopoles.  The tables that need no monopole go on
     // the context's side stream while the monopole pass climbs (its last
     // levels leave most SMs idle); the centres of mass follow both.
-    float *hmx = nullptr, *hmn = nullptr;
-    if (s->psoft) {
-        TPM_CHECK(tmp.get(&hmx, nn, st));
-        TPM_CHECK(tmp.get(&hmn, nn, st));
-        TPM_CHECK(s->mem.get(&s->nsoft, nn, st));
-        TPM_CHECK(s->mem.get(&s->bsoft, nn, st));
-    }
-    TPM_CHECK(s->mem.get(&s->ncen, nn, st));
-    TPM_CHECK(s->mem.get(&s->ncom, nn, st));
-    TPM_CHECK(s->mem.get(&s->nlink, nn, st));
-    TPM_CHECK(s->mem.get(&s->nlevel, nn, st));
-    TPM_CHECK(s->mem.get(&s->nprefix, nn, st));
-    TPM_CHECK(s->mem.get(&s->bcen, nn, st));
-    TPM_CHECK(s->mem.get(&s->bcom, nn, st));
-    TPM_CHECK(s->mem.get(&s->blink, nn, st));
     NodeOut o{s->ncen, s->ncom,  s->nlink, s->nlevel, s->nprefix, s->bcen,
               s->bcom, s->blink, s->spart, s->nsoft,  s->bsoft};
     TPM_CUDA(cudaEventRecord(c->ev_fork, st));

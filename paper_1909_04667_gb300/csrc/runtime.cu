@@ -281,9 +281,13 @@ int tpm_create(tpm_ctx **out, int device, size_t budget) {
         e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess)
         e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess)
+        e = cudaEventCreateWithFlags(&c->ev_state, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         if (c->ev_fork)
             cudaEventDestroy(c->ev_fork);
+        if (c->ev_join)
+            cudaEventDestroy(c->ev_join);
         if (c->side)
             cudaStreamDestroy(c->side);
         if (c->pinned_state)
@@ -323,6 +327,7 @@ int tpm_destroy(tpm_ctx *h) {
     cudaFreeHost(c->pinned_state);
     cudaEventDestroy(c->ev_fork);
     cudaEventDestroy(c->ev_join);
+    cudaEventDestroy(c->ev_state);
     cudaStreamDestroy(c->side);
     delete c;
     return TPM_OK;

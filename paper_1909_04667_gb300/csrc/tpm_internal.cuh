@@ -88,6 +88,39 @@ struct AllocSet {
     }
 };
 
+// Several arrays carved from one allocation of an AllocSet (one pool call
+// instead of one per array; each array starts on a 256-byte boundary).
+struct Carve {
+    struct Item {
+        void *p;
+        void (*set)(void *, char *);
+        size_t off;
+    };
+    std::vector<Item> items;
+    size_t total = 0;
+    template <class T>
+    static void set_ptr(void *pp, char *v) {
+        *static_cast<T **>(pp) = reinterpret_cast<T *>(v);
+    }
+    template <class T>
+    void add(T **p, size_t count) {
+        size_t b = count * sizeof(T);
+        if (b == 0)
+            b = 16;
+        items.push_back({static_cast<void *>(p), &set_ptr<T>, total});
+        total += (b + 255) & ~size_t(255);
+    }
+    int commit(AllocSet &set, cudaStream_t st) {
+        char *base = nullptr;
+        const int rc = set.get(&base, total, st);
+        if (rc != TPM_OK)
+            return rc;
+        for (auto &it : items)
+            it.set(it.p, base + it.off);
+        return TPM_OK;
+    }
+};
+
 // ------------------------------------------------------------------ system
 struct System {
     uint64_t id = 0;
@@ -160,6 +193,7 @@ struct Ctx {
     // its fork / join events; used under build_mu
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_state = nullptr;  // a build's state has reached the pinned page
     int num_sms = 0;
     size_t budget = 0;
     size_t used = 0;
