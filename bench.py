@@ -64,7 +64,7 @@ HERNQUIST = dict(n=1 << 20, seed=W.CONFIG_SEEDS[2], h=0.005, G=1.0, bucket=8, th
 PLUMMER = dict(n=8192, h=0.01, G=1.0, bucket=8, theta=0.7)
 SERVING = dict(seed=W.CONFIG_SEEDS[5], budget_gb=60, n_requests=10000, warmup_requests=4000, rate=200.0,
                load_factors=(1, 8), nmin=1 << 12, nmax=1 << 20, overcommit=1.5, bytes_per_particle=118,
-               round_ids=1 << 21, accuracy_every=1000, accuracy_targets=1024)
+               round_ids=1 << 21, accuracy_every=1000, accuracy_targets=1024, aold_cache_gb=2)
 TIMEBINS = dict(nbins=8, seed=W.CONFIG_SEEDS[4], req_lo=64, req_hi=65536)
 HIERARCHY = dict(nbins=8, dt_tick=0.005, c_grav=0.025)
 ISOLATED = dict(pm_n=64, asmth=2.5, rcut=4.5)
@@ -609,7 +609,7 @@ def run_serving(tpm, torch, dev):
     res = {}
     ctx = tpm.Context(dev.index, budget_bytes=budget)
     srv = ForceServer(ctx, source, max_round_ids=cfg["round_ids"], max_round_requests=512, policy="adaptive",
-                      keep_results=sampled)
+                      keep_results=sampled, aold_cache_bytes=cfg["aold_cache_gb"] << 30)
     srv.serve(make(True), realtime=False)
     for f in cfg["load_factors"]:
         b0, e0 = srv.builds, srv.evictions
@@ -651,7 +651,8 @@ def run_serving(tpm, torch, dev):
     res.update(workload="serving_%d_systems_N2^12-2^20_poisson%dHz_%d_requests_after_%d_budget%dGB" % (
         len(cat), int(cfg["rate"]), cfg["n_requests"], nw, cfg["budget_gb"]), hbm_budget_bytes=budget,
         catalogue_bytes=footprint,
-        arms={"continuous_batching": "server: mixed precision, up to two batched rounds in flight",
+        arms={"continuous_batching": "server: mixed precision, batched rounds, builds overlapping the walks, |a| "
+                                     "of evicted systems kept in pinned host memory for the relative criterion",
               "per_request": "one build (if needed), one compute_forces call and one synchronisation per "
                              "request, mixed precision",
               "per_request_plain_fp32": "the same with the plain FP32 form (absolute FP32 coordinates)"},

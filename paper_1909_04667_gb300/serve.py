@@ -3,13 +3,14 @@
 A request asks for the forces on a subset of one system's particles.  The
 server keeps the trees of recently used systems resident on the GPU under the
 context's HBM budget and serves requests in rounds: requests that arrive while
-rounds are on the GPU are admitted as round slots, plan capacity and memory
-free up (up to two rounds in flight, on their own streams, so that a request
-need not wait for a long round to finish), their missing trees are built on a
-separate stream -- overlapping the walks in flight -- and each round runs as
-one batched walk launch (``tpm_compute_forces_batch``).
-When memory runs short, resident systems that no request in flight needs are
-evicted, least recently used first.
+a round is on the GPU are admitted as plan capacity and memory free up (one
+round in flight by default, optionally two on their own streams), their
+missing trees are built on a separate stream -- overlapping the walk in
+flight -- and each round runs as one batched walk launch
+(``tpm_compute_forces_batch``).  When memory runs short, resident systems
+that no waiting or running request needs are evicted, least recently used
+first; their |a| stays on the host for the relative criterion after a
+rebuild.
 
 The first request for a system uses the geometric criterion; later requests
 use the relative criterion (paper Sec. 3.1) when every requested particle has
@@ -44,6 +45,7 @@ class ServeRequest:
     pot: np.ndarray = None
     n_int: np.ndarray = None
     criterion: int = -1
+    t_start: float = float("nan")  # when its walk was enqueued (the build, if any, came before)
     t_done: float = float("nan")
 
     @property
@@ -116,23 +118,29 @@ class ForceServer:
     taken as they are).
 
     Up to ``slots`` rounds are in flight at once, each on its own stream with
-    its own plan and buffers, so that requests arriving while a long round
-    walks start at once and share the GPU with it; a system is in at most one
-    round in flight, with at most one request (its |a| bookkeeping is ordered
-    on that round's stream, and a later request on it can use the relative
-    criterion with this round's |a|).
+    its own plan and buffers (with two, a request arriving while a long round
+    walks starts at once and shares the GPU with it; on the serving workload
+    one slot measured better: concurrent rounds stretch the large rounds that
+    set the tail); a system is in at most one round in flight, with at most
+    one request (its |a| bookkeeping is ordered on that round's stream, and a
+    later request on it can use the relative criterion with this round's |a|).
     A round takes the waiting requests whose trees are ready first (in arrival
     order); requests whose trees are still building wait for a later round
     rather than hold ready ones back.  A tree that a queued request needs is
     not evicted before that request has been served (trees built ahead for
     waiting requests would otherwise be evicted by the next build ahead).
+    With ``keep_aold`` an evicted system's |a| (and which particles have one)
+    is kept in a pinned host ring of ``aold_cache_bytes`` (the oldest entries
+    are forgotten as it wraps) and restored when its tree is rebuilt: the
+    rebuilt tree is the same tree, so the relative criterion stays available.
     ``keep_results`` is a bool or a
     predicate on the request: results of the others are timed back to the
     host and dropped."""
 
     def __init__(self, ctx: Context, source, max_round_ids: int = 1 << 21, max_round_requests: int = 512,
                  theta: float = 0.5, alpha: float = 0.0025, policy: str = "adaptive", group_size: int = None,
-                 keep_results=True, slots: int = 2, prioritise_large: bool = True):
+                 keep_results=True, slots: int = 1, prioritise_large: bool = True, keep_aold: bool = True,
+                 aold_cache_bytes: int = 256 << 20):
         import torch
 
         self.torch = torch
@@ -156,6 +164,17 @@ class ForceServer:
         self.keep_results = keep_results
         self._wanted = collections.Counter()  # queued requests per system: not evictable
         self._busy = set()  # systems in a round in flight
+        self._t0 = time.perf_counter()  # start of the current serve() call
+        # |a| of evicted systems (pinned host copies): a rebuilt tree is the
+        # same tree (the build is deterministic), so its particles' |a| stay
+        # valid for the relative criterion
+        self.keep_aold = bool(keep_aold)
+        self._aold_host = collections.OrderedDict()  # sid -> (offset, n, valid mask, n_valid), oldest first
+        # pinned float32 ring, allocated here: a pinned allocation of this size
+        # takes tens of milliseconds and must not fall inside a request
+        self._ring_cap = max(int(aold_cache_bytes) // 4, 1 << 20)
+        self._ring = torch.empty(self._ring_cap, dtype=torch.float32).pin_memory() if self.keep_aold else None
+        self._ring_head = 0
         # a build was refused for memory: no other is tried (and no system drawn
         # for it) until a round completes and systems become evictable again
         self._blocked = False
@@ -164,6 +183,7 @@ class ForceServer:
         for r in self.resident.values():
             r.system.release()
         self.resident.clear()
+        self._aold_host.clear()
         for sl in self.slots:
             sl.plan.close()
 
@@ -174,11 +194,36 @@ class ForceServer:
     def _evict_one(self) -> bool:
         for sid, r in self.resident.items():  # least recently used first
             if r.inflight == 0 and r.ready() and not self._wanted[sid]:
+                if self.keep_aold and r.n_valid:
+                    self._save_aold(sid, r)
                 r.system.release()
                 del self.resident[sid]
                 self.evictions += 1
                 return True
         return False
+
+    def _save_aold(self, sid, r):
+        """Copies the system's |a| into the pinned ring on the build stream
+        (its last round's bookkeeping has completed: the system is not in
+        flight).  Saved entries the copy overwrites (the oldest) are
+        forgotten.  Saves and uploads all run on the build stream, in order,
+        and the device copy was allocated on it, so none needs an event."""
+        torch = self.torch
+        n = int(r.aold.shape[0])
+        if n > self._ring_cap:
+            return
+        off = self._ring_head
+        if off + n > self._ring_cap:
+            off = 0
+        while self._aold_host:  # entries overlapping [off, off + n) are the oldest ones
+            old_sid, (o, m, _, _) = next(iter(self._aold_host.items()))
+            if o + m <= off or o >= off + n:
+                break
+            del self._aold_host[old_sid]
+        with torch.cuda.stream(self.build_stream):
+            self._ring[off:off + n].copy_(r.aold, non_blocking=True)
+        self._ring_head = off + n
+        self._aold_host[sid] = (off, n, r.aold_valid, r.n_valid)
 
     def ensure_resident(self, sid: int) -> bool:
         """Enqueues the build of ``sid`` on the build stream if it is not
@@ -204,11 +249,20 @@ class ForceServer:
                         return False
                     raise
         n = system.n
+        saved = self._aold_host.pop(sid, None)
         with torch.cuda.stream(self.build_stream):
-            aold = torch.zeros(n, dtype=torch.float32, device=self.dev)
+            aold = torch.empty(n, dtype=torch.float32, device=self.dev)
+            if saved is not None:  # the copy to the host came earlier on this stream
+                aold.copy_(self._ring[saved[0]:saved[0] + n], non_blocking=True)
+            else:
+                aold.zero_()
             ev = torch.cuda.Event()
             ev.record(self.build_stream)
-        self.resident[sid] = _Resident(system, aold, np.zeros(n, dtype=bool), built=ev)
+        if saved is not None:
+            res = _Resident(system, aold, saved[2], built=ev, n_valid=saved[3])
+        else:
+            res = _Resident(system, aold, np.zeros(n, dtype=bool), built=ev)
+        self.resident[sid] = res
         self.builds += 1
         return True
 
@@ -228,6 +282,9 @@ class ForceServer:
         torch = self.torch
         st = slot.stream
         slot.busy = True
+        now = time.perf_counter() - self._t0
+        for r in reqs:
+            r.t_start = now
         for r in reqs:  # the round waits for its own systems' builds only
             self.resident.move_to_end(r.sid)  # most recently used
             b = self.resident[r.sid].built
@@ -379,7 +436,7 @@ class ForceServer:
         queue = collections.deque()
         inflight = []
         i = 0
-        t0 = time.perf_counter()
+        t0 = self._t0 = time.perf_counter()
         while i < len(reqs) or queue or inflight:
             now = time.perf_counter() - t0
             while i < len(reqs) and (not realtime or reqs[i].arrival <= now):
@@ -460,6 +517,7 @@ def serve_per_request(ctx: Context, source, requests, theta: float = 0.5, alpha:
         else:
             fp = ForceParams(crit=CRIT_RELATIVE, alpha=alpha, plain_fp32=plain_fp32)
         r.criterion = fp.crit
+        r.t_start = time.perf_counter() - t0
         while True:
             try:
                 acc, pot, nint = system.compute_forces(active_ids=ids_d, a_old=aold[part].contiguous(), fp=fp)

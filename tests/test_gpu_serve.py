@@ -91,7 +91,7 @@ def test_budget_evictions_keep_results(setup):
     # resident tree holds that tree's build (its scratch nearly doubles it) but
     # not the five smaller trees (together ~0.9 of it) next to the build
     probe = tpm.Context(0)
-    plans = [probe.create_plan(1 << 16, 8) for _ in range(2)]  # the server's two round slots
+    plans = [probe.create_plan(1 << 16, 8)]  # the server's round slot
     plan_bytes = probe.memory()[0]
     tree = probe.build_tree(*source(order[-1]))
     tree_bytes = probe.memory()[0] - plan_bytes
@@ -133,4 +133,40 @@ def test_rounds_in_flight_together_give_the_same_results(setup):
         np.testing.assert_array_equal(r.n_int, out[1][rid].n_int)
         e = rel(r.acc.astype(np.float64), out[1][rid].acc.astype(np.float64))
         assert e.max() < 1e-5
+    ctx.close()
+
+
+def test_evicted_system_keeps_its_a_old(setup):
+    """An evicted system's |a| comes back with its rebuilt tree: the next
+    request on it uses the relative criterion and gets the forces of a plain
+    call with that |a| (the same tree, the same walk)."""
+    tpm, torch, cat, source, _ = setup
+    from paper_1909_04667_gb300.serve import ForceServer, ServeRequest
+
+    sid = max(range(len(cat)), key=lambda i: cat[i].n)
+    n = cat[sid].n
+    ids = np.arange(n, dtype=np.int32)
+    ctx = tpm.Context(0)
+    srv = ForceServer(ctx, source, max_round_ids=1 << 18, max_round_requests=8)
+    first = srv.serve([ServeRequest(0, sid, ids.copy())], realtime=False)[0]
+    assert first.criterion == tpm.CRIT_BH
+    assert srv._evict_one() and sid not in srv.resident
+    again = srv.serve([ServeRequest(1, sid, ids.copy())], realtime=False)[0]
+    assert again.criterion == tpm.CRIT_RELATIVE
+    srv.close()
+    dev = torch.device("cuda", 0)
+    a_old = torch.linalg.vector_norm(torch.from_numpy(first.acc).to(dev), dim=1).contiguous()
+    pos, mass, bp = source(sid)
+    s = ctx.build_tree(pos, mass, bp)
+    a, p, k = s.compute_forces(active_ids=torch.from_numpy(ids).to(dev), a_old=a_old,
+                               fp=tpm.ForceParams(crit=tpm.CRIT_RELATIVE, alpha=0.0025))
+    np.testing.assert_array_equal(again.acc, a.cpu().numpy())
+    np.testing.assert_array_equal(again.n_int, k.cpu().numpy())
+    s.release()
+    # without the option the rebuilt system starts over with the geometric criterion
+    srv = ForceServer(ctx, source, max_round_ids=1 << 18, max_round_requests=8, keep_aold=False)
+    srv.serve([ServeRequest(2, sid, ids.copy())], realtime=False)
+    assert srv._evict_one()
+    assert srv.serve([ServeRequest(3, sid, ids.copy())], realtime=False)[0].criterion == tpm.CRIT_BH
+    srv.close()
     ctx.close()
