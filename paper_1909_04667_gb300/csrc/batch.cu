@@ -56,32 +56,41 @@ struct Plan {
     bool staged_pending = false;
 };
 
-// Per request (one block each): the sorted position of every requested id in
-// its own tree; either directly the walk's sorted index (requests given in key
-// order) or a (request, sorted position) sort key with the id's slot.  An id
-// out of range sets bit 0 of the status word and is read as particle 0.
-__global__ void k_batch_keys(const KeyReq *__restrict__ kr, const int64_t *__restrict__ off,
-                             const uint32_t *__restrict__ ids, int presorted, uint64_t *__restrict__ keys,
-                             uint32_t *__restrict__ vals, uint32_t *__restrict__ sidx, uint32_t *__restrict__ slot,
-                             int *__restrict__ err) {
-    const int64_t r = blockIdx.x;
-    const int64_t lo = off[r], hi = off[r + 1];
-    const uint32_t *rank = kr[r].rank;
-    const int64_t n = kr[r].n;
-    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        uint32_t id = ids[i];
-        if (id >= (uint64_t)n) {
-            atomicOr(err, 1);
-            id = 0;
-        }
-        const uint32_t rk = rank[id];
-        if (presorted) {
-            sidx[i] = rk;
-            slot[i] = (uint32_t)i;
-        } else {
-            keys[i] = ((uint64_t)r << 32) | rk;
-            vals[i] = (uint32_t)i;
-        }
+// Per requested id (one thread each, over all requests: one block per
+// request left a large request to a single block): the sorted position of the
+// id in its own tree; either directly the walk's sorted index (requests given
+// in key order) or a (request, sorted position) sort key with the id's slot.
+// The request of position i is the last r with off[r] <= i (empty requests
+// share their offset with the next one).  An id out of range sets bit 0 of
+// the status word and is read as particle 0.
+__global__ void k_batch_keys(const KeyReq *__restrict__ kr, const int64_t *__restrict__ off, int64_t n_req,
+                             int64_t n_ids, const uint32_t *__restrict__ ids, int presorted,
+                             uint64_t *__restrict__ keys, uint32_t *__restrict__ vals, uint32_t *__restrict__ sidx,
+                             uint32_t *__restrict__ slot, int *__restrict__ err) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_ids)
+        return;
+    int64_t lo = 0, hi = n_req - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= i)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const int64_t r = lo;
+    uint32_t id = ids[i];
+    if (id >= (uint64_t)kr[r].n) {
+        atomicOr(err, 1);
+        id = 0;
+    }
+    const uint32_t rk = kr[r].rank[id];
+    if (presorted) {
+        sidx[i] = rk;
+        slot[i] = (uint32_t)i;
+    } else {
+        keys[i] = ((uint64_t)r << 32) | rk;
+        vals[i] = (uint32_t)i;
     }
 }
 
@@ -227,8 +236,9 @@ int run_batch(Ctx *c, Plan *pl, int64_t n_req, const tpm_sys *systems, const int
         pl->staged_pending = true;
     }
     const bool presorted = flags & TPM_BATCH_PRESORTED;
-    k_batch_keys<<<(unsigned)n_req, 256, 0, st>>>(pl->kreq_dev, pl->off_dev, ids, presorted ? 1 : 0, pl->keys,
-                                                  pl->vals, pl->sidx, pl->slot, pl->err);
+    k_batch_keys<<<(unsigned)((n_ids + 255) / 256), 256, 0, st>>>(pl->kreq_dev, pl->off_dev, n_req, n_ids, ids,
+                                                                  presorted ? 1 : 0, pl->keys, pl->vals, pl->sidx,
+                                                                  pl->slot, pl->err);
     count_launch();
     TPM_CUDA(cudaGetLastError());
     if (!presorted) {
