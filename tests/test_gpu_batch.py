@@ -108,6 +108,35 @@ def test_batch_matches_per_request_calls(env, group):
     plan.close()
 
 
+def test_batch_with_empty_and_large_requests(env):
+    """Empty requests between others, and one request spanning many key
+    blocks (all 60000 particles of a tree): every id finds its own request,
+    and each request gets what a plain call gives it (bit for bit at the
+    plan's default group size and depth)."""
+    tpm, torch, dev, ctx, reqs, aold = env
+    s1, s2 = reqs[0][0], reqs[1][0]
+    rng = np.random.default_rng(12)
+    empty = np.zeros(0, np.int32)
+    fp_rel = tpm.ForceParams(crit=tpm.CRIT_RELATIVE, alpha=0.002)
+    mixed = [(s1, empty, fp_rel), (s2, rng.permutation(s2.n).astype(np.int32), fp_rel), (s1, empty, fp_rel),
+             (s1, empty, fp_rel), (s1, rng.choice(s1.n, 700, replace=False).astype(np.int32), fp_rel),
+             (s2, empty, fp_rel)]
+    ids, off, a_old = batch_inputs(torch, dev, mixed, aold)
+    plan = ctx.create_plan(int(off[-1]), 8)
+    acc = torch.empty((len(ids), 3), device=dev)
+    pot = torch.empty(len(ids), device=dev)
+    nint = torch.empty(len(ids), dtype=torch.int32, device=dev)
+    plan.compute_forces_batch([r[0] for r in mixed], off, [r[2] for r in mixed], ids, acc, a_old=a_old, pot=pot,
+                              n_int=nint)
+    plan.sync_status()
+    acc, nint = acc.cpu().numpy(), nint.cpu().numpy()
+    for r, (a, p, n) in enumerate(reference(tpm, torch, dev, mixed, aold)):
+        sl = slice(off[r], off[r + 1])
+        np.testing.assert_array_equal(acc[sl], a)
+        np.testing.assert_array_equal(nint[sl], n)
+    plan.close()
+
+
 def test_batch_presorted_and_graph_replay(env):
     tpm, torch, dev, ctx, reqs, aold = env
     # ids in each tree's key order: the presorted flag skips the sort
