@@ -209,6 +209,7 @@ int tpm_pm_long_range(tpm_ctx *ctx, tpm_sys s, const tpm_force_params *p, void *
  * centres in FP64.
  *   active_ids  n_active indices into the particle order given at build time,
  *               or NULL for all particles in that order (n_active must be n).
+ *               n_active = 0 returns TPM_OK at once (the arrays may be NULL).
  *   a_old       n_active |a| from the previous evaluation (relative criterion),
  *               or NULL (only with TPM_CRIT_BH).
  *   acc         out: n_active x 3 accelerations, in active_ids order.

@@ -496,6 +496,8 @@ int tpm_compute_forces(tpm_ctx *h, tpm_sys sid, const uint32_t *active_ids, int6
         set_error("n_active must lie in [0, n]");
         return TPM_EINVAL;
     }
+    if (n_active == 0)  // an empty active set: nothing to compute (its arrays may be null)
+        return TPM_OK;
     if (!active_ids && n_active != s->n) {
         set_error("active_ids = NULL means all particles: n_active must equal n");
         return TPM_EINVAL;
@@ -512,8 +514,6 @@ int tpm_compute_forces(tpm_ctx *h, tpm_sys sid, const uint32_t *active_ids, int6
             return TPM_EINVAL;
         }
     }
-    if (n_active == 0)
-        return TPM_OK;
     TPM_CUDA(cudaSetDevice(c->device));
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
 

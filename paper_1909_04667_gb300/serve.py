@@ -89,6 +89,40 @@ class _Round:
     slot: object = None
 
 
+class _RingIndex:
+    """Placement of saved entries in a ring of ``cap`` elements (host logic
+    only; the server keeps the data in a pinned buffer): entries go one after
+    another, wrapping to the start when one does not fit at the end, and the
+    entries a new one overlaps are forgotten (they are older: an entry from
+    two laps back can survive past the end of the last lap, so these are not
+    always the oldest ones)."""
+
+    def __init__(self, cap: int):
+        self.cap = int(cap)
+        self.head = 0
+        self.entries = collections.OrderedDict()  # key -> (offset, n, payload), oldest first
+
+    def place(self, key, n: int, payload=None):
+        """Offset of a new entry of ``n`` elements, or None if it cannot fit."""
+        n = int(n)
+        if n > self.cap:
+            return None
+        self.entries.pop(key, None)
+        off = self.head if self.head + n <= self.cap else 0
+        for old in [k for k, (o, m, _) in self.entries.items() if o < off + n and off < o + m]:
+            del self.entries[old]
+        self.head = off + n
+        self.entries[key] = (off, n, payload)
+        return off
+
+    def take(self, key):
+        """(offset, n, payload) of the entry, removed, or None."""
+        return self.entries.pop(key, None)
+
+    def clear(self):
+        self.entries.clear()
+
+
 class _Slot:
     """What one round in flight needs: a stream, a plan (batched calls on one
     plan must not overlap), device buffers and pinned staging."""
@@ -169,12 +203,10 @@ class ForceServer:
         # same tree (the build is deterministic), so its particles' |a| stay
         # valid for the relative criterion
         self.keep_aold = bool(keep_aold)
-        self._aold_host = collections.OrderedDict()  # sid -> (offset, n, valid mask, n_valid), oldest first
         # pinned float32 ring, allocated here: a pinned allocation of this size
         # takes tens of milliseconds and must not fall inside a request
-        self._ring_cap = max(int(aold_cache_bytes) // 4, 1 << 20)
-        self._ring = torch.empty(self._ring_cap, dtype=torch.float32).pin_memory() if self.keep_aold else None
-        self._ring_head = 0
+        self._ring_index = _RingIndex(max(int(aold_cache_bytes) // 4, 1 << 20))  # payload: (valid mask, n_valid)
+        self._ring = torch.empty(self._ring_index.cap, dtype=torch.float32).pin_memory() if self.keep_aold else None
         # a build was refused for memory: no other is tried (and no system drawn
         # for it) until a round completes and systems become evictable again
         self._blocked = False
@@ -183,7 +215,7 @@ class ForceServer:
         for r in self.resident.values():
             r.system.release()
         self.resident.clear()
-        self._aold_host.clear()
+        self._ring_index.clear()
         for sl in self.slots:
             sl.plan.close()
 
@@ -210,20 +242,11 @@ class ForceServer:
         and the device copy was allocated on it, so none needs an event."""
         torch = self.torch
         n = int(r.aold.shape[0])
-        if n > self._ring_cap:
+        off = self._ring_index.place(sid, n, (r.aold_valid, r.n_valid))
+        if off is None:
             return
-        off = self._ring_head
-        if off + n > self._ring_cap:
-            off = 0
-        while self._aold_host:  # entries overlapping [off, off + n) are the oldest ones
-            old_sid, (o, m, _, _) = next(iter(self._aold_host.items()))
-            if o + m <= off or o >= off + n:
-                break
-            del self._aold_host[old_sid]
         with torch.cuda.stream(self.build_stream):
             self._ring[off:off + n].copy_(r.aold, non_blocking=True)
-        self._ring_head = off + n
-        self._aold_host[sid] = (off, n, r.aold_valid, r.n_valid)
 
     def ensure_resident(self, sid: int) -> bool:
         """Enqueues the build of ``sid`` on the build stream if it is not
@@ -249,7 +272,7 @@ class ForceServer:
                         return False
                     raise
         n = system.n
-        saved = self._aold_host.pop(sid, None)
+        saved = self._ring_index.take(sid) if self.keep_aold else None
         with torch.cuda.stream(self.build_stream):
             aold = torch.empty(n, dtype=torch.float32, device=self.dev)
             if saved is not None:  # the copy to the host came earlier on this stream
@@ -259,7 +282,7 @@ class ForceServer:
             ev = torch.cuda.Event()
             ev.record(self.build_stream)
         if saved is not None:
-            res = _Resident(system, aold, saved[2], built=ev, n_valid=saved[3])
+            res = _Resident(system, aold, saved[2][0], built=ev, n_valid=saved[2][1])
         else:
             res = _Resident(system, aold, np.zeros(n, dtype=bool), built=ev)
         self.resident[sid] = res
