@@ -323,6 +323,11 @@ def run_ours(args, rank, world):
     h2d = pos.nbytes + mass.nbytes + aold_h.numel() * 4
     d2h = acc_h.numel() * 4 + pot_h.numel() * 4
 
+    # the other workloads are single-GPU measurements: taken at N = 1 only (at
+    # N > 1 every rank would repeat them while all N GPUs are held)
+    if world > 1:
+        args.no_periodic = args.no_batching = args.no_hierarchy = args.no_isolated = True
+        args.no_ewald = args.no_species = args.no_serving = True
     # ---------------- periodic TreePM box (128^3, PM 256^3)
     periodic = None if args.no_periodic else run_periodic(ctx, tpm, torch, dev, stream, flush,
                                                           max(2, min(args.steps, 5)))
@@ -335,7 +340,7 @@ def run_ours(args, rank, world):
     ewald = None if args.no_ewald else run_ewald(ctx, tpm, torch, dev, stream, flush, max(2, min(args.steps, 3)))
     species = None if args.no_species else run_two_species(ctx, tpm, torch, dev, stream, flush,
                                                            max(2, min(args.steps, 5)))
-    plummer = run_plummer(ctx, tpm, torch, dev, stream, flush, max(3, min(args.steps, 10)))
+    plummer = None if world > 1 else run_plummer(ctx, tpm, torch, dev, stream, flush, max(3, min(args.steps, 10)))
 
     ctx.close()
     serving = None if args.no_serving else run_serving(tpm, torch, dev)
@@ -1123,7 +1128,7 @@ def main():
         floor_ctx = out.pop("_floor_ctx", None)
         samples = out["serving"].pop("_samples", None) if out.get("serving") else None
         serve_cpu = out["serving"].pop("_cpu_systems", None) if out.get("serving") else None
-        if not args.no_cpu_baseline:
+        if not args.no_cpu_baseline and world == 1:  # the CPU baseline: rank 0 at N = 1 only
             import oracle
 
             oracle.build()
