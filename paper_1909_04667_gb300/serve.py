@@ -164,9 +164,10 @@ class ForceServer:
     not evicted before that request has been served (trees built ahead for
     waiting requests would otherwise be evicted by the next build ahead).
     With ``keep_aold`` an evicted system's |a| (and which particles have one)
-    is kept in a pinned host ring of ``aold_cache_bytes`` (the oldest entries
-    are forgotten as it wraps) and restored when its tree is rebuilt: the
-    rebuilt tree is the same tree, so the relative criterion stays available.
+    is kept in a pinned host ring of ``aold_cache_bytes`` (entries that a
+    later one overwrites as the ring wraps are forgotten) and restored when
+    its tree is rebuilt: the rebuilt tree is the same tree, so the relative
+    criterion stays available.
     ``keep_results`` is a bool or a
     predicate on the request: results of the others are timed back to the
     host and dropped."""
