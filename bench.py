@@ -2,7 +2,7 @@
 force path on one GB300 (or N replicas under torchrun).
 
 Workload (headline): Hernquist halo, N = 2^20 (M = G = a = 1, r <= 100 a),
-softening h = 0.005, leaf bucket 8, all particles active.  One step is one
+softening h = 0.005, leaf bucket 16, all particles active.  One step is one
 local time step of the paper's gravity path: tree construction from scratch
 (keys, sort, nodes, FP64 monopoles) followed by the relative-criterion walk
 (alpha = 0.0025) against |a| of the previous step.  Before timing, the first
@@ -43,8 +43,8 @@ FLOPS_PER_INTERACTION = 20  # monopole pair term with potential, FP32: offset 3,
 # from: DRAM bytes (read + write) and the pipe activity of that launch (the
 # FMA pipe's busy cycles, counting the two-wide FP32 instructions, and the
 # ALU pipe's instructions, both against their peaks)
-WALK_TRAFFIC = {"bytes": 100.765184e6 + 14.582784e6,
-                "fma_pipe_active": 0.43417447, "alu_pipe_inst": 0.54919054,
+WALK_TRAFFIC = {"bytes": 87.394048e6 + 14.233344e6,
+                "fma_pipe_active": 0.43799987, "alu_pipe_inst": 0.54087898,
                 "walk_cu_sha256": "b5647f3b414cb0904d1dbc84cd4b2a472a79d8c57a0d2e47584f9ecc2cc3b967"}
 
 
@@ -60,7 +60,7 @@ def walk_capture():
     return WALK_TRAFFIC if digest == WALK_TRAFFIC["walk_cu_sha256"] else None
 
 # ------------------------------------------------------------------ configs
-HERNQUIST = dict(n=1 << 20, seed=W.CONFIG_SEEDS[2], h=0.005, G=1.0, bucket=8, theta=0.5, alpha=0.0025)
+HERNQUIST = dict(n=1 << 20, seed=W.CONFIG_SEEDS[2], h=0.005, G=1.0, bucket=16, theta=0.5, alpha=0.0025)
 PLUMMER = dict(n=8192, h=0.01, G=1.0, bucket=8, theta=0.7)
 SERVING = dict(seed=W.CONFIG_SEEDS[5], budget_gb=60, n_requests=10000, warmup_requests=4000, rate=200.0,
                load_factors=(1, 8), nmin=1 << 12, nmax=1 << 20, overcommit=1.5, bytes_per_particle=118,
@@ -1103,7 +1103,7 @@ def main():
     ap.add_argument("--profile-workload", choices=["periodic", "hernquist"], default=None,
                     help="run one workload alone (first force + three steps) for a profiler, print its step times")
     ap.add_argument("--serving-requests", type=int, default=None,
-                    help="requests of the serving measurement (default 2000; 10000 is the full stream)")
+                    help="timed requests of the serving measurement (default: the full stream of 10^4)")
     args = ap.parse_args()
     if args.bucket:
         HERNQUIST["bucket"] = args.bucket
