@@ -2,7 +2,8 @@
 computes every particle; the oracle recomputes a seeded sample one by one.
 
 Hernquist N = 2^20: geometric first force (theta = 0.5), then the relative
-criterion (alpha = 0.0025) against the previous |a|, leaf bucket 8.  The
+criterion (alpha = 0.0025) against the previous |a|, at the headline's leaf
+bucket (bench.HERNQUIST).  The
 periodic 128^3 Zel'dovich box: PM 256^3, a_s = 1.25, a_cut = 4.5.
 """
 import numpy as np

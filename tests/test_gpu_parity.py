@@ -255,16 +255,17 @@ def test_plain_fp32_arm_loses_precision_far_from_the_origin(oracle_mod, tpm, ctx
     assert p99[1.0e3][1] > 1e-4 and p99[1.0e3][1] > 20 * p99[1.0e3][0], p99
 
 
-def test_walk_relative_hernquist(oracle_mod, tpm, ctx, torch_dev):
+@pytest.mark.parametrize("bucket", [8, 16])
+def test_walk_relative_hernquist(oracle_mod, tpm, ctx, torch_dev, bucket):
     n = 1 << 16
     pos, mass = W.hernquist(n, 1002)
     shift = tuple(W.root_shift(2))
-    tree = oracle_mod.Tree(pos, mass, bucket=8, shift=shift)
+    tree = oracle_mod.Tree(pos, mass, bucket=bucket, shift=shift)
     a_bh, _, _ = tree.walk(np.arange(n), 1.0, 0.005, theta=0.5)
     a_old = np.linalg.norm(a_bh, axis=1).astype(np.float32)
     a_o, p_o, n_o = tree.walk(np.arange(n), 1.0, 0.005, crit="rel", alpha=0.0025, a_old=a_old)
     s = ctx.build_tree(to_dev(pos, torch_dev), to_dev(mass, torch_dev),
-                       tpm.BuildParams(G=1.0, h=0.005, shift=shift, leaf_bucket=8))
+                       tpm.BuildParams(G=1.0, h=0.005, shift=shift, leaf_bucket=bucket))
     acc, pot, nint = s.compute_forces(a_old=to_dev(a_old, torch_dev),
                                       fp=tpm.ForceParams(crit=tpm.CRIT_RELATIVE, alpha=0.0025))
     s.release()
